@@ -1,0 +1,192 @@
+/*
+ * hog.h -- C ABI of libhog, GB300 (sm_103a) HOG face detection.
+ *
+ * The library computes, for 8-bit grayscale frames, the HOG face-detection
+ * path of Bakker et al., "Real-time face and landmark localization for
+ * eyeblink detection" (Section 4.1.1, algorithm breakdown; Section 5.1, GPU
+ * implementation):
+ *   scale-space pyramid (5/6 steps down to the 80x80 window)
+ *   -> per-pixel gradient, 18 signed orientation bins, 8x8-pixel cells with
+ *      bilinear voting into the 4 nearest cells
+ *   -> energy of each cell and its 8 neighbours, block normalisation and
+ *      truncation into 31 features (18 signed + 9 unsigned + 4 energy)
+ *   -> correlation with F linear filters of 10x10 cells x 31 (3100 weights)
+ *   -> strict threshold, non-maximum suppression over levels and filters.
+ *
+ * Conventions for every call:
+ *   - Return HOG_OK (0) or a negative HOG_E* code.  No C++ exception crosses
+ *     the ABI.  hog_last_error(ctx) gives a message for the last failure.
+ *   - "device" pointers are CUDA device memory, "host" pointers host memory.
+ *     The caller owns every buffer it passes; the context owns its arenas
+ *     and its copy of the filters.
+ *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  Calls that return host results
+ *     synchronise that stream before returning.
+ *   - One context is used by one host thread at a time.
+ *   - Image coordinates: x = column, y = row.  Cells (i, j) = (row, col).
+ *     Windows (u, v) = (row, col) of the window's top-left cell.
+ *   - Frames smaller than min_size in either dimension have 0 levels and 0
+ *     detections; this is not an error.
+ */
+#ifndef HOG_H
+#define HOG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define HOG_OK          0
+#define HOG_EINVAL     (-1)  /* bad argument (null, size, layout, parameter)  */
+#define HOG_ENOMEM     (-2)  /* device or pinned-host allocation failed        */
+#define HOG_ECUDA      (-3)  /* a CUDA runtime call or kernel launch failed    */
+#define HOG_ECAPACITY  (-4)  /* output truncated to its capacity; counts exact */
+#define HOG_ETIMEOUT   (-5)  /* a bounded device wait gave up                  */
+#define HOG_EINTERNAL  (-6)  /* a kernel's own consistency check failed        */
+
+/* ---- fixed sizes of the method (Section 4.1.1) ------------------------- */
+#define HOG_CELL        8    /* 8x8-pixel cells                               */
+#define HOG_NBIN        18   /* signed orientation bins                       */
+#define HOG_NFEAT       31   /* 18 signed + 9 unsigned + 4 energy features    */
+#define HOG_WIN         10   /* 10x10-cell (80x80-pixel) window               */
+#define HOG_MAX_FILTERS 8    /* filters per context (the paper uses 5)        */
+#define HOG_MAX_LEVELS  32   /* pyramid levels per frame                      */
+
+typedef struct hog_ctx hog_ctx;   /* opaque, owned by the library */
+
+/* Detector parameters.  hog_default_params() fills the paper's values plus
+ * the readings this library takes where the paper is silent.  cell,
+ * win_cells_w/h and scale_num/den are fixed by the paper (8, 10, 10, 5/6);
+ * other values are rejected with HOG_EINVAL. */
+typedef struct {
+    int32_t cell;               /* 8                                          */
+    int32_t win_cells_w;        /* 10                                         */
+    int32_t win_cells_h;        /* 10                                         */
+    int32_t scale_num;          /* 5  (each level is 5/6 of the previous)     */
+    int32_t scale_den;          /* 6                                          */
+    int32_t min_size;           /* 80: keep a level while min(w,h) >= this    */
+    int32_t skip_levels;        /* 0: levels < skip_levels are not scanned    */
+    float   eps;                /* 1e-4: added to block energies              */
+    float   trunc;              /* 0.2: truncation of normalised bins         */
+    float   threshold;          /* 0: detection iff score > threshold         */
+    float   nms_iou;            /* 0.5: suppress iff IoU > nms_iou (>= 0.45)  */
+    int32_t max_w, max_h;       /* largest frame the context accepts          */
+    int32_t max_batch;          /* frames per internal batch                  */
+    int32_t max_dets_per_frame; /* device capacity of kept boxes per frame    */
+    int32_t float_pyramid;      /* 0: uint8 pyramid (detection)               */
+} hog_params;
+
+/* One frame: 8-bit grayscale, row pitch in bytes (>= w).  For the device
+ * entry points data is a device pointer; for hog_detect_host a host one. */
+typedef struct {
+    const uint8_t *data;
+    int32_t w, h, pitch;
+} hog_frame;
+
+/* One kept detection.  Box (x, y, w, h) is in frame pixels: the window's
+ * (8v, 8u, 80, 80) in level pixels scaled by (W0/Wl, H0/Hl) in FP64. */
+typedef struct {
+    int32_t frame, level, filter, u, v;
+    float   score;
+    double  x, y, w, h;
+} hog_det;
+
+/* Geometry of one pyramid level.  offset = element offset of this level in
+ * the output buffer of the call that filled it (bytes for hog_pyramid,
+ * floats for hog_features / hog_scores). */
+typedef struct {
+    int32_t w, h, cx, cy;
+    int64_t offset;
+} hog_level;
+
+/* Fill *p with the defaults listed in the struct comments; max_w/max_h
+ * 1280x1024, max_batch 64, max_dets_per_frame 16384. */
+void hog_default_params(hog_params *p);
+
+/* Level geometry for a w x h frame (host only, no GPU work).  Writes up to
+ * cap levels; *n_levels = the true count.  Offsets are those hog_features
+ * uses (floats, [cy][cx][31] per level, levels back to back). */
+int hog_level_geometry(const hog_params *p, int32_t w, int32_t h, hog_level *levels,
+                       int32_t cap, int32_t *n_levels);
+
+/* Create a context: validates *p, copies n_filters filters from host memory
+ * (layout [f][row a][col b][channel c], 10 x 10 x 31 floats each; the five
+ * rotation filters of Section 4.1.1) to the device and allocates the device
+ * arenas for max_batch frames of max_w x max_h.  *out is NULL on failure. */
+int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters,
+               hog_ctx **out);
+
+/* Replace the filters (same layout; 1 <= n_filters <= HOG_MAX_FILTERS).
+ * Stream-ordered on the legacy default stream; synchronises the device. */
+int hog_set_filters(hog_ctx *ctx, const float *filters_host, int32_t n_filters);
+
+/* Release everything the context owns.  NULL-safe. */
+void hog_destroy(hog_ctx *ctx);
+
+/* Message of the last failed call on ctx (never NULL; "" if none).  With
+ * ctx == NULL, the message of the last failed hog_create on this thread. */
+const char *hog_last_error(const hog_ctx *ctx);
+
+/* Pyramid of one frame (Section 4.1.1, first step; Section 5.1 scaling
+ * kernel): level 0 is the frame, level l+1 the 5/6 resample of level l
+ * (exact integer bilinear, pixel-centre aligned, rounded half up).  out
+ * (device, caller-owned) receives all levels back to back, [h_l][w_l]
+ * bytes each; levels (host) gets sizes and byte offsets.  HOG_EINVAL if
+ * cap_bytes or cap_levels is too small (*n_levels still set). */
+int hog_pyramid(hog_ctx *ctx, const hog_frame *frame, uint8_t *out, size_t cap_bytes,
+                hog_level *levels, int32_t cap_levels, int32_t *n_levels, void *stream);
+
+/* 31-d features of every level of one frame (Section 4.1.1 gradient,
+ * histogramisation, normalisation and feature steps).  feat_out (device,
+ * caller-owned) receives [cy][cx][31] floats per level, levels back to back
+ * at levels[l].offset.  HOG_EINVAL if a capacity is too small. */
+int hog_features(hog_ctx *ctx, const hog_frame *frame, float *feat_out, size_t cap_floats,
+                 hog_level *levels, int32_t cap_levels, int32_t *n_levels, void *stream);
+
+/* Scores of every window of every level for every filter (Section 4.1.1,
+ * linear classification filter): scores_out (device) receives
+ * [F][cy-9][cx-9] floats per level at levels[l].offset. */
+int hog_scores(hog_ctx *ctx, const hog_frame *frame, float *scores_out, size_t cap_floats,
+               hog_level *levels, int32_t cap_levels, int32_t *n_levels, void *stream);
+
+/* Detect faces in n_frames device frames (any mix of sizes <= max_w x
+ * max_h): the whole path, batched per stage, then suppression (Section
+ * 4.1.1 last step) on the device.  dets (host) receives the kept boxes of
+ * all frames, frame by frame, each frame's boxes in (level, u, v) order;
+ * counts (host, n_frames) the kept count per frame.  Returns HOG_ECAPACITY
+ * if det_cap or max_dets_per_frame truncated the output (counts exact).
+ * Synchronises the stream. */
+int hog_detect(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
+               int32_t det_cap, int32_t *counts, void *stream);
+
+/* Same result as hog_detect, from frames in HOST memory: the frames are
+ * copied to the device inside the call (pinned staging). */
+int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
+                    int32_t det_cap, int32_t *counts, void *stream);
+
+/* ---- stage timing (tracing; no counterpart in the paper, which reads its
+ * kernel times from a profiler, Section 5.1) ------------------------------ */
+#define HOG_NSTAGES 5   /* 0 pyramid, 1 gradient+histogram, 2 normalisation+
+                           features, 3 correlation+threshold, 4 suppression */
+typedef struct {
+    double  ms;         /* summed GPU time between CUDA events around the stage */
+    int64_t launches;   /* kernel launches of the stage                         */
+    int64_t units;      /* work units: output pixels, cells, cells, window x
+                           filter products, frames                            */
+} hog_stage_stat;
+
+/* Turn per-stage CUDA-event timing on (1) or off (0).  Events are recorded
+ * on the caller's stream around each stage; stats accumulate until reset. */
+int hog_set_profiling(hog_ctx *ctx, int32_t on);
+
+/* Copy the accumulated per-stage stats (HOG_NSTAGES entries) into out
+ * (host); waits for the last profiled work.  reset != 0 clears them. */
+int hog_stage_stats(hog_ctx *ctx, hog_stage_stat *out, int32_t cap, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOG_H */

@@ -1,0 +1,812 @@
+// hog_api.cu -- C ABI of libhog: contexts, device arenas, per-batch plans
+// and the orchestration of the kernels (see include/hog.h).
+//
+// Memory: a context allocates, once, arenas for max_batch frames of
+// max_w x max_h (pyramid levels >= 1, cell histograms, features in the
+// internal [4][cy][cx][8] layout, suppression keys and states, kept boxes),
+// the way the paper allocates its arrays once for a sequence of equal-size
+// images (Section 5.1).  Per call the host writes a plan -- one descriptor
+// per (frame, level), one per frame, and per kernel a list of (descriptor,
+// tile) jobs -- copies it to the device in one transfer, and launches one
+// grid per stage over all frames of the batch (the paper's grid-z batching,
+// Section 5.1, generalised to frames of different sizes).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hog_internal.cuh"
+
+using namespace hogk;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Geometry {
+    int W = 0, H = 0, nlev = 0;
+    int lw[MAX_LEVELS], lh[MAX_LEVELS], cx[MAX_LEVELS], cy[MAX_LEVELS];
+    int nu[MAX_LEVELS], nv[MAX_LEVELS], pitch[MAX_LEVELS];
+    size_t pyr_off[MAX_LEVELS];    // bytes, levels >= 1, in a slot's pyramid arena
+    size_t hist_off[MAX_LEVELS];   // floats
+    size_t feat_off[MAX_LEVELS];   // floats, internal layout
+    size_t ufeat_off[MAX_LEVELS];  // floats, user layout [cy][cx][31]
+    size_t uscore_off[MAX_LEVELS]; // floats, user layout [F][nu][nv] (F filled later)
+    int pos_off[MAX_LEVELS + 1];
+    int npos = 0;
+    size_t pyr_bytes = 0, hist_floats = 0, feat_floats = 0, ufeat_floats = 0, pyr_px = 0;
+    int32_t *d_nbr = nullptr;
+    uint8_t *d_cnt = nullptr;
+};
+
+// Level sizes: w' = floor(5w/6), h' = floor(5h/6), kept while min(w,h) >= min_size.
+int compute_geometry(const hog_params &p, int W, int H, Geometry &g) {
+    g = Geometry();
+    g.W = W;
+    g.H = H;
+    int w = W, h = H, n = 0;
+    size_t pyr = 0, hist = 0, feat = 0, ufeat = 0, px = 0;
+    int pos = 0;
+    while (w >= p.min_size && h >= p.min_size) {
+        if (n >= MAX_LEVELS) return HOG_EINVAL;
+        g.lw[n] = w;
+        g.lh[n] = h;
+        g.cx[n] = w / CELL;
+        g.cy[n] = h / CELL;
+        g.nu[n] = std::max(g.cy[n] - WIN + 1, 0);
+        g.nv[n] = std::max(g.cx[n] - WIN + 1, 0);
+        g.pitch[n] = (int)align_up((size_t)w, 16);
+        g.pyr_off[n] = pyr;
+        if (n >= 1) pyr += align_up((size_t)g.pitch[n] * h, 256);
+        g.hist_off[n] = hist;
+        hist += align_up((size_t)g.cx[n] * g.cy[n] * NBIN, 64);
+        g.feat_off[n] = feat;
+        feat += align_up((size_t)g.cx[n] * g.cy[n] * CHUNK, 64) * NCHUNK;
+        g.ufeat_off[n] = ufeat;
+        ufeat += (size_t)g.cx[n] * g.cy[n] * NFEAT;
+        px += (size_t)w * h;
+        g.pos_off[n] = pos;
+        pos += g.nu[n] * g.nv[n];
+        n++;
+        w = p.scale_num * w / p.scale_den;
+        h = p.scale_num * h / p.scale_den;
+    }
+    g.nlev = n;
+    g.pos_off[n] = pos;
+    g.npos = pos;
+    g.pyr_bytes = pyr;
+    g.hist_floats = hist;
+    g.feat_floats = feat;
+    g.ufeat_floats = ufeat;
+    g.pyr_px = px;
+    // the internal feature layout requires each chunk plane offset to keep float4 alignment
+    return HOG_OK;
+}
+
+}  // namespace
+
+struct hog_ctx {
+    hog_params p;
+    int nf = 0, nfk = 0;
+    float *d_w = nullptr;   // [4][nfk][10][10][8]
+    Geometry maxg;
+    size_t pyr_slot = 0, hist_slot = 0, feat_slot = 0, pos_slot = 0;
+    uint8_t *d_pyr = nullptr;
+    float *d_hist = nullptr, *d_feat = nullptr;
+    uint64_t *d_keys = nullptr;
+    uint8_t *d_state = nullptr;
+    hog_det *d_dets = nullptr;
+    int32_t *d_counts = nullptr;
+    int *d_flags = nullptr;
+    char *h_plan = nullptr, *d_plan = nullptr;
+    size_t plan_cap = 0;
+    hog_det *h_dets = nullptr;      // pinned
+    int32_t *h_counts = nullptr;    // pinned
+    int *h_flags = nullptr;         // pinned
+    uint8_t *h_stage = nullptr, *d_stage = nullptr;
+    size_t stage_cap = 0;
+    cudaEvent_t plan_done = nullptr;
+    // stage timing
+    bool prof = false, prof_pending = false;
+    cudaEvent_t prof_ev[2 * HOG_NSTAGES] = {};
+    hog_stage_stat stats[HOG_NSTAGES] = {};
+    std::vector<Geometry *> geoms;
+    std::string err;
+};
+
+namespace {
+
+int fail(hog_ctx *ctx, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(hog_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf; else g_create_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail((ctx), HOG_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+int check_params(const hog_params *p, std::string &why) {
+    if (!p) { why = "params is NULL"; return HOG_EINVAL; }
+    if (p->cell != CELL || p->win_cells_w != WIN || p->win_cells_h != WIN) {
+        why = "cell must be 8 and the window 10x10 cells"; return HOG_EINVAL;
+    }
+    if (p->scale_num != 5 || p->scale_den != 6) { why = "scale must be 5/6"; return HOG_EINVAL; }
+    if (p->min_size < CELL * WIN) { why = "min_size must be >= 80"; return HOG_EINVAL; }
+    if (p->skip_levels < 0) { why = "skip_levels < 0"; return HOG_EINVAL; }
+    if (!(p->eps > 0.0f) || !(p->trunc > 0.0f)) { why = "eps and trunc must be > 0"; return HOG_EINVAL; }
+    if (!(p->nms_iou >= 0.45f && p->nms_iou < 1.0f)) { why = "nms_iou must be in [0.45, 1)"; return HOG_EINVAL; }
+    if (!std::isfinite(p->threshold)) { why = "threshold must be finite"; return HOG_EINVAL; }
+    if (p->max_w < p->min_size || p->max_h < p->min_size || p->max_w > 16384 || p->max_h > 16384) {
+        why = "max_w/max_h out of range"; return HOG_EINVAL;
+    }
+    if (p->max_batch < 1 || p->max_batch > 4096) { why = "max_batch out of range"; return HOG_EINVAL; }
+    if (p->max_dets_per_frame < 1) { why = "max_dets_per_frame < 1"; return HOG_EINVAL; }
+    if (p->float_pyramid != 0) { why = "float_pyramid is only used by hog_backward"; return HOG_EINVAL; }
+    return HOG_OK;
+}
+
+int upload_filters(hog_ctx *ctx, const float *filters, int n) {
+    if (!filters || n < 1 || n > HOG_MAX_FILTERS)
+        return fail(ctx, HOG_EINVAL, "need 1..%d filters", HOG_MAX_FILTERS);
+    const int nfk = n == 1 ? 1 : (n <= 5 ? 5 : 8);
+    if (ctx->d_w && nfk != ctx->nfk) {
+        cudaFree(ctx->d_w);
+        ctx->d_w = nullptr;
+    }
+    std::vector<float> wc((size_t)NCHUNK * nfk * WIN * WIN * CHUNK, 0.0f);
+    for (int f = 0; f < n; f++)
+        for (int a = 0; a < WIN; a++)
+            for (int b = 0; b < WIN; b++)
+                for (int c = 0; c < NFEAT; c++) {
+                    const int ch = c / CHUNK, cc = c % CHUNK;
+                    wc[((((size_t)ch * nfk + f) * WIN + a) * WIN + b) * CHUNK + cc] =
+                        filters[(((size_t)f * WIN + a) * WIN + b) * NFEAT + c];
+                }
+    if (!ctx->d_w) CUDA_TRY(ctx, cudaMalloc(&ctx->d_w, wc.size() * sizeof(float)));
+    CUDA_TRY(ctx, cudaMemcpy(ctx->d_w, wc.data(), wc.size() * sizeof(float), cudaMemcpyHostToDevice));
+    ctx->nf = n;
+    ctx->nfk = nfk;
+    return HOG_OK;
+}
+
+void free_ctx(hog_ctx *ctx) {
+    if (!ctx) return;
+    auto F = [](void *p) { if (p) cudaFree(p); };
+    auto FH = [](void *p) { if (p) cudaFreeHost(p); };
+    F(ctx->d_w); F(ctx->d_pyr); F(ctx->d_hist); F(ctx->d_feat); F(ctx->d_keys);
+    F(ctx->d_state); F(ctx->d_dets); F(ctx->d_counts); F(ctx->d_flags); F(ctx->d_plan);
+    F(ctx->d_stage);
+    FH(ctx->h_plan); FH(ctx->h_dets); FH(ctx->h_counts); FH(ctx->h_flags); FH(ctx->h_stage);
+    if (ctx->plan_done) cudaEventDestroy(ctx->plan_done);
+    for (cudaEvent_t e : ctx->prof_ev)
+        if (e) cudaEventDestroy(e);
+    for (Geometry *g : ctx->geoms) {
+        F(g->d_nbr);
+        F(g->d_cnt);
+        delete g;
+    }
+    delete ctx;
+}
+
+// Geometry of a frame size, with its suppression neighbour table (built on
+// the device, on `stream`, the first time the size is seen).
+int get_geometry(hog_ctx *ctx, int W, int H, cudaStream_t stream, Geometry **out) {
+    for (Geometry *g : ctx->geoms)
+        if (g->W == W && g->H == H) { *out = g; return HOG_OK; }
+    if (ctx->geoms.size() >= 64)
+        return fail(ctx, HOG_EINVAL, "more than 64 distinct frame sizes in one context");
+    Geometry *g = new (std::nothrow) Geometry();
+    if (!g) return fail(ctx, HOG_ENOMEM, "host allocation failed");
+    int rc = compute_geometry(ctx->p, W, H, *g);
+    if (rc) { delete g; return fail(ctx, rc, "frame %dx%d has more than %d levels", W, H, MAX_LEVELS); }
+    if (g->npos > 0) {
+        cudaError_t e1 = cudaMalloc(&g->d_nbr, (size_t)g->npos * MAXN * sizeof(int32_t));
+        cudaError_t e2 = cudaMalloc(&g->d_cnt, (size_t)g->npos);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            cudaFree(g->d_nbr);
+            cudaFree(g->d_cnt);
+            delete g;
+            return fail(ctx, HOG_ENOMEM, "neighbour table allocation failed");
+        }
+        GeomDesc gd;
+        std::memset(&gd, 0, sizeof gd);
+        gd.W = W; gd.H = H; gd.nlev = g->nlev; gd.npos = g->npos;
+        gd.iou = (double)ctx->p.nms_iou;
+        for (int l = 0; l < g->nlev; l++) {
+            gd.lev_w[l] = g->lw[l]; gd.lev_h[l] = g->lh[l];
+            gd.lev_nu[l] = g->nu[l]; gd.lev_nv[l] = g->nv[l];
+            gd.lev_pos[l] = g->pos_off[l];
+        }
+        gd.lev_pos[g->nlev] = g->npos;
+        // levels l, m can only exceed the IoU threshold if area ratio allows it
+        for (int l = 0; l < g->nlev; l++) {
+            const double al = (80.0 * W / g->lw[l]) * (80.0 * H / g->lh[l]);
+            for (int m = 0; m < g->nlev; m++) {
+                const double am = (80.0 * W / g->lw[m]) * (80.0 * H / g->lh[m]);
+                const double bound = std::min(al, am) / std::max(al, am);
+                if (bound > gd.iou - 1e-12) gd.pair_mask[l] |= 1u << m;
+            }
+        }
+        *ctx->h_flags = 0;
+        cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), stream);
+        cudaError_t e = launch_nms_geometry(gd, g->d_nbr, g->d_cnt, ctx->d_flags, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int),
+                                                  cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) {
+            cudaFree(g->d_nbr); cudaFree(g->d_cnt); delete g;
+            return fail(ctx, HOG_ECUDA, "suppression geometry: %s", cudaGetErrorString(e));
+        }
+        if (*ctx->h_flags) {
+            cudaFree(g->d_nbr); cudaFree(g->d_cnt); delete g;
+            return fail(ctx, HOG_EINVAL, "nms_iou %.3f gives more than %d overlapping windows",
+                        (double)ctx->p.nms_iou, MAXN);
+        }
+    }
+    ctx->geoms.push_back(g);
+    *out = g;
+    return HOG_OK;
+}
+
+// ---- plans ---------------------------------------------------------------
+
+struct PlanBuilder {
+    std::vector<LevelDesc> descs;
+    std::vector<FrameDesc> frames;
+    std::vector<std::vector<Job>> pyr;   // per step (target level)
+    std::vector<Job> hist, feat, corr;
+};
+
+struct PlanLayout {
+    size_t descs = 0, frames = 0, hist = 0, feat = 0, corr = 0, total = 0;
+    std::vector<size_t> pyr;
+    std::vector<int> npyr;
+};
+
+// Per-frame options for plan building.
+struct FrameOpts {
+    float *feat_user = nullptr;     // [cy][cx][31] per level, at geometry ufeat offsets
+    float *scores_user = nullptr;   // [F][nu][nv] per level
+    const size_t *score_off = nullptr;
+    bool corr = true, nms = true, feat = true;
+};
+
+void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame &f, int slot,
+               int frame_index, const FrameOpts &o) {
+    uint8_t *pyr = ctx->d_pyr + (size_t)slot * ctx->pyr_slot;
+    float *hist = ctx->d_hist + (size_t)slot * ctx->hist_slot;
+    float *feat = ctx->d_feat + (size_t)slot * ctx->feat_slot;
+    uint64_t *keys = ctx->d_keys + (size_t)slot * ctx->pos_slot;
+    const int first = (int)pb.descs.size();
+    for (int l = 0; l < g.nlev; l++) {
+        LevelDesc d;
+        std::memset(&d, 0, sizeof d);
+        d.w = g.lw[l]; d.h = g.lh[l];
+        d.cx = g.cx[l]; d.cy = g.cy[l]; d.nu = g.nu[l]; d.nv = g.nv[l];
+        d.frame = frame_index; d.level = l;
+        d.scan = l >= ctx->p.skip_levels ? 1 : 0;
+        d.pos_off = g.pos_off[l];
+        if (l == 0) {
+            d.img = f.data;
+            d.pitch = f.pitch;
+        } else {
+            d.dst = pyr + g.pyr_off[l];
+            d.img = d.dst;
+            d.pitch = g.pitch[l];
+            const LevelDesc &prev = pb.descs[first + l - 1];
+            d.src = prev.img;
+            d.sw = prev.w; d.sh = prev.h; d.spitch = prev.pitch;
+        }
+        d.hist = hist + g.hist_off[l];
+        d.feat = feat + g.feat_off[l];
+        d.feat_user = o.feat_user ? o.feat_user + g.ufeat_off[l] : nullptr;
+        d.scores_user = o.scores_user ? o.scores_user + o.score_off[l] : nullptr;
+        d.keys = keys + g.pos_off[l];
+        pb.descs.push_back(d);
+        const int di = first + l;
+        if (l >= 1) {
+            if ((int)pb.pyr.size() < l + 1) pb.pyr.resize(l + 1);
+            const int nt = ((d.w + PYR_TX - 1) / PYR_TX) * ((d.h + PYR_TY - 1) / PYR_TY);
+            for (int k = 0; k < nt; k++) pb.pyr[l].push_back({di, k});
+        }
+        if (o.feat) {
+            const int nh = ((d.cx + HIST_TX - 1) / HIST_TX) * ((d.cy + HIST_TY - 1) / HIST_TY);
+            for (int k = 0; k < nh; k++) pb.hist.push_back({di, k});
+            const int nfj = ((d.cx + FEAT_TX - 1) / FEAT_TX) * ((d.cy + FEAT_TY - 1) / FEAT_TY);
+            for (int k = 0; k < nfj; k++) pb.feat.push_back({di, k});
+        }
+        if (o.corr && d.nu > 0 && d.nv > 0 && (d.scan || o.scores_user)) {
+            const int nc = ((d.nu + CORR_TU - 1) / CORR_TU) * ((d.nv + CORR_TV - 1) / CORR_TV);
+            for (int k = 0; k < nc; k++) pb.corr.push_back({di, k});
+        }
+    }
+    if (o.nms) {
+        FrameDesc fd;
+        std::memset(&fd, 0, sizeof fd);
+        fd.W = g.W; fd.H = g.H; fd.nlev = g.nlev; fd.npos = g.npos;
+        fd.frame = frame_index;
+        for (int l = 0; l < g.nlev; l++) {
+            fd.lev_w[l] = g.lw[l]; fd.lev_h[l] = g.lh[l];
+            fd.lev_nu[l] = g.nu[l]; fd.lev_nv[l] = g.nv[l];
+            fd.lev_pos[l] = g.pos_off[l];
+        }
+        fd.lev_pos[g.nlev] = g.npos;
+        fd.keys = keys;
+        fd.state = ctx->d_state + (size_t)slot * ctx->pos_slot;
+        fd.nbr = g.d_nbr;
+        fd.nbr_cnt = g.d_cnt;
+        fd.out = ctx->d_dets + (size_t)slot * ctx->p.max_dets_per_frame;
+        fd.out_cap = ctx->p.max_dets_per_frame;
+        fd.count = ctx->d_counts + slot;
+        pb.frames.push_back(fd);
+    }
+}
+
+int layout_plan(const PlanBuilder &pb, PlanLayout &L) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.descs = take(pb.descs.size() * sizeof(LevelDesc));
+    L.frames = take(pb.frames.size() * sizeof(FrameDesc));
+    L.pyr.resize(pb.pyr.size());
+    L.npyr.resize(pb.pyr.size());
+    for (size_t s = 0; s < pb.pyr.size(); s++) {
+        L.pyr[s] = take(pb.pyr[s].size() * sizeof(Job));
+        L.npyr[s] = (int)pb.pyr[s].size();
+    }
+    L.hist = take(pb.hist.size() * sizeof(Job));
+    L.feat = take(pb.feat.size() * sizeof(Job));
+    L.corr = take(pb.corr.size() * sizeof(Job));
+    L.total = off;
+    return HOG_OK;
+}
+
+int ensure_plan_capacity(hog_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->plan_cap) return HOG_OK;
+    size_t cap = align_up(std::max(bytes, ctx->plan_cap * 2), 1 << 16);
+    if (ctx->plan_done) cudaEventSynchronize(ctx->plan_done);
+    cudaFreeHost(ctx->h_plan);
+    cudaFree(ctx->d_plan);
+    ctx->h_plan = nullptr;
+    ctx->d_plan = nullptr;
+    ctx->plan_cap = 0;
+    CUDA_TRY(ctx, cudaMallocHost(&ctx->h_plan, cap));
+    CUDA_TRY(ctx, cudaMalloc(&ctx->d_plan, cap));
+    ctx->plan_cap = cap;
+    return HOG_OK;
+}
+
+// Fold the elapsed times of the last profiled plan into the stats.
+int collect_profile(hog_ctx *ctx) {
+    if (!ctx->prof_pending) return HOG_OK;
+    CUDA_TRY(ctx, cudaEventSynchronize(ctx->prof_ev[2 * HOG_NSTAGES - 1]));
+    for (int k = 0; k < HOG_NSTAGES; k++) {
+        float ms = 0.0f;
+        CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->prof_ev[2 * k], ctx->prof_ev[2 * k + 1]));
+        ctx->stats[k].ms += ms;
+    }
+    ctx->prof_pending = false;
+    return HOG_OK;
+}
+
+// Copy the plan to the device and launch the stages on `stream`.
+int run_plan(hog_ctx *ctx, const PlanBuilder &pb, cudaStream_t stream) {
+    PlanLayout L;
+    layout_plan(pb, L);
+    int rc = ensure_plan_capacity(ctx, L.total);
+    if (rc) return rc;
+    CUDA_TRY(ctx, cudaEventSynchronize(ctx->plan_done));   // previous plan copy has finished
+    char *h = ctx->h_plan;
+    std::memcpy(h + L.descs, pb.descs.data(), pb.descs.size() * sizeof(LevelDesc));
+    std::memcpy(h + L.frames, pb.frames.data(), pb.frames.size() * sizeof(FrameDesc));
+    for (size_t s = 0; s < pb.pyr.size(); s++)
+        std::memcpy(h + L.pyr[s], pb.pyr[s].data(), pb.pyr[s].size() * sizeof(Job));
+    std::memcpy(h + L.hist, pb.hist.data(), pb.hist.size() * sizeof(Job));
+    std::memcpy(h + L.feat, pb.feat.data(), pb.feat.size() * sizeof(Job));
+    std::memcpy(h + L.corr, pb.corr.data(), pb.corr.size() * sizeof(Job));
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_plan, h, L.total, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->plan_done, stream));
+    char *d = ctx->d_plan;
+    const LevelDesc *descs = reinterpret_cast<const LevelDesc *>(d + L.descs);
+    rc = collect_profile(ctx);
+    if (rc) return rc;
+    auto mark = [&](int i) -> cudaError_t {
+        return ctx->prof ? cudaEventRecord(ctx->prof_ev[i], stream) : cudaSuccess;
+    };
+    int64_t px = 0, cells = 0, wins = 0;
+    for (const LevelDesc &ld : pb.descs) {
+        if (ld.level >= 1) px += (int64_t)ld.w * ld.h;
+        cells += (int64_t)ld.cx * ld.cy;
+    }
+    for (const Job &j : pb.corr) (void)j;
+    for (size_t k = 0; k < pb.descs.size(); k++) {
+        const LevelDesc &ld = pb.descs[k];
+        if (ld.nu > 0 && ld.nv > 0 && (ld.scan || ld.scores_user)) wins += (int64_t)ld.nu * ld.nv;
+    }
+    const bool do_corr = !pb.corr.empty();
+    CUDA_TRY(ctx, mark(0));
+    int npyr = 0;
+    for (size_t s = 1; s < pb.pyr.size(); s++) {
+        CUDA_TRY(ctx, launch_pyramid(descs, reinterpret_cast<const Job *>(d + L.pyr[s]),
+                                     L.npyr[s], stream));
+        npyr += L.npyr[s] > 0;
+    }
+    CUDA_TRY(ctx, mark(1));
+    CUDA_TRY(ctx, mark(2));
+    CUDA_TRY(ctx, launch_hist(descs, reinterpret_cast<const Job *>(d + L.hist),
+                              (int)pb.hist.size(), stream));
+    CUDA_TRY(ctx, mark(3));
+    CUDA_TRY(ctx, mark(4));
+    CUDA_TRY(ctx, launch_feat(descs, reinterpret_cast<const Job *>(d + L.feat),
+                              (int)pb.feat.size(), ctx->p.eps, ctx->p.trunc, stream));
+    CUDA_TRY(ctx, mark(5));
+    CUDA_TRY(ctx, mark(6));
+    CUDA_TRY(ctx, launch_corr(descs, reinterpret_cast<const Job *>(d + L.corr),
+                              (int)pb.corr.size(), ctx->d_w, ctx->nfk, ctx->nf,
+                              ctx->p.threshold, stream));
+    CUDA_TRY(ctx, mark(7));
+    CUDA_TRY(ctx, mark(8));
+    if (!pb.frames.empty())
+        CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames),
+                                 (int)pb.frames.size(), ctx->d_flags, stream));
+    CUDA_TRY(ctx, mark(9));
+    if (ctx->prof) {
+        ctx->prof_pending = true;
+        hog_stage_stat *st = ctx->stats;
+        st[0].launches += npyr; st[0].units += px;
+        st[1].launches += !pb.hist.empty(); st[1].units += pb.hist.empty() ? 0 : cells;
+        st[2].launches += !pb.feat.empty(); st[2].units += pb.feat.empty() ? 0 : cells;
+        st[3].launches += do_corr; st[3].units += do_corr ? wins * ctx->nf : 0;
+        st[4].launches += !pb.frames.empty(); st[4].units += (int64_t)pb.frames.size();
+    }
+    return HOG_OK;
+}
+
+int check_frame(hog_ctx *ctx, const hog_frame *f, bool device) {
+    if (!f) return fail(ctx, HOG_EINVAL, "frame is NULL");
+    if (f->w < 0 || f->h < 0 || f->w > ctx->p.max_w || f->h > ctx->p.max_h)
+        return fail(ctx, HOG_EINVAL, "frame %dx%d outside 0..%dx%d", f->w, f->h, ctx->p.max_w,
+                    ctx->p.max_h);
+    if (f->w > 0 && f->h > 0 && (!f->data || f->pitch < f->w))
+        return fail(ctx, HOG_EINVAL, "frame data NULL or pitch %d < width %d", f->pitch, f->w);
+    (void)device;
+    return HOG_OK;
+}
+
+int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, hog_det *dets,
+                  int det_cap, int *written_out, int32_t *counts, cudaStream_t stream) {
+    int written = 0;
+    bool truncated = false;
+    for (int b0 = 0; b0 < n; b0 += ctx->p.max_batch) {
+        const int nb = std::min(ctx->p.max_batch, n - b0);
+        PlanBuilder pb;
+        for (int i = 0; i < nb; i++) {
+            const hog_frame &f = frames[b0 + i];
+            if (f.w < ctx->p.min_size || f.h < ctx->p.min_size) continue;
+            Geometry *g;
+            int rc = get_geometry(ctx, f.w, f.h, stream, &g);
+            if (rc) return rc;
+            FrameOpts o;
+            o.nms = g->npos > 0;
+            add_frame(ctx, pb, *g, f, i, frame_base + b0 + i, o);
+        }
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_counts, 0, sizeof(int32_t) * nb, stream));
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), stream));
+        int rc = run_plan(ctx, pb, stream);
+        if (rc) return rc;
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, sizeof(int32_t) * nb,
+                                      cudaMemcpyDeviceToHost, stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        // kept boxes: one copy per frame that has any, into pinned staging
+        const size_t D = (size_t)ctx->p.max_dets_per_frame;
+        for (int i = 0; i < nb; i++) {
+            const int k = std::min(ctx->h_counts[i], ctx->p.max_dets_per_frame);
+            if (k > 0)
+                CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_dets + i * D, ctx->d_dets + i * D,
+                                              sizeof(hog_det) * k, cudaMemcpyDeviceToHost, stream));
+        }
+        CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        for (int i = 0; i < nb; i++) {
+            const int c = ctx->h_counts[i];
+            if (counts) counts[b0 + i] = c;
+            const int k = std::min(c, ctx->p.max_dets_per_frame);
+            if (c > k) truncated = true;
+            for (int j = 0; j < k; j++) {
+                if (written < det_cap && dets) dets[written++] = ctx->h_dets[i * D + j];
+                else truncated = true;
+            }
+        }
+    }
+    if (written_out) *written_out = written;
+    return truncated ? fail(ctx, HOG_ECAPACITY, "detections truncated (%d written)", written)
+                     : HOG_OK;
+}
+
+}  // namespace
+
+// ==== C ABI ===============================================================
+
+extern "C" {
+
+void hog_default_params(hog_params *p) {
+    if (!p) return;
+    p->cell = CELL;
+    p->win_cells_w = WIN;
+    p->win_cells_h = WIN;
+    p->scale_num = 5;
+    p->scale_den = 6;
+    p->min_size = 80;
+    p->skip_levels = 0;
+    p->eps = 1e-4f;
+    p->trunc = 0.2f;
+    p->threshold = 0.0f;
+    p->nms_iou = 0.5f;
+    p->max_w = 1280;
+    p->max_h = 1024;
+    p->max_batch = 64;
+    p->max_dets_per_frame = 16384;
+    p->float_pyramid = 0;
+}
+
+int hog_level_geometry(const hog_params *p, int32_t w, int32_t h, hog_level *levels, int32_t cap,
+                       int32_t *n_levels) {
+    std::string why;
+    if (check_params(p, why)) return HOG_EINVAL;
+    if (w < 0 || h < 0 || !n_levels || (cap > 0 && !levels)) return HOG_EINVAL;
+    Geometry g;
+    if (compute_geometry(*p, w, h, g)) return HOG_EINVAL;
+    *n_levels = g.nlev;
+    for (int l = 0; l < g.nlev && l < cap; l++)
+        levels[l] = hog_level{g.lw[l], g.lh[l], g.cx[l], g.cy[l], (int64_t)g.ufeat_off[l]};
+    return g.nlev > cap ? HOG_EINVAL : HOG_OK;
+}
+
+int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters, hog_ctx **out) {
+    if (!out) { g_create_error = "out is NULL"; return HOG_EINVAL; }
+    *out = nullptr;
+    std::string why;
+    if (check_params(p, why)) { g_create_error = why; return HOG_EINVAL; }
+    hog_ctx *ctx = new (std::nothrow) hog_ctx();
+    if (!ctx) { g_create_error = "host allocation failed"; return HOG_ENOMEM; }
+    ctx->p = *p;
+    int rc = upload_filters(ctx, filters_host, n_filters);
+    if (rc) { g_create_error = ctx->err; free_ctx(ctx); return rc; }
+    if (compute_geometry(ctx->p, ctx->p.max_w, ctx->p.max_h, ctx->maxg)) {
+        g_create_error = "max frame has too many levels";
+        free_ctx(ctx);
+        return HOG_EINVAL;
+    }
+    const Geometry &g = ctx->maxg;
+    ctx->pyr_slot = align_up(std::max<size_t>(g.pyr_bytes, 256), 256);
+    ctx->hist_slot = align_up(std::max<size_t>(g.hist_floats, 64), 64);
+    ctx->feat_slot = align_up(std::max<size_t>(g.feat_floats, 64), 64);
+    ctx->pos_slot = align_up(std::max<size_t>(g.npos, 1), 32);
+    const size_t B = (size_t)ctx->p.max_batch;
+    const size_t D = (size_t)ctx->p.max_dets_per_frame;
+    cudaError_t e = cudaSuccess;
+    auto M = [&](void **ptr, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(ptr, bytes); };
+    M((void **)&ctx->d_pyr, B * ctx->pyr_slot);
+    M((void **)&ctx->d_hist, B * ctx->hist_slot * sizeof(float));
+    M((void **)&ctx->d_feat, B * ctx->feat_slot * sizeof(float));
+    M((void **)&ctx->d_keys, B * ctx->pos_slot * sizeof(uint64_t));
+    M((void **)&ctx->d_state, B * ctx->pos_slot);
+    M((void **)&ctx->d_dets, B * D * sizeof(hog_det));
+    M((void **)&ctx->d_counts, B * sizeof(int32_t));
+    M((void **)&ctx->d_flags, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_dets, B * D * sizeof(hog_det));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_counts, B * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_flags, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->plan_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("allocation failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        free_ctx(ctx);
+        return HOG_ENOMEM;
+    }
+    rc = ensure_plan_capacity(ctx, 1 << 20);
+    if (rc) { g_create_error = ctx->err; free_ctx(ctx); return rc; }
+    *out = ctx;
+    return HOG_OK;
+}
+
+int hog_set_filters(hog_ctx *ctx, const float *filters_host, int32_t n_filters) {
+    if (!ctx) return HOG_EINVAL;
+    cudaDeviceSynchronize();
+    return upload_filters(ctx, filters_host, n_filters);
+}
+
+void hog_destroy(hog_ctx *ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    free_ctx(ctx);
+}
+
+const char *hog_last_error(const hog_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int hog_set_profiling(hog_ctx *ctx, int32_t on) {
+    if (!ctx) return HOG_EINVAL;
+    if (on && !ctx->prof_ev[0])
+        for (cudaEvent_t &e : ctx->prof_ev) CUDA_TRY(ctx, cudaEventCreate(&e));
+    int rc = collect_profile(ctx);
+    if (rc) return rc;
+    ctx->prof = on != 0;
+    return HOG_OK;
+}
+
+int hog_stage_stats(hog_ctx *ctx, hog_stage_stat *out, int32_t cap, int32_t reset) {
+    if (!ctx || (cap > 0 && !out)) return HOG_EINVAL;
+    int rc = collect_profile(ctx);
+    if (rc) return rc;
+    for (int k = 0; k < HOG_NSTAGES && k < cap; k++) out[k] = ctx->stats[k];
+    if (reset) std::memset(ctx->stats, 0, sizeof ctx->stats);
+    return HOG_OK;
+}
+
+int hog_pyramid(hog_ctx *ctx, const hog_frame *frame, uint8_t *out, size_t cap_bytes,
+                hog_level *levels, int32_t cap_levels, int32_t *n_levels, void *stream_) {
+    if (!ctx) return HOG_EINVAL;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int rc = check_frame(ctx, frame, true);
+    if (rc) return rc;
+    if (!n_levels) return fail(ctx, HOG_EINVAL, "n_levels is NULL");
+    Geometry g;
+    if (compute_geometry(ctx->p, frame->w, frame->h, g)) return fail(ctx, HOG_EINVAL, "too many levels");
+    *n_levels = g.nlev;
+    if (g.nlev > cap_levels || (g.nlev > 0 && !levels))
+        return fail(ctx, HOG_EINVAL, "level capacity %d < %d", cap_levels, g.nlev);
+    size_t off = 0;
+    for (int l = 0; l < g.nlev; l++) {
+        levels[l] = hog_level{g.lw[l], g.lh[l], g.cx[l], g.cy[l], (int64_t)off};
+        off += (size_t)g.lw[l] * g.lh[l];
+    }
+    if (g.nlev == 0) return HOG_OK;
+    if (!out || off > cap_bytes) return fail(ctx, HOG_EINVAL, "output capacity %zu < %zu", cap_bytes, off);
+    PlanBuilder pb;
+    FrameOpts o;
+    o.corr = false; o.nms = false; o.feat = false;
+    add_frame(ctx, pb, g, *frame, 0, 0, o);
+    rc = run_plan(ctx, pb, stream);
+    if (rc) return rc;
+    for (int l = 0; l < g.nlev; l++) {
+        const LevelDesc &d = pb.descs[l];
+        CUDA_TRY(ctx, cudaMemcpy2DAsync(out + levels[l].offset, (size_t)d.w, d.img, (size_t)d.pitch,
+                                        (size_t)d.w, (size_t)d.h, cudaMemcpyDeviceToDevice, stream));
+    }
+    return HOG_OK;
+}
+
+int hog_features(hog_ctx *ctx, const hog_frame *frame, float *feat_out, size_t cap_floats,
+                 hog_level *levels, int32_t cap_levels, int32_t *n_levels, void *stream_) {
+    if (!ctx) return HOG_EINVAL;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int rc = check_frame(ctx, frame, true);
+    if (rc) return rc;
+    if (!n_levels) return fail(ctx, HOG_EINVAL, "n_levels is NULL");
+    Geometry g;
+    if (compute_geometry(ctx->p, frame->w, frame->h, g)) return fail(ctx, HOG_EINVAL, "too many levels");
+    *n_levels = g.nlev;
+    if (g.nlev > cap_levels || (g.nlev > 0 && !levels))
+        return fail(ctx, HOG_EINVAL, "level capacity %d < %d", cap_levels, g.nlev);
+    for (int l = 0; l < g.nlev; l++)
+        levels[l] = hog_level{g.lw[l], g.lh[l], g.cx[l], g.cy[l], (int64_t)g.ufeat_off[l]};
+    if (g.nlev == 0) return HOG_OK;
+    if (!feat_out || g.ufeat_floats > cap_floats)
+        return fail(ctx, HOG_EINVAL, "feature capacity %zu < %zu floats", cap_floats, g.ufeat_floats);
+    PlanBuilder pb;
+    FrameOpts o;
+    o.corr = false; o.nms = false;
+    o.feat_user = feat_out;
+    add_frame(ctx, pb, g, *frame, 0, 0, o);
+    return run_plan(ctx, pb, stream);
+}
+
+int hog_scores(hog_ctx *ctx, const hog_frame *frame, float *scores_out, size_t cap_floats,
+               hog_level *levels, int32_t cap_levels, int32_t *n_levels, void *stream_) {
+    if (!ctx) return HOG_EINVAL;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int rc = check_frame(ctx, frame, true);
+    if (rc) return rc;
+    if (!n_levels) return fail(ctx, HOG_EINVAL, "n_levels is NULL");
+    Geometry g;
+    if (compute_geometry(ctx->p, frame->w, frame->h, g)) return fail(ctx, HOG_EINVAL, "too many levels");
+    *n_levels = g.nlev;
+    if (g.nlev > cap_levels || (g.nlev > 0 && !levels))
+        return fail(ctx, HOG_EINVAL, "level capacity %d < %d", cap_levels, g.nlev);
+    size_t off = 0, soff[MAX_LEVELS];
+    for (int l = 0; l < g.nlev; l++) {
+        soff[l] = off;
+        levels[l] = hog_level{g.lw[l], g.lh[l], g.cx[l], g.cy[l], (int64_t)off};
+        off += (size_t)ctx->nf * g.nu[l] * g.nv[l];
+    }
+    if (g.nlev == 0 || off == 0) return HOG_OK;
+    if (!scores_out || off > cap_floats)
+        return fail(ctx, HOG_EINVAL, "score capacity %zu < %zu floats", cap_floats, off);
+    PlanBuilder pb;
+    FrameOpts o;
+    o.nms = false;
+    o.scores_user = scores_out;
+    o.score_off = soff;
+    add_frame(ctx, pb, g, *frame, 0, 0, o);
+    return run_plan(ctx, pb, stream);
+}
+
+int hog_detect(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
+               int32_t det_cap, int32_t *counts, void *stream_) {
+    if (!ctx) return HOG_EINVAL;
+    if (n_frames < 0 || (n_frames > 0 && !frames) || det_cap < 0 || (det_cap > 0 && !dets))
+        return fail(ctx, HOG_EINVAL, "bad frames/dets arguments");
+    for (int i = 0; i < n_frames; i++) {
+        int rc = check_frame(ctx, &frames[i], true);
+        if (rc) return rc;
+    }
+    return detect_device(ctx, frames, n_frames, 0, dets, det_cap, nullptr, counts,
+                         (cudaStream_t)stream_);
+}
+
+int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
+                    int32_t det_cap, int32_t *counts, void *stream_) {
+    if (!ctx) return HOG_EINVAL;
+    if (n_frames < 0 || (n_frames > 0 && !frames) || det_cap < 0 || (det_cap > 0 && !dets))
+        return fail(ctx, HOG_EINVAL, "bad frames/dets arguments");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const size_t fbytes = (size_t)ctx->p.max_w * ctx->p.max_h;
+    if (!ctx->d_stage) {
+        ctx->stage_cap = fbytes * ctx->p.max_batch;
+        CUDA_TRY(ctx, cudaMalloc(&ctx->d_stage, ctx->stage_cap));
+        CUDA_TRY(ctx, cudaMallocHost(&ctx->h_stage, ctx->stage_cap));
+    }
+    int total = 0;
+    bool truncated = false;
+    std::vector<hog_frame> dev((size_t)ctx->p.max_batch);
+    for (int b0 = 0; b0 < n_frames; b0 += ctx->p.max_batch) {
+        const int nb = std::min(ctx->p.max_batch, n_frames - b0);
+        for (int i = 0; i < nb; i++) {
+            const hog_frame &f = frames[b0 + i];
+            int rc = check_frame(ctx, &f, false);
+            if (rc) return rc;
+            uint8_t *d = ctx->d_stage + (size_t)i * fbytes;
+            dev[i] = hog_frame{d, f.w, f.h, f.w};
+            if (f.w == 0 || f.h == 0) continue;
+            cudaPointerAttributes attr;
+            const bool pinned = cudaPointerGetAttributes(&attr, f.data) == cudaSuccess &&
+                                attr.type == cudaMemoryTypeHost;
+            cudaGetLastError();
+            const uint8_t *srcp = f.data;
+            size_t spitch = (size_t)f.pitch;
+            if (!pinned) {   // stage through pinned memory so the copy is asynchronous
+                uint8_t *h = ctx->h_stage + (size_t)i * fbytes;
+                for (int y = 0; y < f.h; y++) std::memcpy(h + (size_t)y * f.w, f.data + (size_t)y * f.pitch, f.w);
+                srcp = h;
+                spitch = (size_t)f.w;
+            }
+            CUDA_TRY(ctx, cudaMemcpy2DAsync(d, (size_t)f.w, srcp, spitch, (size_t)f.w, (size_t)f.h,
+                                            cudaMemcpyHostToDevice, stream));
+        }
+        const int cap = dets ? std::max(det_cap - total, 0) : 0;
+        int wrote = 0;
+        int rc = detect_device(ctx, dev.data(), nb, b0, dets ? dets + total : nullptr, cap, &wrote,
+                               counts ? counts + b0 : nullptr, stream);
+        if (rc == HOG_ECAPACITY) truncated = true;
+        else if (rc) return rc;
+        total += wrote;
+    }
+    return truncated ? fail(ctx, HOG_ECAPACITY, "detections truncated") : HOG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// hog_internal.cuh -- descriptors and kernel entry points shared by the
+// translation units of libhog.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hog.h"
+
+namespace hogk {
+
+constexpr int CELL = 8;
+constexpr int NBIN = 18;
+constexpr int NFEAT = 31;
+constexpr int WIN = 10;
+constexpr int CHUNK = 8;            // channels per chunk of the internal feature layout
+constexpr int NCHUNK = 4;           // 4 x 8 = 32 channels (31 + one zero pad)
+constexpr int MAX_LEVELS = HOG_MAX_LEVELS;
+constexpr int MAXN = 192;           // suppression neighbours per window position (<= 150 seen at IoU 0.45)
+
+// Tile shapes of the plain kernels.
+constexpr int PYR_TX = 128, PYR_TY = 8;          // output pixels per CTA (256 threads)
+constexpr int HIST_TX = 32, HIST_TY = 4;         // cells per CTA (128 threads)
+constexpr int FEAT_TX = 32, FEAT_TY = 8;         // cells per CTA (256 threads)
+constexpr int CORR_TU = 16, CORR_TV = 32;        // windows per CTA (128 threads)
+
+// A key ranks suppression candidates: smaller key = higher rank.  High word
+// = score mapped to a descending unsigned order, low word = (level, filter,
+// u, v) so that equal scores fall back to ascending (level, filter, u, v).
+constexpr uint64_t KEY_NONE = ~0ull;
+
+__host__ __device__ inline uint32_t float_to_ascending(float s) {
+#ifdef __CUDA_ARCH__
+    uint32_t u = __float_as_uint(s);
+#else
+    uint32_t u;
+    static_assert(sizeof(float) == 4, "");
+    __builtin_memcpy(&u, &s, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__host__ __device__ inline float ascending_to_float(uint32_t o) {
+    uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    __builtin_memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+
+__host__ __device__ inline uint64_t make_key(float score, int level, int filter, int u, int v) {
+    score = score + 0.0f;   // -0 -> +0: equal scores must share a key prefix
+    uint32_t hi = ~float_to_ascending(score);
+    uint32_t lo = ((uint32_t)level << 27) | ((uint32_t)filter << 24) |
+                  ((uint32_t)u << 12) | (uint32_t)v;
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__host__ __device__ inline float key_score(uint64_t k) {
+    return ascending_to_float(~(uint32_t)(k >> 32));
+}
+__host__ __device__ inline int key_level(uint64_t k) { return (int)((k >> 27) & 31); }
+__host__ __device__ inline int key_filter(uint64_t k) { return (int)((k >> 24) & 7); }
+__host__ __device__ inline int key_u(uint64_t k) { return (int)((k >> 12) & 4095); }
+__host__ __device__ inline int key_v(uint64_t k) { return (int)(k & 4095); }
+
+// One (frame, level) of a batch.
+struct LevelDesc {
+    const uint8_t *img;     // this level's image (level 0: the caller's frame)
+    uint8_t *dst;           // where a pyramid job writes this level (levels >= 1)
+    const uint8_t *src;     // previous level (pyramid jobs)
+    int32_t w, h, pitch;    // this level
+    int32_t sw, sh, spitch; // previous level
+    int32_t cx, cy, nu, nv; // cells, windows
+    int32_t frame, level;   // batch-relative frame index, level index
+    int32_t scan;           // 1: this level takes part in detection
+    int32_t pos_off;        // first window position of this level in the frame
+    float *hist;            // [cy][cx][18]
+    float *feat;            // [4][cy][cx][8] internal layout
+    float *feat_user;       // optional [cy][cx][31] copy (hog_features)
+    float *scores_user;     // optional [F][nu][nv] (hog_scores)
+    uint64_t *keys;         // [nu][nv] suppression keys of this level
+};
+
+// Per-frame suppression work.
+struct FrameDesc {
+    int32_t W, H, nlev, npos;
+    int32_t frame;                    // batch-relative frame index
+    int32_t lev_w[MAX_LEVELS], lev_h[MAX_LEVELS];
+    int32_t lev_nu[MAX_LEVELS], lev_nv[MAX_LEVELS];
+    int32_t lev_pos[MAX_LEVELS + 1];
+    const uint64_t *keys;             // [npos]
+    uint8_t *state;                   // [npos]
+    const int32_t *nbr;               // [npos][MAXN]
+    const uint8_t *nbr_cnt;           // [npos]
+    hog_det *out;                     // [out_cap]
+    int32_t out_cap;
+    int32_t *count;                   // kept count (exact)
+};
+
+struct Job {
+    int32_t desc;
+    int32_t tile;
+};
+
+// Geometry of one frame size for suppression: window positions of all
+// levels, neighbour lists (IoU > nms_iou), built once per frame size.
+struct GeomDesc {
+    int32_t W, H, nlev, npos;
+    double iou;
+    int32_t lev_w[MAX_LEVELS], lev_h[MAX_LEVELS];
+    int32_t lev_nu[MAX_LEVELS], lev_nv[MAX_LEVELS];
+    int32_t lev_pos[MAX_LEVELS + 1];
+    uint32_t pair_mask[MAX_LEVELS];   // bit m set: levels (l, m) can exceed the IoU
+};
+
+// ---- launchers (each enqueues on `stream`; return cudaGetLastError()) ----
+cudaError_t launch_pyramid(const LevelDesc *descs, const Job *jobs, int njobs,
+                           cudaStream_t stream);
+cudaError_t launch_hist(const LevelDesc *descs, const Job *jobs, int njobs,
+                        cudaStream_t stream);
+cudaError_t launch_feat(const LevelDesc *descs, const Job *jobs, int njobs, float eps,
+                        float tau, cudaStream_t stream);
+cudaError_t launch_corr(const LevelDesc *descs, const Job *jobs, int njobs,
+                        const float *wchunks, int nf_kernel, int nf_real, float threshold,
+                        cudaStream_t stream);
+cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, uint8_t *cnt, int *overflow,
+                                cudaStream_t stream);
+cudaError_t launch_nms(const FrameDesc *frames, int nframes, int *flags, cudaStream_t stream);
+
+}  // namespace hogk

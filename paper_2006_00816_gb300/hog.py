@@ -1,0 +1,252 @@
+"""Python binding of libhog (ctypes; argument marshalling only).
+
+Every step of the detection path runs in the CUDA kernels behind the C ABI of
+``include/hog.h``.  PyTorch supplies device memory and the current stream.
+If ``libhog.so`` is missing this module raises at import: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhog.so")
+
+HOG_OK, HOG_EINVAL, HOG_ENOMEM, HOG_ECUDA, HOG_ECAPACITY, HOG_ETIMEOUT, HOG_EINTERNAL = (
+    0, -1, -2, -3, -4, -5, -6)
+NFEAT, NBIN, CELL, WIN = 31, 18, 8, 10
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libhog.so not built (run __graft_entry__.build()): %s" % LIB_PATH)
+_lib = C.CDLL(LIB_PATH)
+
+
+class Params(C.Structure):
+    _fields_ = [("cell", C.c_int32), ("win_cells_w", C.c_int32), ("win_cells_h", C.c_int32),
+                ("scale_num", C.c_int32), ("scale_den", C.c_int32), ("min_size", C.c_int32),
+                ("skip_levels", C.c_int32), ("eps", C.c_float), ("trunc", C.c_float),
+                ("threshold", C.c_float), ("nms_iou", C.c_float), ("max_w", C.c_int32),
+                ("max_h", C.c_int32), ("max_batch", C.c_int32),
+                ("max_dets_per_frame", C.c_int32), ("float_pyramid", C.c_int32)]
+
+
+class Frame(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("w", C.c_int32), ("h", C.c_int32), ("pitch", C.c_int32)]
+
+
+class Det(C.Structure):
+    _fields_ = [("frame", C.c_int32), ("level", C.c_int32), ("filter", C.c_int32),
+                ("u", C.c_int32), ("v", C.c_int32), ("score", C.c_float), ("x", C.c_double),
+                ("y", C.c_double), ("w", C.c_double), ("h", C.c_double)]
+
+
+class StageStat(C.Structure):
+    _fields_ = [("ms", C.c_double), ("launches", C.c_int64), ("units", C.c_int64)]
+
+
+STAGES = ("pyramid", "hist", "feat", "corr", "nms")
+
+
+class Level(C.Structure):
+    _fields_ = [("w", C.c_int32), ("h", C.c_int32), ("cx", C.c_int32), ("cy", C.c_int32),
+                ("offset", C.c_int64)]
+
+
+DET_DTYPE = np.dtype([("frame", "<i4"), ("level", "<i4"), ("filter", "<i4"), ("u", "<i4"),
+                      ("v", "<i4"), ("score", "<f4"), ("x", "<f8"), ("y", "<f8"), ("w", "<f8"),
+                      ("h", "<f8")], align=True)
+assert DET_DTYPE.itemsize == C.sizeof(Det) == 56
+
+_P, _vp, _i32 = C.POINTER, C.c_void_p, C.c_int32
+_SIGS = {
+    "hog_default_params": (None, [_P(Params)]),
+    "hog_level_geometry": (C.c_int, [_P(Params), _i32, _i32, _P(Level), _i32, _P(_i32)]),
+    "hog_create": (C.c_int, [_P(Params), _vp, _i32, _P(_vp)]),
+    "hog_set_filters": (C.c_int, [_vp, _vp, _i32]),
+    "hog_destroy": (None, [_vp]),
+    "hog_last_error": (C.c_char_p, [_vp]),
+    "hog_pyramid": (C.c_int, [_vp, _P(Frame), _vp, C.c_size_t, _P(Level), _i32, _P(_i32), _vp]),
+    "hog_features": (C.c_int, [_vp, _P(Frame), _vp, C.c_size_t, _P(Level), _i32, _P(_i32), _vp]),
+    "hog_scores": (C.c_int, [_vp, _P(Frame), _vp, C.c_size_t, _P(Level), _i32, _P(_i32), _vp]),
+    "hog_detect": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
+    "hog_detect_host": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
+    "hog_set_profiling": (C.c_int, [_vp, _i32]),
+    "hog_stage_stats": (C.c_int, [_vp, _vp, _i32, _i32]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+#: every symbol the header declares (the CPU tests check the library exports them)
+EXPORTED = tuple(_SIGS)
+
+
+class HogError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libhog error %d: %s" % (code, msg))
+        self.code = code
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _lib.hog_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def level_geometry(w: int, h: int, params: Params | None = None):
+    p = params or default_params()
+    lv = (Level * 64)()
+    n = _i32(0)
+    rc = _lib.hog_level_geometry(C.byref(p), int(w), int(h), lv, 64, C.byref(n))
+    if rc:
+        raise HogError(rc, "level geometry")
+    return [(lv[i].w, lv[i].h, lv[i].cx, lv[i].cy, lv[i].offset) for i in range(n.value)]
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _frame_of(t) -> Frame:
+    """A device uint8 tensor [h, w] (row stride in bytes = pitch)."""
+    assert t.dtype.itemsize == 1 and t.dim() == 2 and t.is_cuda
+    return Frame(C.c_void_p(t.data_ptr()), int(t.shape[1]), int(t.shape[0]), int(t.stride(0)))
+
+
+class Detector:
+    """One libhog context (filters on the device, arenas allocated once)."""
+
+    def __init__(self, filters, **params):
+        self.params = default_params(**params)
+        w = np.ascontiguousarray(np.asarray(filters, dtype=np.float32))
+        assert w.ndim == 4 and w.shape[1:] == (10, 10, NFEAT), w.shape
+        self.n_filters = w.shape[0]
+        h = _vp()
+        rc = _lib.hog_create(C.byref(self.params), w.ctypes.data_as(_vp), self.n_filters,
+                             C.byref(h))
+        if rc:
+            raise HogError(rc, _lib.hog_last_error(None).decode())
+        self._h = h
+
+    # --------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hog_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc and rc not in allow:
+            raise HogError(rc, _lib.hog_last_error(self._h).decode())
+        return rc
+
+    def set_profiling(self, on=True):
+        self._check(_lib.hog_set_profiling(self._h, int(bool(on))))
+
+    def stage_stats(self, reset=False):
+        """{stage: (gpu_ms, launches, units)} accumulated since the last reset."""
+        st = (StageStat * len(STAGES))()
+        self._check(_lib.hog_stage_stats(self._h, st, len(STAGES), int(bool(reset))))
+        return {n: (st[i].ms, st[i].launches, st[i].units) for i, n in enumerate(STAGES)}
+
+    def set_filters(self, filters):
+        w = np.ascontiguousarray(np.asarray(filters, dtype=np.float32))
+        self._check(_lib.hog_set_filters(self._h, w.ctypes.data_as(_vp), w.shape[0]))
+        self.n_filters = w.shape[0]
+
+    # --------------------------------------------------------------
+    def pyramid(self, frame, stream=None):
+        """List of device uint8 tensors, one per level."""
+        import torch
+        fr = _frame_of(frame)
+        geo = level_geometry(fr.w, fr.h, self.params)
+        total = sum(g[0] * g[1] for g in geo)
+        out = torch.empty(max(total, 1), dtype=torch.uint8, device=frame.device)
+        lv = (Level * 64)()
+        n = _i32(0)
+        self._check(_lib.hog_pyramid(self._h, C.byref(fr), C.c_void_p(out.data_ptr()), out.numel(),
+                                     lv, 64, C.byref(n), _stream_ptr(stream)))
+        return [out[lv[i].offset:lv[i].offset + lv[i].w * lv[i].h].view(lv[i].h, lv[i].w)
+                for i in range(n.value)]
+
+    def features(self, frame, stream=None):
+        """List of device float32 tensors [cy, cx, 31], one per level."""
+        import torch
+        fr = _frame_of(frame)
+        geo = level_geometry(fr.w, fr.h, self.params)
+        total = sum(g[2] * g[3] * NFEAT for g in geo)
+        out = torch.empty(max(total, 1), dtype=torch.float32, device=frame.device)
+        lv = (Level * 64)()
+        n = _i32(0)
+        self._check(_lib.hog_features(self._h, C.byref(fr), C.c_void_p(out.data_ptr()),
+                                      out.numel(), lv, 64, C.byref(n), _stream_ptr(stream)))
+        res = []
+        for i in range(n.value):
+            k = lv[i].cx * lv[i].cy * NFEAT
+            res.append(out[lv[i].offset:lv[i].offset + k].view(lv[i].cy, lv[i].cx, NFEAT))
+        return res
+
+    def scores(self, frame, stream=None):
+        """List of device float32 tensors [F, cy-9, cx-9], one per level."""
+        import torch
+        fr = _frame_of(frame)
+        geo = level_geometry(fr.w, fr.h, self.params)
+        F = self.n_filters
+        dims = [(max(g[3] - 9, 0), max(g[2] - 9, 0)) for g in geo]
+        total = sum(F * a * b for a, b in dims)
+        out = torch.empty(max(total, 1), dtype=torch.float32, device=frame.device)
+        lv = (Level * 64)()
+        n = _i32(0)
+        self._check(_lib.hog_scores(self._h, C.byref(fr), C.c_void_p(out.data_ptr()), out.numel(),
+                                    lv, 64, C.byref(n), _stream_ptr(stream)))
+        res = []
+        for i in range(n.value):
+            nu, nv = dims[i]
+            res.append(out[lv[i].offset:lv[i].offset + F * nu * nv].view(F, nu, nv))
+        return res
+
+    def detect(self, frames, det_cap=None, stream=None, allow_capacity=False):
+        """Detect on a list of device uint8 frames.  Returns (dets, counts):
+        dets a numpy structured array (DET_DTYPE), counts int32 per frame."""
+        n = len(frames)
+        arr = (Frame * max(n, 1))(*[_frame_of(f) for f in frames])
+        if det_cap is None:
+            det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
+        dets = np.zeros(max(det_cap, 1), DET_DTYPE)
+        counts = np.zeros(max(n, 1), np.int32)
+        rc = _lib.hog_detect(self._h, arr, n, dets.ctypes.data_as(_vp), det_cap,
+                             counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
+        self._check(rc, allow=(HOG_ECAPACITY,) if allow_capacity else ())
+        total = int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum())
+        return dets[:min(total, det_cap)].copy(), counts[:n].copy()
+
+    def detect_host(self, frames, det_cap=None, stream=None, allow_capacity=False):
+        """Same as detect, from host numpy uint8 frames [h, w] (copied in the call)."""
+        n = len(frames)
+        frames = [np.ascontiguousarray(f, dtype=np.uint8) for f in frames]
+        arr = (Frame * max(n, 1))(*[Frame(f.ctypes.data_as(_vp), f.shape[1], f.shape[0],
+                                          f.strides[0]) for f in frames])
+        if det_cap is None:
+            det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
+        dets = np.zeros(max(det_cap, 1), DET_DTYPE)
+        counts = np.zeros(max(n, 1), np.int32)
+        rc = _lib.hog_detect_host(self._h, arr, n, dets.ctypes.data_as(_vp), det_cap,
+                                  counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
+        self._check(rc, allow=(HOG_ECAPACITY,) if allow_capacity else ())
+        total = int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum())
+        return dets[:min(total, det_cap)].copy(), counts[:n].copy()

@@ -1,0 +1,83 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every symbol
+include/hog.h declares, and its host-only logic (parameter validation, level
+geometry) behaves; no GPU compute is called here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hog():
+    from paper_2006_00816_gb300 import _build
+    _build.build()
+    from paper_2006_00816_gb300 import hog as H
+    return H
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "hog.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hog_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(hog):
+    names = _declared()
+    assert "hog_create" in names and "hog_detect" in names and "hog_destroy" in names
+    lib = C.CDLL(hog.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(hog.EXPORTED)
+
+
+def test_default_params(hog):
+    p = hog.default_params()
+    assert (p.cell, p.win_cells_w, p.win_cells_h, p.scale_num, p.scale_den) == (8, 10, 10, 5, 6)
+    assert p.min_size == 80 and p.threshold == 0.0 and abs(p.nms_iou - 0.5) < 1e-7
+    assert abs(p.eps - 1e-4) < 1e-9 and abs(p.trunc - 0.2) < 1e-7
+
+
+def test_level_geometry_matches_oracle(hog, oracle):
+    for w, h in [(320, 240), (640, 480), (1280, 720), (1280, 1024), (128, 128), (80, 80),
+                 (81, 97), (79, 300)]:
+        g = hog.level_geometry(w, h)
+        assert [(a, b) for a, b, *_ in g] == oracle.level_sizes(w, h)
+        off = 0
+        for lw, lh, cx, cy, o in g:
+            assert (cx, cy) == (lw // 8, lh // 8)
+            assert o == off
+            off += cx * cy * 31
+
+
+@pytest.mark.parametrize("field,value", [("cell", 4), ("win_cells_w", 8), ("scale_num", 3),
+                                         ("min_size", 40), ("nms_iou", 0.3), ("max_batch", 0),
+                                         ("skip_levels", -1), ("eps", 0.0),
+                                         ("max_dets_per_frame", 0)])
+def test_create_rejects_bad_params(hog, field, value):
+    import numpy as np
+    p = hog.default_params(**{field: value})
+    w = np.zeros((1, 10, 10, 31), np.float32)
+    h = C.c_void_p()
+    rc = hog._lib.hog_create(C.byref(p), w.ctypes.data_as(C.c_void_p), 1, C.byref(h))
+    assert rc == hog.HOG_EINVAL
+    assert not h.value
+    assert len(hog._lib.hog_last_error(None)) > 0
+
+
+def test_create_rejects_bad_filter_count(hog):
+    import numpy as np
+    p = hog.default_params()
+    w = np.zeros((9, 10, 10, 31), np.float32)
+    h = C.c_void_p()
+    for n in (0, 9):
+        rc = hog._lib.hog_create(C.byref(p), w.ctypes.data_as(C.c_void_p), n, C.byref(h))
+        assert rc == hog.HOG_EINVAL
+
+
+def test_null_safety(hog):
+    hog._lib.hog_destroy(None)
+    assert hog._lib.hog_detect(None, None, 0, None, 0, None, None) == hog.HOG_EINVAL
+    assert hog._lib.hog_level_geometry(None, 10, 10, None, 0, None) == hog.HOG_EINVAL
