@@ -167,6 +167,24 @@ int hog_detect(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det 
 int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
                     int32_t det_cap, int32_t *counts, void *stream);
 
+/* Features of one frame, exactly as hog_features computes them, for callers
+ * that cannot allocate device memory: a frame loop with a hard deadline
+ * (cudaMalloc can block and synchronise the device) or a host application
+ * whose own pool owns all device memory.  The paper has no counterpart; it
+ * allocates its arrays once per image sequence.  No context is needed and
+ * nothing is allocated: the scratch (pyramid, histograms, internal features,
+ * launch tables) is a 4 MiB file-scope device array that every GPU loading
+ * libhog keeps until exit.  Only *p's min_size, eps and trunc are used (the
+ * fixed fields are still checked).  frame (device) must be at most 640 x 480,
+ * else HOG_EINVAL with a message in err.  feat_out (device), levels (host)
+ * and the capacities behave as in hog_features.  err (host, may be NULL)
+ * receives a message on failure.  All calls on a device share the array:
+ * calls whose GPU work overlaps race.  The first call on each device looks up
+ * the array's address; make it before any stream capture. */
+int hog_features_static(const hog_params *p, const hog_frame *frame, float *feat_out,
+                        size_t cap_floats, hog_level *levels, int32_t cap_levels,
+                        int32_t *n_levels, char *err, size_t err_cap, void *stream);
+
 /* ---- stage timing (tracing; no counterpart in the paper, which reads its
  * kernel times from a profiler, Section 5.1) ------------------------------ */
 #define HOG_NSTAGES 5   /* 0 pyramid, 1 gradient+histogram, 2 normalisation+

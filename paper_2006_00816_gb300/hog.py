@@ -73,6 +73,8 @@ _SIGS = {
     "hog_scores": (C.c_int, [_vp, _P(Frame), _vp, C.c_size_t, _P(Level), _i32, _P(_i32), _vp]),
     "hog_detect": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
     "hog_detect_host": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
+    "hog_features_static": (C.c_int, [_P(Params), _P(Frame), _vp, C.c_size_t, _P(Level), _i32,
+                                      _P(_i32), C.c_char_p, C.c_size_t, _vp]),
     "hog_set_profiling": (C.c_int, [_vp, _i32]),
     "hog_stage_stats": (C.c_int, [_vp, _vp, _i32, _i32]),
 }
@@ -109,6 +111,29 @@ def level_geometry(w: int, h: int, params: Params | None = None):
     if rc:
         raise HogError(rc, "level geometry")
     return [(lv[i].w, lv[i].h, lv[i].cx, lv[i].cy, lv[i].offset) for i in range(n.value)]
+
+
+def features_static(frame, params: Params | None = None, stream=None):
+    """hog_features_static: features of one device frame (<= 640x480) with no
+    device allocation by the library; the output tensor is allocated here by
+    the caller side (torch).  Returns (list of [cy, cx, 31] tensors, rc, msg)."""
+    import torch
+    p = params or default_params()
+    fr = _frame_of(frame)
+    geo = level_geometry(fr.w, fr.h, p) if fr.w <= 16384 and fr.h <= 16384 else []
+    total = sum(g[2] * g[3] * NFEAT for g in geo)
+    out = torch.empty(max(total, 1), dtype=torch.float32, device=frame.device)
+    lv = (Level * 64)()
+    n = _i32(0)
+    err = C.create_string_buffer(256)
+    rc = _lib.hog_features_static(C.byref(p), C.byref(fr), C.c_void_p(out.data_ptr()),
+                                  out.numel(), lv, 64, C.byref(n), err, 256, _stream_ptr(stream))
+    res = []
+    if rc == 0:
+        for i in range(n.value):
+            k = lv[i].cx * lv[i].cy * NFEAT
+            res.append(out[lv[i].offset:lv[i].offset + k].view(lv[i].cy, lv[i].cx, NFEAT))
+    return res, rc, err.value.decode()
 
 
 def _stream_ptr(stream=None):
