@@ -91,6 +91,29 @@ int compute_geometry(const hog_params &p, int W, int H, Geometry &g) {
 
 }  // namespace
 
+namespace {
+struct PlanLayout {
+    size_t descs = 0, frames = 0, hist = 0, feat = 0, corr = 0, total = 0;
+    std::vector<size_t> pyr;
+    std::vector<int> npyr;
+};
+
+// Sizes and per-stage work of a laid-out plan (what a launch needs).
+struct PlanInfo {
+    PlanLayout L;
+    int nhist = 0, nfeat = 0, ncorr = 0, nframes = 0, max_npos = 0;
+    int64_t px = 0, cells = 0, wins = 0;
+};
+
+struct CachedPlan {
+    std::vector<uint64_t> sig;
+    PlanInfo info;
+    char *d = nullptr;
+    size_t cap = 0;
+    uint64_t used = 0;
+};
+}  // namespace
+
 struct hog_ctx {
     hog_params p;
     int nf = 0, nfk = 0;
@@ -106,8 +129,10 @@ struct hog_ctx {
     int *d_flags = nullptr;
     char *h_plan = nullptr, *d_plan = nullptr;
     size_t plan_cap = 0;
-    hog_det *h_dets = nullptr;      // pinned
-    int32_t *h_counts = nullptr;    // pinned
+    hog_det *h_dets = nullptr;      // pinned, mapped
+    int32_t *h_counts = nullptr;    // pinned, mapped
+    hog_det *m_dets = nullptr;      // device view of h_dets
+    int32_t *m_counts = nullptr;    // device view of h_counts
     int *h_flags = nullptr;         // pinned
     uint8_t *h_stage = nullptr, *d_stage = nullptr;
     size_t stage_cap = 0;
@@ -117,6 +142,8 @@ struct hog_ctx {
     cudaEvent_t prof_ev[2 * HOG_NSTAGES] = {};
     hog_stage_stat stats[HOG_NSTAGES] = {};
     std::vector<Geometry *> geoms;
+    std::vector<CachedPlan> plans;
+    uint64_t plan_clock = 0;
     std::string err;
 };
 
@@ -195,6 +222,7 @@ void free_ctx(hog_ctx *ctx) {
     if (ctx->plan_done) cudaEventDestroy(ctx->plan_done);
     for (cudaEvent_t e : ctx->prof_ev)
         if (e) cudaEventDestroy(e);
+    for (auto &cp : ctx->plans) F(cp.d);
     for (Geometry *g : ctx->geoms) {
         F(g->d_nbr);
         F(g->d_cnt);
@@ -272,11 +300,7 @@ struct PlanBuilder {
     std::vector<Job> hist, feat, corr;
 };
 
-struct PlanLayout {
-    size_t descs = 0, frames = 0, hist = 0, feat = 0, corr = 0, total = 0;
-    std::vector<size_t> pyr;
-    std::vector<int> npyr;
-};
+
 
 // Per-frame options for plan building.
 struct FrameOpts {
@@ -331,8 +355,14 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
             for (int k = 0; k < nfj; k++) pb.feat.push_back({di, k});
         }
         if (o.corr && d.nu > 0 && d.nv > 0 && (d.scan || o.scores_user)) {
-            const int nc = ((d.nu + CORR_TU - 1) / CORR_TU) * ((d.nv + CORR_TV - 1) / CORR_TV);
-            for (int k = 0; k < nc; k++) pb.corr.push_back({di, k});
+            // warp-tile shape that pads this level's window grid least
+            int best = 0, best_slots = 0, best_n = 0;
+            for (int sh = 0; sh < CORR_NSHAPE; sh++) {
+                const int n = ((d.nu + corr_tu(sh) - 1) / corr_tu(sh)) *
+                              ((d.nv + corr_tv(sh) - 1) / corr_tv(sh));
+                if (sh == 0 || n * 128 < best_slots) { best = sh; best_slots = n * 128; best_n = n; }
+            }
+            for (int k = 0; k < best_n; k++) pb.corr.push_back({di, (best << 28) | k});
         }
     }
     if (o.nms) {
@@ -357,7 +387,10 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
     }
 }
 
-int layout_plan(const PlanBuilder &pb, PlanLayout &L) {
+
+
+void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
+    PlanLayout &L = info.L;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
     L.descs = take(pb.descs.size() * sizeof(LevelDesc));
@@ -372,7 +405,19 @@ int layout_plan(const PlanBuilder &pb, PlanLayout &L) {
     L.feat = take(pb.feat.size() * sizeof(Job));
     L.corr = take(pb.corr.size() * sizeof(Job));
     L.total = off;
-    return HOG_OK;
+    info.nhist = (int)pb.hist.size();
+    info.nfeat = (int)pb.feat.size();
+    info.ncorr = (int)pb.corr.size();
+    info.nframes = (int)pb.frames.size();
+    info.max_npos = 0;
+    for (const FrameDesc &f : pb.frames) info.max_npos = std::max(info.max_npos, f.npos);
+    info.px = info.cells = info.wins = 0;
+    for (const LevelDesc &ld : pb.descs) {
+        if (ld.level >= 1) info.px += (int64_t)ld.w * ld.h;
+        info.cells += (int64_t)ld.cx * ld.cy;
+        if (ld.nu > 0 && ld.nv > 0 && (ld.scan || ld.scores_user)) info.wins += (int64_t)ld.nu * ld.nv;
+    }
+    info.wins *= nf;
 }
 
 int ensure_plan_capacity(hog_ctx *ctx, size_t bytes) {
@@ -403,10 +448,11 @@ int collect_profile(hog_ctx *ctx) {
     return HOG_OK;
 }
 
-// Copy the plan to the device and launch the stages on `stream`.
-int run_plan(hog_ctx *ctx, const PlanBuilder &pb, cudaStream_t stream) {
-    PlanLayout L;
-    layout_plan(pb, L);
+// Serialise pb into the pinned staging buffer and copy it to d_dst
+// (capacity >= info.L.total) on `stream`.
+int upload_plan(hog_ctx *ctx, const PlanBuilder &pb, const PlanInfo &info, char *d_dst,
+                cudaStream_t stream) {
+    const PlanLayout &L = info.L;
     int rc = ensure_plan_capacity(ctx, L.total);
     if (rc) return rc;
     CUDA_TRY(ctx, cudaEventSynchronize(ctx->plan_done));   // previous plan copy has finished
@@ -418,61 +464,125 @@ int run_plan(hog_ctx *ctx, const PlanBuilder &pb, cudaStream_t stream) {
     std::memcpy(h + L.hist, pb.hist.data(), pb.hist.size() * sizeof(Job));
     std::memcpy(h + L.feat, pb.feat.data(), pb.feat.size() * sizeof(Job));
     std::memcpy(h + L.corr, pb.corr.data(), pb.corr.size() * sizeof(Job));
-    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_plan, h, L.total, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(ctx, cudaMemcpyAsync(d_dst ? d_dst : ctx->d_plan, h, L.total, cudaMemcpyHostToDevice,
+                                  stream));
     CUDA_TRY(ctx, cudaEventRecord(ctx->plan_done, stream));
-    char *d = ctx->d_plan;
+    return HOG_OK;
+}
+
+// Launch every stage of a plan that is resident at d on `stream`.
+int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t stream) {
+    const PlanLayout &L = info.L;
     const LevelDesc *descs = reinterpret_cast<const LevelDesc *>(d + L.descs);
-    rc = collect_profile(ctx);
+    int rc = collect_profile(ctx);
     if (rc) return rc;
     auto mark = [&](int i) -> cudaError_t {
         return ctx->prof ? cudaEventRecord(ctx->prof_ev[i], stream) : cudaSuccess;
     };
-    int64_t px = 0, cells = 0, wins = 0;
-    for (const LevelDesc &ld : pb.descs) {
-        if (ld.level >= 1) px += (int64_t)ld.w * ld.h;
-        cells += (int64_t)ld.cx * ld.cy;
-    }
-    for (const Job &j : pb.corr) (void)j;
-    for (size_t k = 0; k < pb.descs.size(); k++) {
-        const LevelDesc &ld = pb.descs[k];
-        if (ld.nu > 0 && ld.nv > 0 && (ld.scan || ld.scores_user)) wins += (int64_t)ld.nu * ld.nv;
-    }
-    const bool do_corr = !pb.corr.empty();
     CUDA_TRY(ctx, mark(0));
     int npyr = 0;
-    for (size_t s = 1; s < pb.pyr.size(); s++) {
+    for (size_t s = 1; s < L.pyr.size(); s++) {
         CUDA_TRY(ctx, launch_pyramid(descs, reinterpret_cast<const Job *>(d + L.pyr[s]),
                                      L.npyr[s], stream));
         npyr += L.npyr[s] > 0;
     }
     CUDA_TRY(ctx, mark(1));
     CUDA_TRY(ctx, mark(2));
-    CUDA_TRY(ctx, launch_hist(descs, reinterpret_cast<const Job *>(d + L.hist),
-                              (int)pb.hist.size(), stream));
+    CUDA_TRY(ctx, launch_hist(descs, reinterpret_cast<const Job *>(d + L.hist), info.nhist, stream));
     CUDA_TRY(ctx, mark(3));
     CUDA_TRY(ctx, mark(4));
-    CUDA_TRY(ctx, launch_feat(descs, reinterpret_cast<const Job *>(d + L.feat),
-                              (int)pb.feat.size(), ctx->p.eps, ctx->p.trunc, stream));
+    CUDA_TRY(ctx, launch_feat(descs, reinterpret_cast<const Job *>(d + L.feat), info.nfeat,
+                              ctx->p.eps, ctx->p.trunc, stream));
     CUDA_TRY(ctx, mark(5));
     CUDA_TRY(ctx, mark(6));
-    CUDA_TRY(ctx, launch_corr(descs, reinterpret_cast<const Job *>(d + L.corr),
-                              (int)pb.corr.size(), ctx->d_w, ctx->nfk, ctx->nf,
-                              ctx->p.threshold, stream));
+    CUDA_TRY(ctx, launch_corr(descs, reinterpret_cast<const Job *>(d + L.corr), info.ncorr,
+                              ctx->d_w, ctx->nfk, ctx->nf, ctx->p.threshold, stream));
     CUDA_TRY(ctx, mark(7));
     CUDA_TRY(ctx, mark(8));
-    if (!pb.frames.empty())
-        CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames),
-                                 (int)pb.frames.size(), ctx->d_flags, stream));
+    if (info.nframes > 0)
+        CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.nframes,
+                                 info.max_npos, ctx->d_flags, stream));
     CUDA_TRY(ctx, mark(9));
     if (ctx->prof) {
         ctx->prof_pending = true;
         hog_stage_stat *st = ctx->stats;
-        st[0].launches += npyr; st[0].units += px;
-        st[1].launches += !pb.hist.empty(); st[1].units += pb.hist.empty() ? 0 : cells;
-        st[2].launches += !pb.feat.empty(); st[2].units += pb.feat.empty() ? 0 : cells;
-        st[3].launches += do_corr; st[3].units += do_corr ? wins * ctx->nf : 0;
-        st[4].launches += !pb.frames.empty(); st[4].units += (int64_t)pb.frames.size();
+        st[0].launches += npyr; st[0].units += info.px;
+        st[1].launches += info.nhist > 0; st[1].units += info.nhist > 0 ? info.cells : 0;
+        st[2].launches += info.nfeat > 0; st[2].units += info.nfeat > 0 ? info.cells : 0;
+        st[3].launches += info.ncorr > 0; st[3].units += info.ncorr > 0 ? info.wins : 0;
+        st[4].launches += info.nframes > 0; st[4].units += info.nframes;
     }
+    return HOG_OK;
+}
+
+// Build, upload and launch a one-off plan (inspection entry points).
+int run_plan(hog_ctx *ctx, const PlanBuilder &pb, cudaStream_t stream) {
+    PlanInfo info;
+    layout_plan(pb, ctx->nf, info);
+    int rc = upload_plan(ctx, pb, info, nullptr, stream);
+    if (rc) return rc;
+    return launch_plan(ctx, ctx->d_plan, info, stream);
+}
+
+// Device-resident plans of recent detection batches, keyed by the batch's
+// frames (pointer, size, pitch) and frame numbering: a repeated batch (a
+// ring of camera buffers, a benchmark loop) skips plan building and upload.
+int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, cudaStream_t stream,
+                const char **d_out, const PlanInfo **info_out) {
+    std::vector<uint64_t> sig;
+    sig.reserve(2 + 2 * (size_t)nb);
+    sig.push_back((uint64_t)nb);
+    sig.push_back((uint64_t)(uint32_t)frame_base);
+    for (int i = 0; i < nb; i++) {
+        sig.push_back((uint64_t)(uintptr_t)frames[i].data);
+        sig.push_back(((uint64_t)(uint32_t)frames[i].w << 40) ^ ((uint64_t)(uint32_t)frames[i].h << 20) ^
+                      (uint64_t)(uint32_t)frames[i].pitch);
+    }
+    ctx->plan_clock++;
+    for (auto &cp : ctx->plans)
+        if (cp.d && cp.sig == sig) {
+            cp.used = ctx->plan_clock;
+            *d_out = cp.d;
+            *info_out = &cp.info;
+            return HOG_OK;
+        }
+    PlanBuilder pb;
+    for (int i = 0; i < nb; i++) {
+        const hog_frame &f = frames[i];
+        if (f.w < ctx->p.min_size || f.h < ctx->p.min_size) continue;
+        Geometry *g;
+        int rc = get_geometry(ctx, f.w, f.h, stream, &g);
+        if (rc) return rc;
+        FrameOpts o;
+        o.nms = g->npos > 0;
+        add_frame(ctx, pb, *g, f, i, frame_base + i, o);
+    }
+    PlanInfo info;
+    layout_plan(pb, ctx->nf, info);
+    // least recently used entry (or a free one)
+    if (ctx->plans.size() < 8) ctx->plans.emplace_back();
+    CachedPlan *victim = &ctx->plans[0];
+    for (auto &cp : ctx->plans)
+        if (!cp.d || cp.used < victim->used) victim = &cp;
+    if (victim->cap < info.L.total) {
+        if (victim->d) {
+            CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+            cudaFree(victim->d);
+        }
+        victim->d = nullptr;
+        victim->cap = 0;
+        victim->sig.clear();
+        const size_t cap = align_up(info.L.total, 1 << 16);
+        CUDA_TRY(ctx, cudaMalloc(&victim->d, cap));
+        victim->cap = cap;
+    }
+    int rc = upload_plan(ctx, pb, info, victim->d, stream);
+    if (rc) { victim->sig.clear(); return rc; }
+    victim->sig = std::move(sig);
+    victim->info = info;
+    victim->used = ctx->plan_clock;
+    *d_out = victim->d;
+    *info_out = &victim->info;
     return HOG_OK;
 }
 
@@ -491,44 +601,50 @@ int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, 
                   int det_cap, int *written_out, int32_t *counts, cudaStream_t stream) {
     int written = 0;
     bool truncated = false;
+    // A pinned (page-locked, mapped) output buffer is written by the device
+    // directly; any other host buffer is filled from the context's staging.
+    hog_det *dets_dev = nullptr;
+    if (dets && det_cap > 0) {
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, dets) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+            attr.devicePointer)
+            dets_dev = static_cast<hog_det *>(attr.devicePointer);
+        cudaGetLastError();
+    }
     for (int b0 = 0; b0 < n; b0 += ctx->p.max_batch) {
         const int nb = std::min(ctx->p.max_batch, n - b0);
-        PlanBuilder pb;
-        for (int i = 0; i < nb; i++) {
-            const hog_frame &f = frames[b0 + i];
-            if (f.w < ctx->p.min_size || f.h < ctx->p.min_size) continue;
-            Geometry *g;
-            int rc = get_geometry(ctx, f.w, f.h, stream, &g);
-            if (rc) return rc;
-            FrameOpts o;
-            o.nms = g->npos > 0;
-            add_frame(ctx, pb, *g, f, i, frame_base + b0 + i, o);
-        }
-        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_counts, 0, sizeof(int32_t) * nb, stream));
-        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), stream));
-        int rc = run_plan(ctx, pb, stream);
+        const char *dplan = nullptr;
+        const PlanInfo *info = nullptr;
+        int rc = cached_plan(ctx, frames + b0, nb, frame_base + b0, stream, &dplan, &info);
         if (rc) return rc;
-        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, sizeof(int32_t) * nb,
-                                      cudaMemcpyDeviceToHost, stream));
-        CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-        // kept boxes: one copy per frame that has any, into pinned staging
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_counts, 0, sizeof(int32_t) * nb, stream));
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, 2 * sizeof(int), stream));
+        rc = launch_plan(ctx, dplan, *info, stream);
+        if (rc) return rc;
+        // kept boxes of all frames, packed frame after frame into mapped
+        // pinned host memory by one kernel, then one synchronisation
         const size_t D = (size_t)ctx->p.max_dets_per_frame;
-        for (int i = 0; i < nb; i++) {
-            const int k = std::min(ctx->h_counts[i], ctx->p.max_dets_per_frame);
-            if (k > 0)
-                CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_dets + i * D, ctx->d_dets + i * D,
-                                              sizeof(hog_det) * k, cudaMemcpyDeviceToHost, stream));
-        }
+        const int room = dets ? std::max(det_cap - written, 0) : 0;
+        if (dets_dev)
+            CUDA_TRY(ctx, launch_pack(ctx->d_dets, ctx->p.max_dets_per_frame, ctx->d_counts, nb,
+                                      dets_dev + written, room, ctx->m_counts, stream));
+        else
+            CUDA_TRY(ctx, launch_pack(ctx->d_dets, ctx->p.max_dets_per_frame, ctx->d_counts, nb,
+                                      ctx->m_dets, (int)(D * ctx->p.max_batch), ctx->m_counts,
+                                      stream));
         CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        size_t off = 0;
         for (int i = 0; i < nb; i++) {
             const int c = ctx->h_counts[i];
             if (counts) counts[b0 + i] = c;
             const int k = std::min(c, ctx->p.max_dets_per_frame);
             if (c > k) truncated = true;
-            for (int j = 0; j < k; j++) {
-                if (written < det_cap && dets) dets[written++] = ctx->h_dets[i * D + j];
-                else truncated = true;
-            }
+            const int take = std::min(k, std::max(det_cap - written, 0));
+            if (take > 0 && !dets_dev)
+                std::memcpy(dets + written, ctx->h_dets + off, sizeof(hog_det) * take);
+            if (take < k) truncated = true;
+            written += take;
+            off += k;
         }
     }
     if (written_out) *written_out = written;
@@ -607,8 +723,12 @@ int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters
     M((void **)&ctx->d_dets, B * D * sizeof(hog_det));
     M((void **)&ctx->d_counts, B * sizeof(int32_t));
     M((void **)&ctx->d_flags, sizeof(int) * 4);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_dets, B * D * sizeof(hog_det));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_counts, B * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaHostAlloc((void **)&ctx->h_dets, B * D * sizeof(hog_det), cudaHostAllocMapped);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc((void **)&ctx->h_counts, B * sizeof(int32_t), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&ctx->m_dets, ctx->h_dets, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&ctx->m_counts, ctx->h_counts, 0);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_flags, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->plan_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {

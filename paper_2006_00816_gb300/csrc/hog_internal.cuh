@@ -21,9 +21,15 @@ constexpr int MAXN = 192;           // suppression neighbours per window positio
 
 // Tile shapes of the plain kernels.
 constexpr int PYR_TX = 128, PYR_TY = 8;          // output pixels per CTA (256 threads)
-constexpr int HIST_TX = 32, HIST_TY = 4;         // cells per CTA (128 threads)
+constexpr int HIST_BX = 16, HIST_BY = 16;        // 8x8-pixel blocks per CTA (256 threads)
+constexpr int HIST_TX = HIST_BX - 1, HIST_TY = HIST_BY - 1;   // 15 x 15 cells per CTA
 constexpr int FEAT_TX = 32, FEAT_TY = 8;         // cells per CTA (256 threads)
-constexpr int CORR_TU = 16, CORR_TV = 32;        // windows per CTA (128 threads)
+// Correlation warp tiles (windows): shape id 0: 8x16, 1: 4x32, 2: 16x8; the
+// shape is stored in bits 28..29 of the job's tile field.
+constexpr int CORR_NSHAPE = 3;
+__host__ __device__ constexpr int corr_tu(int s) { return s == 0 ? 8 : (s == 1 ? 4 : 16); }
+__host__ __device__ constexpr int corr_tv(int s) { return s == 0 ? 16 : (s == 1 ? 32 : 8); }
+constexpr int CORR_WARPS = 4;                    // warps (independent tiles) per CTA
 
 // A key ranks suppression candidates: smaller key = higher rank.  High word
 // = score mapped to a descending unsigned order, low word = (level, filter,
@@ -118,6 +124,28 @@ struct GeomDesc {
     uint32_t pair_mask[MAX_LEVELS];   // bit m set: levels (l, m) can exceed the IoU
 };
 
+// ---- cp.async helpers (16-byte global -> shared copies, sm_80+) -----------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+// Copies 16 bytes when valid, else writes 16 zero bytes (gmem is not read).
+__device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // ---- launchers (each enqueues on `stream`; return cudaGetLastError()) ----
 cudaError_t launch_pyramid(const LevelDesc *descs, const Job *jobs, int njobs,
                            cudaStream_t stream);
@@ -130,6 +158,16 @@ cudaError_t launch_corr(const LevelDesc *descs, const Job *jobs, int njobs,
                         cudaStream_t stream);
 cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, uint8_t *cnt, int *overflow,
                                 cudaStream_t stream);
-cudaError_t launch_nms(const FrameDesc *frames, int nframes, int *flags, cudaStream_t stream);
+// Gather the kept boxes of nframes frames (slot i holds counts[i] boxes at
+// dets + i*per_frame, at most per_frame) into out[0..out_cap) frame after
+// frame, and copy the exact counts to counts_out; out and counts_out may be
+// mapped host memory.
+cudaError_t launch_pack(const hog_det *dets, int per_frame, const int32_t *counts, int nframes,
+                        hog_det *out, int out_cap, int32_t *counts_out, cudaStream_t stream);
+
+// max_npos: largest npos of the frames (selects shared- or global-memory states).
+// flags[0] |= 1 on capacity overflow; flags[1] = max rounds taken by a frame.
+cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *flags,
+                       cudaStream_t stream);
 
 }  // namespace hogk

@@ -11,51 +11,68 @@
 // best filter only (equal scores: the lowest filter index).
 //
 // GB300 design: FP32 FMA on the CUDA cores, bound by the FMA pipe.
-//  - CTA = 128 threads, tile = 16 x 32 windows; each warp owns 8 x 16, each
-//    thread 4 consecutive windows of one row for all filters, so a thread
-//    keeps 4 x NF accumulators and reuses every staged feature for up to 4
-//    windows x NF filters.
-//  - Features come in 8-channel chunks (internal layout [4][cy][cx][8]):
-//    the CTA stages the 25 x 41-cell region of a chunk in shared memory
-//    with a 16-byte row pad (row stride 83 float4), which makes the
-//    per-lane float4 loads of a quarter-warp (8 consecutive rows) hit 8
-//    different bank groups.  The filter chunk is staged beside it and read
-//    with uniform (broadcast) float4 loads.
-//  - For a filter row a and 4 channels, a thread loads the 13 float4 of its
-//    feature row once and slides over the 10 filter columns in registers.
+//  - Each warp owns one tile of 128 windows, shaped 8x16, 4x32 or 16x8 per
+//    level (the host picks the shape that pads the level's window grid
+//    least); a lane owns 4 consecutive windows of one row for all filters,
+//    so it keeps 4 x NF accumulators and uses every feature it loads for 4
+//    windows x NF filters.  The four warps of a CTA are independent (no
+//    block barrier).
+//  - Features stream in half-chunks of 4 channels (one float4 per cell of
+//    the internal layout [4][cy][cx][8]): the warp copies the
+//    (TU+9) x (TV+9)-cell region of the next half-chunk into shared memory
+//    with cp.async while it computes on the current one (double buffer).
+//    The region's row stride TV+9 is odd, so the float4 loads of a
+//    quarter-warp (consecutive rows, or rows x column groups) fall on
+//    distinct bank groups.
+//  - For a filter row a, a lane loads the 13 float4 of its feature row once
+//    and slides over the 10 filter columns in registers.  Filter weights are
+//    read with warp-uniform loads through L1 (62 KB for five filters).
 #include "hog_internal.cuh"
 
 namespace hogk {
 
 namespace {
-constexpr int NT = 128;
-constexpr int RU = CORR_TU + WIN - 1;        // 25 staged rows
-constexpr int RV = CORR_TV + WIN - 1;        // 41 staged columns
-constexpr int ROW4 = RV * 2 + 1;             // 83 float4 per staged row (incl. pad)
-constexpr int WPT = 4;                       // windows per thread
-
-template <int NF>
-constexpr size_t corr_smem() {
-    return sizeof(float4) * ((size_t)RU * ROW4 + (size_t)NF * WIN * WIN * 2);
-}
+constexpr int NT = 32 * CORR_WARPS;
+constexpr int WPT = 4;                  // windows per lane
+constexpr int BUF4 = 544;               // float4 per region buffer (max 13 x 41 = 533)
+constexpr size_t SMEM = sizeof(float4) * BUF4 * 2 * CORR_WARPS;   // 69,632 bytes
 }  // namespace
 
 template <int NF>
 __global__ void __launch_bounds__(NT, 3) corr_kernel(const LevelDesc *__restrict__ descs,
-                                                     const Job *__restrict__ jobs,
+                                                     const Job *__restrict__ jobs, int njobs,
                                                      const float *__restrict__ wchunks,
                                                      int nf_real, float threshold) {
     extern __shared__ float4 sm4[];
-    float4 *fS = sm4;                     // [RU][ROW4]
-    float4 *wS = sm4 + RU * ROW4;         // [NF][10][10][2]
-
-    const Job jb = jobs[blockIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int jid = blockIdx.x * CORR_WARPS + w;
+    if (jid >= njobs) return;
+    float4 *buf0 = sm4 + (size_t)w * 2 * BUF4;
+    const Job jb = jobs[jid];
     const LevelDesc &d = descs[jb.desc];
-    const int ntv = (d.nv + CORR_TV - 1) / CORR_TV;
-    const int u0 = (jb.tile / ntv) * CORR_TU, v0 = (jb.tile % ntv) * CORR_TV;
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int lr = (w >> 1) * 8 + (lane & 7);           // window row in tile
-    const int lc = (w & 1) * 16 + (lane >> 3) * WPT;     // first window column in tile
+    const int shape = (jb.tile >> 28) & 3, tile = jb.tile & 0x0fffffff;
+    const int TU = corr_tu(shape), TV = corr_tv(shape);
+    const int RU = TU + WIN - 1, RV = TV + WIN - 1;
+    const int ntv = (d.nv + TV - 1) / TV;
+    const int u0 = (tile / ntv) * TU, v0 = (tile % ntv) * TV;
+    const int lr = lane % TU, lc = (lane / TU) * WPT;    // window row / first column in tile
+
+    const float4 *feat4 = reinterpret_cast<const float4 *>(d.feat);
+    const size_t plane4 = (size_t)d.cy * d.cx * 2;       // float4 per chunk plane
+    const float4 *w4 = reinterpret_cast<const float4 *>(wchunks);
+
+    // copy half-chunk h (chunk h/2, channels 4*(h&1)..+3) of the tile region
+    auto stage = [&](int h, float4 *dst) {
+        const float4 *src = feat4 + (size_t)(h >> 1) * plane4 + (h & 1);
+        for (int k = lane; k < RU * RV; k += 32) {
+            const int rr = k / RV, cc = k - rr * RV;
+            const int i = u0 + rr, j = v0 + cc;
+            const bool ok = i < d.cy && j < d.cx;
+            cp_async16_zfill(dst + k, ok ? (const void *)(src + ((size_t)i * d.cx + j) * 2)
+                                         : (const void *)src, ok);
+        }
+        cp_async_commit();
+    };
 
     float acc[WPT][NF];
 #pragma unroll
@@ -63,52 +80,46 @@ __global__ void __launch_bounds__(NT, 3) corr_kernel(const LevelDesc *__restrict
 #pragma unroll
         for (int f = 0; f < NF; f++) acc[j][f] = 0.0f;
 
-    const size_t plane = (size_t)d.cy * d.cx * CHUNK;
-    for (int ch = 0; ch < NCHUNK; ch++) {
-        __syncthreads();
-        const float4 *src = reinterpret_cast<const float4 *>(d.feat + ch * plane);
-        for (int k = t; k < RU * RV * 2; k += NT) {
-            const int rr = k / (RV * 2);
-            const int rem = k - rr * RV * 2;
-            const int cc = rem >> 1, half = rem & 1;
-            const int i = u0 + rr, j = v0 + cc;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < d.cy && j < d.cx) v = __ldg(src + ((size_t)i * d.cx + j) * 2 + half);
-            fS[rr * ROW4 + cc * 2 + half] = v;
+    stage(0, buf0);
+#pragma unroll 1
+    for (int h = 0; h < 2 * NCHUNK; h++) {
+        float4 *cur = buf0 + (h & 1) * BUF4;
+        if (h + 1 < 2 * NCHUNK) {
+            stage(h + 1, buf0 + ((h + 1) & 1) * BUF4);
+            cp_async_wait_group<1>();
+        } else {
+            cp_async_wait_group<0>();
         }
-        const float4 *wsrc = reinterpret_cast<const float4 *>(wchunks) + (size_t)ch * NF * 200;
-        for (int k = t; k < NF * 200; k += NT) wS[k] = __ldg(wsrc + k);
-        __syncthreads();
-
+        __syncwarp();
+        const int ch = h >> 1, c4 = h & 1;
+        const float4 *wch = w4 + (size_t)ch * NF * 200 + c4;
 #pragma unroll 1
         for (int a = 0; a < WIN; a++) {
-            const float4 *frow = fS + (lr + a) * ROW4 + lc * 2;
-#pragma unroll 1
-            for (int c4 = 0; c4 < 2; c4++) {
-                float4 fv[WPT + WIN - 1];
+            const float4 *frow = cur + (lr + a) * RV + lc;
+            float4 fv[WPT + WIN - 1];
 #pragma unroll
-                for (int j = 0; j < WPT + WIN - 1; j++) fv[j] = frow[j * 2 + c4];
+            for (int j = 0; j < WPT + WIN - 1; j++) fv[j] = frow[j];
 #pragma unroll
-                for (int b = 0; b < WIN; b++) {
-                    float4 wv[NF];
+            for (int b = 0; b < WIN; b++) {
+                float4 wv[NF];
 #pragma unroll
-                    for (int f = 0; f < NF; f++) wv[f] = wS[((f * WIN + a) * WIN + b) * 2 + c4];
+                for (int f = 0; f < NF; f++) wv[f] = __ldg(wch + ((f * WIN + a) * WIN + b) * 2);
 #pragma unroll
-                    for (int j = 0; j < WPT; j++) {
-                        const float4 x = fv[j + b];
+                for (int j = 0; j < WPT; j++) {
+                    const float4 x = fv[j + b];
 #pragma unroll
-                        for (int f = 0; f < NF; f++) {
-                            float s = acc[j][f];
-                            s = fmaf(wv[f].x, x.x, s);
-                            s = fmaf(wv[f].y, x.y, s);
-                            s = fmaf(wv[f].z, x.z, s);
-                            s = fmaf(wv[f].w, x.w, s);
-                            acc[j][f] = s;
-                        }
+                    for (int f = 0; f < NF; f++) {
+                        float s = acc[j][f];
+                        s = fmaf(wv[f].x, x.x, s);
+                        s = fmaf(wv[f].y, x.y, s);
+                        s = fmaf(wv[f].z, x.z, s);
+                        s = fmaf(wv[f].w, x.w, s);
+                        acc[j][f] = s;
                     }
                 }
             }
         }
+        __syncwarp();   // every lane is done with `cur` before it is refilled
     }
 
     const int u = u0 + lr;
@@ -142,13 +153,13 @@ static cudaError_t launch_corr_t(const LevelDesc *descs, const Job *jobs, int nj
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(corr_kernel<NF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)corr_smem<NF>());
+                                             (int)SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     if (njobs <= 0) return cudaSuccess;
-    corr_kernel<NF><<<njobs, NT, corr_smem<NF>(), stream>>>(descs, jobs, wchunks, nf_real,
-                                                            threshold);
+    const int grid = (njobs + CORR_WARPS - 1) / CORR_WARPS;
+    corr_kernel<NF><<<grid, NT, SMEM, stream>>>(descs, jobs, njobs, wchunks, nf_real, threshold);
     return cudaGetLastError();
 }
 

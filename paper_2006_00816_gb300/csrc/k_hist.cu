@@ -8,16 +8,17 @@
 // nearest 8x8 cells (cell centres at 8j+4, weight 1 - |offset|/8 per axis).
 //
 // GB300 design.  The paper scatters votes with fixed-point shared-memory
-// atomics.  Here each thread owns one cell and gathers its 16x16-pixel
-// footprint in a fixed order, so the result is deterministic and needs no
-// atomics:
-//   phase 1: the CTA computes (bin, magnitude) for its 264x40-pixel region
-//            (32x4 cells + half-cell borders) into shared memory;
-//   phase 2: each thread walks its footprint as four 8x8 quadrants at once
-//            (four independent read-modify-write chains into private
-//            shared-memory partial histograms), then adds the quadrants.
-// Shared layouts put the 32 lanes of a warp (32 consecutive cells) on 32
-// different banks: pixel column rc is stored at (rc & 7) * 33 + (rc >> 3).
+// atomics.  Here the pixels between four neighbouring cell centres form an
+// 8x8 "block" (block (bi, bj) spans x in [8bj-4, 8bj+4), y in [8bi-4,
+// 8bi+4)); all of a block's pixels vote into the same four cells (bi-1 or
+// bi) x (bj-1 or bj).  One thread owns one block: it computes its 64
+// pixels' gradients, bins and magnitudes straight from the staged bytes and
+// accumulates four private partial histograms (one per corner cell) in
+// shared memory, laid out [corner][bin][thread] so a warp's 32 lanes always
+// hit 32 banks.  A cell's histogram is then the fixed-order sum of the
+// partials of its four blocks: deterministic, no atomics, and no sum longer
+// than 64 terms.  A CTA owns 16x16 blocks and emits the 15x15 cells whose
+// four blocks it holds.
 //
 // Orientation in exact integer arithmetic: fold (dx, dy) into the first
 // quadrant; the sector there is the number of bin boundaries (10, 30, 50 and
@@ -33,20 +34,14 @@ namespace hogk {
 
 namespace {
 
-constexpr int RX = HIST_TX * CELL + CELL;   // 264 region columns
-constexpr int RY = HIST_TY * CELL + CELL;   // 40 region rows
-constexpr int SXW = RX + 4;                 // staged source row (266 used)
-constexpr int SYH = RY + 2;                 // 42 staged source rows
-constexpr int PLANE = 33;                   // (rc & 7) plane stride
-constexpr int MROW = 8 * PLANE;             // 264 entries per region row
-constexpr int NT = HIST_TX * HIST_TY;       // 128 threads = cells per CTA
-
-constexpr size_t SMEM_MAG = sizeof(float) * RY * MROW;             // 42,240
-constexpr size_t SMEM_BIN = sizeof(uint8_t) * RY * MROW;           // 10,560
-constexpr size_t SMEM_SRC = sizeof(uint8_t) * SYH * SXW;           // 11,256
-constexpr size_t SMEM_QH = sizeof(float) * 4 * NBIN * NT;          // 36,864
-constexpr size_t SMEM_U = SMEM_QH > SMEM_SRC ? SMEM_QH : SMEM_SRC; // src and qh alias
-constexpr size_t SMEM_TOTAL = SMEM_MAG + SMEM_BIN + SMEM_U;
+constexpr int NT = HIST_BX * HIST_BY;          // 256 threads, one per block
+constexpr int PX = HIST_BX * CELL + 2;         // 130 staged columns (blocks + 1-px halo)
+constexpr int PY = HIST_BY * CELL + 2;         // 130 staged rows
+constexpr int NCH = 10;                        // 16-byte chunks per staged row (130 + 15 <= 160)
+constexpr int SROWB = NCH * 16;                // 160 bytes per staged row
+constexpr size_t SMEM_SRC = (size_t)PY * SROWB;                     // 20,800
+constexpr size_t SMEM_PART = sizeof(float) * 4 * NBIN * NT;         // 73,728
+constexpr size_t SMEM_TOTAL = SMEM_PART + SMEM_SRC;
 
 __device__ __forceinline__ int orientation_bin_i(int dx, int dy) {
     if (dx == 0) return dy > 0 ? 4 : 13;
@@ -65,84 +60,89 @@ __host__ __device__ constexpr float tent16(int t) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(NT) hist_kernel(const LevelDesc *__restrict__ descs,
-                                                  const Job *__restrict__ jobs) {
+__global__ void __launch_bounds__(NT, 2) hist_kernel(const LevelDesc *__restrict__ descs,
+                                                     const Job *__restrict__ jobs) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float *magS = reinterpret_cast<float *>(smem);
-    uint8_t *binS = smem + SMEM_MAG;
-    unsigned char *uni = smem + SMEM_MAG + SMEM_BIN;
-    uint8_t *srcS = uni;
-    float *qh = reinterpret_cast<float *>(uni);
+    float *part = reinterpret_cast<float *>(smem);             // [4][18][NT]
+    uint8_t *srcS = smem + SMEM_PART;                          // [PY][SROWB]
+    __shared__ int xbase[PY];
 
     const Job jb = jobs[blockIdx.x];
     const LevelDesc &d = descs[jb.desc];
     const int ntx = (d.cx + HIST_TX - 1) / HIST_TX;
     const int j0 = (jb.tile % ntx) * HIST_TX, i0 = (jb.tile / ntx) * HIST_TY;
     const int t = threadIdx.x;
-    const int X0 = CELL * j0 - 4, Y0 = CELL * i0 - 4;   // region origin (pixels)
     const int xmax = min(d.w - 2, CELL * d.cx - 1);
     const int ymax = min(d.h - 2, CELL * d.cy - 1);
 
-    // stage source pixels [Y0-1, Y0+RY] x [X0-1, X0+RX]
-    for (int p = t; p < SYH * (RX + 2); p += NT) {
-        const int sy = p / (RX + 2), sx = p - sy * (RX + 2);
-        const int Y = Y0 - 1 + sy, X = X0 - 1 + sx;
-        uint8_t v = 0;
-        if (X >= 0 && X < d.w && Y >= 0 && Y < d.h) v = __ldg(d.img + (size_t)Y * d.pitch + X);
-        srcS[sy * SXW + sx] = v;
+    // Stage rows Ys .. Ys+PY-1, columns Xs .. Xs+PX-1 (clipped to the image)
+    // with 16-byte cp.async copies of the aligned chunks covering them.  A
+    // 16-byte-aligned chunk holding at least one byte of the frame lies on
+    // that byte's memory page, so the copies stay in mapped memory even
+    // where they reach past the clipped range; those bytes are never read.
+    // xbase[r] = image column of staged byte 0 of staged row r.
+    const int Xs = CELL * j0 - 5, Ys = CELL * i0 - 5;
+    const int xa = max(Xs, 0), xb = min(Xs + PX, d.w);
+    for (int idx = t; idx < PY * NCH; idx += NT) {
+        const int r = idx / NCH, ci = idx - r * NCH;
+        const int Y = Ys + r;
+        if (Y < 0 || Y >= d.h || xa >= xb) continue;
+        const uintptr_t rp = (uintptr_t)(d.img + (size_t)Y * d.pitch);
+        const uintptr_t c0 = (rp + (uintptr_t)xa) & ~(uintptr_t)15;
+        const uintptr_t a = c0 + 16 * (uintptr_t)ci;
+        if (ci == 0) xbase[r] = (int)((intptr_t)c0 - (intptr_t)rp);
+        if (a <= rp + (uintptr_t)(xb - 1)) cp_async16(srcS + r * SROWB + 16 * ci, (const void *)a);
     }
+    for (int k = t; k < 4 * NBIN * NT; k += NT) part[k] = 0.0f;
+    cp_async_wait_all();
     __syncthreads();
 
-    // phase 1: (bin, magnitude) of every region pixel; non-voting pixels get 0
-    for (int p = t; p < RX * RY; p += NT) {
-        const int ry = p / RX, rx = p - ry * RX;
-        const int X = X0 + rx, Y = Y0 + ry;
-        float m = 0.0f;
-        int b = 0;
-        if (X >= 1 && X <= xmax && Y >= 1 && Y <= ymax) {
-            const uint8_t *s = srcS + (ry + 1) * SXW + (rx + 1);
-            const int dx = (int)s[1] - (int)s[-1];
-            const int dy = (int)s[SXW] - (int)s[-SXW];
-            if (dx != 0 || dy != 0) {
-                b = orientation_bin_i(dx, dy);
-                m = sqrtf((float)(dx * dx + dy * dy));
-            }
+    // one 8x8 block per thread: pixels X = 8 bj - 4 + ox, Y = 8 bi - 4 + oy
+    const int by = t / HIST_BX, bx = t - by * HIST_BX;
+    const int X0 = CELL * (j0 + bx) - 4, Y0 = CELL * (i0 + by) - 4;
+    float *p0 = part + t;
+#pragma unroll 1
+    for (int oy = 0; oy < 8; oy++) {
+        const int Y = Y0 + oy;
+        if (Y < 1 || Y > ymax) continue;
+        const int r = Y - Ys;                       // staged row of Y
+        const uint8_t *up = srcS + (r - 1) * SROWB - xbase[r - 1];
+        const uint8_t *mid = srcS + r * SROWB - xbase[r];
+        const uint8_t *dn = srcS + (r + 1) * SROWB - xbase[r + 1];
+        const float wy1 = tent16(oy), wy0 = tent16(oy + 8);   // to cell rows bi, bi-1
+#pragma unroll
+        for (int ox = 0; ox < 8; ox++) {
+            const int X = X0 + ox;
+            if (X < 1 || X > xmax) continue;
+            const int dx = (int)mid[X + 1] - (int)mid[X - 1];
+            const int dy = (int)dn[X] - (int)up[X];
+            if ((dx | dy) == 0) continue;
+            const int b = orientation_bin_i(dx, dy);
+            const float m = sqrtf((float)(dx * dx + dy * dy));
+            const float wx1 = tent16(ox), wx0 = tent16(ox + 8);   // to cell cols bj, bj-1
+            float *pb = p0 + b * NT;
+            pb[0 * NBIN * NT] += m * (wy0 * wx0);   // cell (bi-1, bj-1)
+            pb[1 * NBIN * NT] += m * (wy0 * wx1);   // cell (bi-1, bj)
+            pb[2 * NBIN * NT] += m * (wy1 * wx0);   // cell (bi,   bj-1)
+            pb[3 * NBIN * NT] += m * (wy1 * wx1);   // cell (bi,   bj)
         }
-        const int idx = ry * MROW + (rx & 7) * PLANE + (rx >> 3);
-        magS[idx] = m;
-        binS[idx] = (uint8_t)b;
     }
-    __syncthreads();   // srcS is dead from here on; qh reuses its space
-
-    // phase 2: zero the private quadrant histograms, then gather
-    for (int k = t; k < 4 * NBIN * NT; k += NT) qh[k] = 0.0f;
     __syncthreads();
 
-    const int ti = t / HIST_TX, tj = t - ti * HIST_TX;
+    // cell (ci, cj) of the tile = blocks (ci,cj) corner 3 + (ci,cj+1) corner 2
+    // + (ci+1,cj) corner 1 + (ci+1,cj+1) corner 0; staged for a coalesced store
+    float *outS = reinterpret_cast<float *>(srcS);   // [15*15][18] = 16,200 bytes
+    if (t < HIST_TX * HIST_TY) {
+        const int ci = t / HIST_TX, cj = t - ci * HIST_TX;
+        const int b00 = ci * HIST_BX + cj;
 #pragma unroll
-    for (int dy = 0; dy < 8; dy++) {
-#pragma unroll
-        for (int dx = 0; dx < 8; dx++) {
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int qy = q >> 1, qx = q & 1;
-                const int idx = (8 * ti + 8 * qy + dy) * MROW + dx * PLANE + tj + qx;
-                const float m = magS[idx];
-                const int b = binS[idx];
-                float *h = qh + (q * NBIN + b) * NT + t;
-                *h += m * (tent16(8 * qx + dx) * tent16(8 * qy + dy));
-            }
+        for (int b = 0; b < NBIN; b++) {
+            const float s3 = part[(3 * NBIN + b) * NT + b00];
+            const float s2 = part[(2 * NBIN + b) * NT + b00 + 1];
+            const float s1 = part[(1 * NBIN + b) * NT + b00 + HIST_BX];
+            const float s0 = part[(0 * NBIN + b) * NT + b00 + HIST_BX + 1];
+            outS[t * NBIN + b] = (s3 + s2) + (s1 + s0);
         }
-    }
-    __syncthreads();
-
-    // sum quadrants, stage [cell][18] in magS, then coalesced copy out
-    float *hs = magS;
-#pragma unroll
-    for (int b = 0; b < NBIN; b++) {
-        const float s01 = qh[(0 * NBIN + b) * NT + t] + qh[(1 * NBIN + b) * NT + t];
-        const float s23 = qh[(2 * NBIN + b) * NT + t] + qh[(3 * NBIN + b) * NT + t];
-        hs[t * NBIN + b] = s01 + s23;
     }
     __syncthreads();
     const int ncol = min(HIST_TX, d.cx - j0);
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(NT) hist_kernel(const LevelDesc *__restrict__ 
         const int i = i0 + r;
         if (i >= d.cy) break;
         float *dst = d.hist + ((size_t)i * d.cx + j0) * NBIN;
-        const float *srcr = hs + r * HIST_TX * NBIN;
+        const float *srcr = outS + r * HIST_TX * NBIN;
         for (int k = t; k < ncol * NBIN; k += NT) dst[k] = srcr[k];
     }
 }

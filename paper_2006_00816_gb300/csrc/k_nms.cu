@@ -28,6 +28,7 @@ namespace hogk {
 namespace {
 constexpr uint8_t ST_DEAD = 0, ST_ALIVE = 1, ST_KEPT = 2;
 constexpr int NMS_NT = 512;
+constexpr int NMS_SMEM_MAX = 200 * 1024;   // dynamic shared memory for keys and states
 
 struct Box {
     double x, y, w, h;
@@ -104,29 +105,42 @@ __global__ void __launch_bounds__(256) nms_geometry_kernel(GeomDesc g, int32_t *
     cnt[p] = (uint8_t)n;
 }
 
+// MODE 2: keys and states in shared memory; 1: states only; 0: both global.
+template <int MODE>
 __global__ void __launch_bounds__(NMS_NT) nms_kernel(const FrameDesc *__restrict__ frames,
                                                      int *flags) {
+    extern __shared__ __align__(16) unsigned char nsm[];
     const FrameDesc &fd = frames[blockIdx.x];
     const int t = threadIdx.x;
     const int npos = fd.npos;
-    volatile uint8_t *state = fd.state;
-    const uint64_t *keys = fd.keys;
+    uint64_t *skeys = reinterpret_cast<uint64_t *>(nsm);
+    uint8_t *sstate = MODE == 2 ? nsm + (size_t)npos * 8 : nsm;
+    volatile uint8_t *state = MODE >= 1 ? sstate : fd.state;
+    const uint64_t *__restrict__ gkeys = fd.keys;
+    const uint64_t *keys = MODE == 2 ? skeys : gkeys;
+    const int32_t *__restrict__ nbr = fd.nbr;
+    const uint8_t *__restrict__ nbr_cnt = fd.nbr_cnt;
 
-    for (int p = t; p < npos; p += NMS_NT) state[p] = keys[p] != KEY_NONE ? ST_ALIVE : ST_DEAD;
+    for (int p = t; p < npos; p += NMS_NT) {
+        const uint64_t k = __ldg(gkeys + p);
+        if (MODE == 2) skeys[p] = k;
+        state[p] = k != KEY_NONE ? ST_ALIVE : ST_DEAD;
+    }
     __syncthreads();
 
     // rounds; each one decides at least the best undecided candidate
-    for (int round = 0; round <= npos; round++) {
+    int round = 0;
+    for (; round <= npos; round++) {
         int undecided = 0;
         for (int p = t; p < npos; p += NMS_NT) {
             if (state[p] != ST_ALIVE) continue;
             const uint64_t kp = keys[p];
-            const int n = fd.nbr_cnt[p];
-            const int32_t *nb = fd.nbr + (size_t)p * MAXN;
+            const int n = __ldg(nbr_cnt + p);
+            const int32_t *nb = nbr + (size_t)p * MAXN;
             bool dead = false, wait = false;
             for (int s = 0; s < n; s++) {
-                const int q = nb[s];
-                if (keys[q] >= kp) continue;          // ranked below p (or no candidate)
+                const int q = __ldg(nb + s);
+                if (keys[q] >= kp) continue;   // ranked below p (or no candidate)
                 const uint8_t sq = state[q];
                 if (sq == ST_KEPT) { dead = true; break; }
                 if (sq == ST_ALIVE) wait = true;
@@ -187,7 +201,40 @@ __global__ void __launch_bounds__(NMS_NT) nms_kernel(const FrameDesc *__restrict
     if (t == 0) {
         *fd.count = total;
         if (total > fd.out_cap) atomicOr(flags, 1);
+        atomicMax(flags + 1, round + 1);
     }
+}
+
+__global__ void __launch_bounds__(256) pack_kernel(const hog_det *__restrict__ dets, int per_frame,
+                                                   const int32_t *__restrict__ counts, int nframes,
+                                                   hog_det *out, int out_cap, int32_t *counts_out) {
+    const int i = blockIdx.x;
+    __shared__ int off_s;
+    if (threadIdx.x < 32) {
+        int s = 0;
+        for (int k = threadIdx.x; k < i; k += 32) s += min(counts[k], per_frame);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) off_s = s;
+    }
+    __syncthreads();
+    const int off = off_s;
+    const int n = min(counts[i], per_frame);
+    // copy as 8-byte words (hog_det is 56 bytes = 7 words)
+    const unsigned long long *src =
+        reinterpret_cast<const unsigned long long *>(dets + (size_t)i * per_frame);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(out + off);
+    const int nw = max(0, min(n, out_cap - off)) * 7;
+    for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = src[k];
+    if (threadIdx.x == 0) counts_out[i] = counts[i];
+}
+
+cudaError_t launch_pack(const hog_det *dets, int per_frame, const int32_t *counts, int nframes,
+                        hog_det *out, int out_cap, int32_t *counts_out, cudaStream_t stream) {
+    if (nframes <= 0) return cudaSuccess;
+    pack_kernel<<<nframes, 256, 0, stream>>>(dets, per_frame, counts, nframes, out, out_cap,
+                                             counts_out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, uint8_t *cnt, int *overflow,
@@ -197,9 +244,26 @@ cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, uint8_t *cnt, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_nms(const FrameDesc *frames, int nframes, int *flags, cudaStream_t stream) {
+cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *flags,
+                       cudaStream_t stream) {
     if (nframes <= 0) return cudaSuccess;
-    nms_kernel<<<nframes, NMS_NT, 0, stream>>>(frames, flags);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(nms_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             NMS_SMEM_MAX);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(nms_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     NMS_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const size_t both = (size_t)max_npos * 9 + 16, states = (size_t)max_npos + 16;
+    if (both <= (size_t)NMS_SMEM_MAX)
+        nms_kernel<2><<<nframes, NMS_NT, both, stream>>>(frames, flags);
+    else if (states <= (size_t)NMS_SMEM_MAX)
+        nms_kernel<1><<<nframes, NMS_NT, states, stream>>>(frames, flags);
+    else
+        nms_kernel<0><<<nframes, NMS_NT, 0, stream>>>(frames, flags);
     return cudaGetLastError();
 }
 

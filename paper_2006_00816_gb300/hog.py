@@ -136,6 +136,14 @@ def features_static(frame, params: Params | None = None, stream=None):
     return res, rc, err.value.decode()
 
 
+def pinned_dets(n):
+    """A DET_DTYPE numpy array of n entries in pinned host memory (kept alive
+    by the returned tensor), for ``Detector.detect(..., out=...)``."""
+    import torch
+    t = torch.empty(n * DET_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+    return t.numpy().view(DET_DTYPE), t
+
+
 def _stream_ptr(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -245,33 +253,49 @@ class Detector:
             res.append(out[lv[i].offset:lv[i].offset + F * nu * nv].view(F, nu, nv))
         return res
 
-    def detect(self, frames, det_cap=None, stream=None, allow_capacity=False):
+    def detect(self, frames, det_cap=None, stream=None, allow_capacity=False, out=None):
         """Detect on a list of device uint8 frames.  Returns (dets, counts):
-        dets a numpy structured array (DET_DTYPE), counts int32 per frame."""
+        dets a numpy structured array (DET_DTYPE), counts int32 per frame.
+        With ``out`` (a DET_DTYPE array, e.g. a view of pinned memory, which
+        the device then fills directly), dets is a view of ``out``."""
         n = len(frames)
         arr = (Frame * max(n, 1))(*[_frame_of(f) for f in frames])
-        if det_cap is None:
-            det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
-        dets = np.zeros(max(det_cap, 1), DET_DTYPE)
+        if out is not None:
+            assert out.dtype == DET_DTYPE and out.flags.c_contiguous
+            dets = out
+            det_cap = len(out) if det_cap is None else min(det_cap, len(out))
+        else:
+            if det_cap is None:
+                det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
+            dets = np.empty(max(det_cap, 1), DET_DTYPE)
         counts = np.zeros(max(n, 1), np.int32)
         rc = _lib.hog_detect(self._h, arr, n, dets.ctypes.data_as(_vp), det_cap,
                              counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
         self._check(rc, allow=(HOG_ECAPACITY,) if allow_capacity else ())
-        total = int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum())
-        return dets[:min(total, det_cap)].copy(), counts[:n].copy()
+        total = min(int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum()), det_cap)
+        if out is not None:
+            return dets[:total], counts[:n].copy()
+        return dets[:total].copy(), counts[:n].copy()
 
-    def detect_host(self, frames, det_cap=None, stream=None, allow_capacity=False):
+    def detect_host(self, frames, det_cap=None, stream=None, allow_capacity=False, out=None):
         """Same as detect, from host numpy uint8 frames [h, w] (copied in the call)."""
         n = len(frames)
         frames = [np.ascontiguousarray(f, dtype=np.uint8) for f in frames]
         arr = (Frame * max(n, 1))(*[Frame(f.ctypes.data_as(_vp), f.shape[1], f.shape[0],
                                           f.strides[0]) for f in frames])
-        if det_cap is None:
-            det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
-        dets = np.zeros(max(det_cap, 1), DET_DTYPE)
+        if out is not None:
+            assert out.dtype == DET_DTYPE and out.flags.c_contiguous
+            dets = out
+            det_cap = len(out) if det_cap is None else min(det_cap, len(out))
+        else:
+            if det_cap is None:
+                det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
+            dets = np.empty(max(det_cap, 1), DET_DTYPE)
         counts = np.zeros(max(n, 1), np.int32)
         rc = _lib.hog_detect_host(self._h, arr, n, dets.ctypes.data_as(_vp), det_cap,
                                   counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
         self._check(rc, allow=(HOG_ECAPACITY,) if allow_capacity else ())
-        total = int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum())
-        return dets[:min(total, det_cap)].copy(), counts[:n].copy()
+        total = min(int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum()), det_cap)
+        if out is not None:
+            return dets[:total], counts[:n].copy()
+        return dets[:total].copy(), counts[:n].copy()

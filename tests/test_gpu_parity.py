@@ -277,3 +277,25 @@ def test_planted_template_top_detection(H, oracle, synth):
     assert (int(top["level"]), int(top["u"]), int(top["v"])) == \
         (int(ok[0]["level"]), int(ok[0]["u"]), int(ok[0]["v"]))
     assert abs(float(top["score"]) - ok[0]["score"]) <= SCORE_ATOL
+
+
+def test_pinned_output_and_plan_cache(H, synth):
+    """Kept boxes written by the device straight into pinned host memory
+    equal the staged path; a repeated batch (cached plan) on buffers whose
+    contents changed gives the new frames' results."""
+    W = synth.filters(5)
+    det = H.Detector(W, max_w=640, max_h=480, max_batch=3)
+    frames = [dev(synth.eyeblink_frame(i)) for i in range(4)]
+    d1, c1 = det.detect(frames)
+    out, keep = H.pinned_dets(4 * 2000)
+    d2, c2 = det.detect(frames, out=out)
+    assert c1.tolist() == c2.tolist() and np.array_equal(d1, d2)
+    d3, c3 = det.detect(frames, out=out)          # cached plans, same frames
+    assert c3.tolist() == c1.tolist() and np.array_equal(d3, d1)
+    for i, f in enumerate(frames):                 # same buffers, new contents
+        f.copy_(dev(synth.eyeblink_frame(50 + i)))
+    d4, c4 = det.detect(frames)
+    fresh = H.Detector(W, max_w=640, max_h=480, max_batch=3)
+    d5, c5 = fresh.detect([f.clone() for f in frames])
+    assert c4.tolist() == c5.tolist()
+    assert _kept_set(d4) == _kept_set(d5)
