@@ -199,49 +199,79 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
-    # ---- batched path: warm-up, then K timed steps
-    for _ in range(args.warmup):
-        det.detect(frames, out=out_np)
-    det.set_profiling(True)
-    det.stage_stats(reset=True)
+    # ---- autotune on the first batch (tile-shape policy, fused vs per-stage)
+    tune_path = os.path.join("/tmp", "hog_gb300_tune_%d.json" % os.getpid())
+    mode, corr_policy = det.autotune(frames[:args.batch], cache_path=tune_path)
+    try:
+        tune = json.load(open(tune_path))
+        os.remove(tune_path)
+    except (OSError, ValueError):
+        tune = {}
+
+    def run_steps(k, batched=True):
+        ms, dets = [], 0
+        for _ in range(k):
+            t0 = time.perf_counter()
+            d, c = det.detect(frames, out=out_np, batched=batched)
+            ms.append((time.perf_counter() - t0) * 1e3)
+            dets += int(c.sum())
+        return ms, dets
+
+    # ---- batched path (autotuned mode, CUDA graphs): warm-up, then K timed steps
+    run_steps(args.warmup)
     sampler = ClockSampler(dev.index)
     sampler.start()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    chunk_ms = []
-    total_dets = 0
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        d, c = det.detect(frames, out=out_np)
-        chunk_ms.append((time.perf_counter() - t0) * 1e3)
-        total_dets += int(c.sum())
+    chunk_ms, total_dets = run_steps(args.steps)
     ev1.record(stream)
     barrier()
     clocks = sampler.stop()
     step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
-    stats = det.stage_stats(reset=True)
-    det.set_profiling(False)
     fps = ws * nfr / (step_ms / 1e3)
 
-    # ---- roofline of the dominant kernel (correlation), from its CUDA events
-    corr_ms, corr_launches, corr_units = stats["corr"]
-    corr_flops = corr_units * CORR_FLOP_PER_UNIT
-    achieved = corr_flops / (corr_ms / 1e3) / 1e12 if corr_ms > 0 else None
+    # ---- the other batched mode, for comparison
+    other = 1 - mode
+    det.set_batched_mode(other)
+    run_steps(max(1, args.warmup))
+    barrier()
+    t0 = time.perf_counter()
+    run_steps(args.steps)
+    barrier()
+    other_fps = ws * nfr * args.steps / max_over_ranks(time.perf_counter() - t0)
+    det.set_batched_mode(mode)
+
+    # ---- profiled pass of the same workload: CUDA events around each stage
+    # (or around the fused launch) on the launching stream
+    det.set_profiling(True)
+    det.stage_stats(reset=True)
+    run_steps(args.steps)
+    stats = det.stage_stats(reset=True)
+    det.set_profiling(False)
+    key = "fused" if mode == 1 else "corr"
+    k_ms, k_launches, k_units = stats[key]
+    k_flops = k_units * CORR_FLOP_PER_UNIT
+    achieved = k_flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None,
-                "traffic": None, "kernel": "corr_kernel<5>",
-                "flop_per_launch": corr_flops / max(corr_launches, 1),
-                "avg_launch_ms": corr_ms / max(corr_launches, 1),
+                "traffic": None,
+                "kernel": "fused_kernel<5> (pyramid..correlation)" if mode == 1 else "corr_kernel<5>",
+                "flop_per_launch": k_flops / max(k_launches, 1),
+                "avg_launch_ms": k_ms / max(k_launches, 1),
+                "flop_note": "correlation FLOPs only (6,200 per window x filter)",
                 "peak_note": "derived FP32 FMA peak (152 SM x 128 lanes x 2 x 2.07 GHz)"}
-    stage_ms = {k: v[0] / args.steps for k, v in stats.items()}
-    gpu_launches = int(sum(v[1] for v in stats.values()))
+    stage_ms = {k: v[0] / args.steps for k, v in stats.items() if v[1] > 0}
+    nchunks = (nfr + args.batch - 1) // args.batch
+    gpu_launches = int(sum(v[1] for v in stats.values())) + nchunks * args.steps   # + pack
 
     # ---- plain per-frame path: one call per frame, latency per call
     nplain = min(args.plain_frames, nfr)
     plain = hog.Detector(W, max_w=W0, max_h=H0, max_batch=1)
     for i in range(10):
         plain.detect([frames[i]], out=out_np)
+    plain.set_profiling(True)
+    plain.stage_stats(reset=True)
     barrier()
     lat = []
     t0 = time.perf_counter()
@@ -251,6 +281,7 @@ def main():
         lat.append((time.perf_counter() - s) * 1e3)
     plain_s = time.perf_counter() - t0
     plain_fps = nplain / plain_s
+    plain_stages = {k: v[0] / nplain for k, v in plain.stage_stats(reset=True).items()}
     plain.close()
 
     # ---- e2e: host frames in pinned memory through hog_detect_host
@@ -298,11 +329,16 @@ def main():
             "config": {"workload": WORKLOAD, "frames_per_step": nfr, "batch": args.batch,
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs 307 MB per step exceed the 129 MB L2; no flush"},
-            "batched": {"frames_per_s": fps, "batch_p50_ms": statistics.median(chunk_ms),
-                        "batch_p99_ms": float(np.percentile(chunk_ms, 99)),
-                        "kept_per_frame": total_dets / (args.steps * nfr)},
+            "batched": {"frames_per_s": fps, "mode": "fused" if mode == 1 else "per-stage",
+                        "graphs": True, "corr_tile_policy": corr_policy,
+                        "other_mode_frames_per_s": other_fps,
+                        "step_p50_ms": statistics.median(chunk_ms),
+                        "step_p99_ms": float(np.percentile(chunk_ms, 99)),
+                        "kept_per_frame": total_dets / (args.steps * nfr),
+                        "autotune": tune},
             "plain": {"frames_per_s": plain_fps, "p50_ms": statistics.median(lat),
-                      "p99_ms": float(np.percentile(lat, 99)), "frames": nplain},
+                      "p99_ms": float(np.percentile(lat, 99)), "frames": nplain,
+                      "stage_ms_per_frame": plain_stages},
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roofline,

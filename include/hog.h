@@ -162,8 +162,41 @@ int hog_scores(hog_ctx *ctx, const hog_frame *frame, float *scores_out, size_t c
 int hog_detect(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
                int32_t det_cap, int32_t *counts, void *stream);
 
+/* Same result as hog_detect (bit for bit), computed the batched way: all
+ * pyramid levels of all frames (any mix of sizes) in one persistent fused
+ * launch -- work items in dependency order, taken from a ticket counter,
+ * bounded waits on per-(frame, level, stage) completion counters -- then
+ * the suppression launch; from the second call on a batch of the same
+ * frame buffers, both replay as a captured CUDA graph.  This generalises
+ * the paper's batching of 16 frames along the grid's z dimension and its
+ * per-scale streams (Section 5.1).  hog_autotune may select the per-stage
+ * launches instead, when they measure faster.  HOG_ETIMEOUT if a bounded
+ * device wait gave up (outputs invalid).  Synchronises the stream. */
+int hog_detect_batched(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
+                       int32_t det_cap, int32_t *counts, void *stream);
+
+/* Execution used by hog_detect_batched and hog_detect_host: 1 = persistent
+ * fused launch (default), 0 = one launch per stage (both as graphs). */
+int hog_set_batched_mode(hog_ctx *ctx, int32_t mode);
+
+/* Autotuner (no counterpart in the paper, which picks block sizes by hand,
+ * Section 5.1 block-size table).  On the given sample batch (device frames)
+ * it times the correlation stage under each warp-tile shape policy (least
+ * padding, or prefer 8x16, 4x32 or 16x8 tiles) with CUDA events, then the
+ * batched call in fused and per-stage mode, and keeps the fastest of each in
+ * the context.  If cache_path names a JSON file written for the same device,
+ * SM count, filter count and frame sizes, its choice is loaded instead of
+ * measured; otherwise the measurement is written there.  cache_path may be
+ * NULL.  Synchronises the stream. */
+int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const char *cache_path,
+                 void *stream);
+
+/* Current tuning: batched mode (0/1) and correlation shape policy (0..3). */
+int hog_get_tuning(const hog_ctx *ctx, int32_t *batched_mode, int32_t *corr_policy);
+
 /* Same result as hog_detect, from frames in HOST memory: the frames are
- * copied to the device inside the call (pinned staging). */
+ * copied to the device inside the call (pinned staging) and processed like
+ * hog_detect_batched. */
 int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
                     int32_t det_cap, int32_t *counts, void *stream);
 
@@ -187,13 +220,14 @@ int hog_features_static(const hog_params *p, const hog_frame *frame, float *feat
 
 /* ---- stage timing (tracing; no counterpart in the paper, which reads its
  * kernel times from a profiler, Section 5.1) ------------------------------ */
-#define HOG_NSTAGES 5   /* 0 pyramid, 1 gradient+histogram, 2 normalisation+
-                           features, 3 correlation+threshold, 4 suppression */
+#define HOG_NSTAGES 6   /* 0 pyramid, 1 gradient+histogram, 2 normalisation+
+                           features, 3 correlation+threshold, 4 suppression,
+                           5 persistent fused launch (pyramid .. correlation) */
 typedef struct {
     double  ms;         /* summed GPU time between CUDA events around the stage */
     int64_t launches;   /* kernel launches of the stage                         */
     int64_t units;      /* work units: output pixels, cells, cells, window x
-                           filter products, frames                            */
+                           filter products, frames, window x filter products  */
 } hog_stage_stat;
 
 /* Turn per-stage CUDA-event timing on (1) or off (0).  Events are recorded

@@ -32,6 +32,8 @@ def _flags(verbose: bool):
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC] + ARCH
     if verbose:
         f += ["-Xptxas", "-v"]
+    # diagnostic knob: extra nvcc flags for experimental builds (e.g. -DHOG_CORR_MINB=4)
+    f += os.environ.get("HOG_NVCC_FLAGS", "").split()
     return f
 
 

@@ -93,6 +93,7 @@ int compute_geometry(const hog_params &p, int W, int H, Geometry &g) {
 
 namespace {
 struct PlanLayout {
+    size_t items = 0;
     size_t descs = 0, frames = 0, hist = 0, feat = 0, corr = 0, total = 0;
     std::vector<size_t> pyr;
     std::vector<int> npyr;
@@ -102,8 +103,13 @@ struct PlanLayout {
 struct PlanInfo {
     PlanLayout L;
     int nhist = 0, nfeat = 0, ncorr = 0, nframes = 0, max_npos = 0;
+    int nitems = 0, nctr = 0;       // persistent fused launch: work items, counters
     int64_t px = 0, cells = 0, wins = 0;
 };
+
+// Execution of a detection batch: one launch per stage, or the persistent
+// fused launch (pyramid .. correlation) followed by the suppression launch.
+enum { MODE_STAGED = 0, MODE_FUSED = 1 };
 
 struct CachedPlan {
     std::vector<uint64_t> sig;
@@ -111,6 +117,8 @@ struct CachedPlan {
     char *d = nullptr;
     size_t cap = 0;
     uint64_t used = 0;
+    int runs = 0;                           // eager runs so far (graphs are captured after one)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // per mode
 };
 }  // namespace
 
@@ -123,7 +131,7 @@ struct hog_ctx {
     uint8_t *d_pyr = nullptr;
     float *d_hist = nullptr, *d_feat = nullptr;
     uint64_t *d_keys = nullptr;
-    uint8_t *d_state = nullptr;
+    uint32_t *d_nmsws = nullptr;    // suppression workspace, 13 bytes (4 words) per position
     hog_det *d_dets = nullptr;
     int32_t *d_counts = nullptr;
     int *d_flags = nullptr;
@@ -139,11 +147,19 @@ struct hog_ctx {
     cudaEvent_t plan_done = nullptr;
     // stage timing
     bool prof = false, prof_pending = false;
+    unsigned prof_mask = 0;         // stages whose events the last profiled batch recorded
     cudaEvent_t prof_ev[2 * HOG_NSTAGES] = {};
     hog_stage_stat stats[HOG_NSTAGES] = {};
     std::vector<Geometry *> geoms;
     std::vector<CachedPlan> plans;
     uint64_t plan_clock = 0;
+    // persistent fused launch and graphs
+    int *d_fctr = nullptr;          // completion counters + ticket + abort flag
+    size_t fctr_cap = 0;            // ints
+    int num_sms = 0, fused_grid = 0;
+    int batched_mode = MODE_FUSED;  // chosen by the autotuner
+    int corr_policy = 0;            // 0: least padding; 1 + s: prefer warp-tile shape s
+    cudaStream_t cap_stream = nullptr;
     std::string err;
 };
 
@@ -216,13 +232,18 @@ void free_ctx(hog_ctx *ctx) {
     auto F = [](void *p) { if (p) cudaFree(p); };
     auto FH = [](void *p) { if (p) cudaFreeHost(p); };
     F(ctx->d_w); F(ctx->d_pyr); F(ctx->d_hist); F(ctx->d_feat); F(ctx->d_keys);
-    F(ctx->d_state); F(ctx->d_dets); F(ctx->d_counts); F(ctx->d_flags); F(ctx->d_plan);
+    F(ctx->d_nmsws); F(ctx->d_dets); F(ctx->d_counts); F(ctx->d_flags); F(ctx->d_plan);
     F(ctx->d_stage);
     FH(ctx->h_plan); FH(ctx->h_dets); FH(ctx->h_counts); FH(ctx->h_flags); FH(ctx->h_stage);
     if (ctx->plan_done) cudaEventDestroy(ctx->plan_done);
     for (cudaEvent_t e : ctx->prof_ev)
         if (e) cudaEventDestroy(e);
-    for (auto &cp : ctx->plans) F(cp.d);
+    for (auto &cp : ctx->plans) {
+        F(cp.d);
+        for (auto &g : cp.graph) if (g) cudaGraphExecDestroy(g);
+    }
+    F(ctx->d_fctr);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (Geometry *g : ctx->geoms) {
         F(g->d_nbr);
         F(g->d_cnt);
@@ -298,7 +319,61 @@ struct PlanBuilder {
     std::vector<FrameDesc> frames;
     std::vector<std::vector<Job>> pyr;   // per step (target level)
     std::vector<Job> hist, feat, corr;
+    std::vector<FusedItem> items;        // persistent fused launch (built on demand)
+    int nctr = 0;
 };
+
+// Work items of the persistent fused launch, in dependency-depth order:
+// pyramid level l at depth l, its histograms at l+1, features at l+2,
+// correlation at l+3; counters ctr[3 d + stage] count finished tiles of
+// level descriptor d (stage 0 pyramid, 1 histograms, 2 features).
+void build_fused_items(PlanBuilder &pb) {
+    const int nd = (int)pb.descs.size();
+    std::vector<int> npyr(nd, 0), nhist(nd, 0), nfeat(nd, 0);
+    for (const auto &seg : pb.pyr)
+        for (const Job &j : seg) npyr[j.desc]++;
+    for (const Job &j : pb.hist) nhist[j.desc]++;
+    for (const Job &j : pb.feat) nfeat[j.desc]++;
+    struct Keyed { int depth, kind, desc, tile; FusedItem it; };
+    std::vector<Keyed> v;
+    v.reserve(pb.hist.size() + pb.feat.size() + pb.corr.size() / 4 + 1024);
+    for (const auto &seg : pb.pyr)
+        for (const Job &j : seg) {
+            const LevelDesc &d = pb.descs[j.desc];
+            FusedItem it{FUSED_PYR, j.desc, j.tile, -1, 0, 3 * j.desc + 0};
+            if (d.level >= 2) { it.wait = 3 * (j.desc - 1) + 0; it.target = npyr[j.desc - 1]; }
+            v.push_back({d.level, FUSED_PYR, j.desc, j.tile, it});
+        }
+    for (const Job &j : pb.hist) {
+        const LevelDesc &d = pb.descs[j.desc];
+        FusedItem it{FUSED_HIST, j.desc, j.tile, -1, 0, 3 * j.desc + 1};
+        if (d.level >= 1) { it.wait = 3 * j.desc + 0; it.target = npyr[j.desc]; }
+        v.push_back({d.level + 1, FUSED_HIST, j.desc, j.tile, it});
+    }
+    for (const Job &j : pb.feat) {
+        const LevelDesc &d = pb.descs[j.desc];
+        FusedItem it{FUSED_FEAT, j.desc, j.tile, 3 * j.desc + 1, nhist[j.desc], 3 * j.desc + 2};
+        v.push_back({d.level + 2, FUSED_FEAT, j.desc, j.tile, it});
+    }
+    for (size_t k = 0; k < pb.corr.size();) {
+        const int desc = pb.corr[k].desc;
+        size_t e = k;
+        while (e < pb.corr.size() && pb.corr[e].desc == desc && e - k < 8) e++;
+        const LevelDesc &d = pb.descs[desc];
+        FusedItem it{FUSED_CORR, (int)k, (int)(e - k), 3 * desc + 2, nfeat[desc], -1};
+        v.push_back({d.level + 3, FUSED_CORR, desc, (int)k, it});
+        k = e;
+    }
+    std::stable_sort(v.begin(), v.end(), [](const Keyed &a, const Keyed &b) {
+        if (a.depth != b.depth) return a.depth < b.depth;
+        if (a.kind != b.kind) return a.kind < b.kind;
+        if (a.desc != b.desc) return a.desc < b.desc;
+        return a.tile < b.tile;
+    });
+    pb.items.clear();
+    for (const Keyed &k : v) pb.items.push_back(k.it);
+    pb.nctr = 3 * nd;
+}
 
 
 
@@ -355,12 +430,20 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
             for (int k = 0; k < nfj; k++) pb.feat.push_back({di, k});
         }
         if (o.corr && d.nu > 0 && d.nv > 0 && (d.scan || o.scores_user)) {
-            // warp-tile shape that pads this level's window grid least
+            // warp-tile shape: the one that pads this level's window grid
+            // least, or the autotuner's preferred shape
             int best = 0, best_slots = 0, best_n = 0;
             for (int sh = 0; sh < CORR_NSHAPE; sh++) {
+                if (!corr_shape_ok(sh)) continue;
                 const int n = ((d.nu + corr_tu(sh) - 1) / corr_tu(sh)) *
                               ((d.nv + corr_tv(sh) - 1) / corr_tv(sh));
                 if (sh == 0 || n * 128 < best_slots) { best = sh; best_slots = n * 128; best_n = n; }
+            }
+            const int pref = ctx->corr_policy - 1;
+            if (pref >= 0 && pref < CORR_NSHAPE && corr_shape_ok(pref)) {
+                best = pref;
+                best_n = ((d.nu + corr_tu(pref) - 1) / corr_tu(pref)) *
+                         ((d.nv + corr_tv(pref) - 1) / corr_tv(pref));
             }
             for (int k = 0; k < best_n; k++) pb.corr.push_back({di, (best << 28) | k});
         }
@@ -377,7 +460,7 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         }
         fd.lev_pos[g.nlev] = g.npos;
         fd.keys = keys;
-        fd.state = ctx->d_state + (size_t)slot * ctx->pos_slot;
+        fd.ws = ctx->d_nmsws + (size_t)slot * ctx->pos_slot * 4;
         fd.nbr = g.d_nbr;
         fd.nbr_cnt = g.d_cnt;
         fd.out = ctx->d_dets + (size_t)slot * ctx->p.max_dets_per_frame;
@@ -404,7 +487,10 @@ void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
     L.hist = take(pb.hist.size() * sizeof(Job));
     L.feat = take(pb.feat.size() * sizeof(Job));
     L.corr = take(pb.corr.size() * sizeof(Job));
+    L.items = take(pb.items.size() * sizeof(FusedItem));
     L.total = off;
+    info.nitems = (int)pb.items.size();
+    info.nctr = pb.nctr;
     info.nhist = (int)pb.hist.size();
     info.nfeat = (int)pb.feat.size();
     info.ncorr = (int)pb.corr.size();
@@ -438,13 +524,15 @@ int ensure_plan_capacity(hog_ctx *ctx, size_t bytes) {
 // Fold the elapsed times of the last profiled plan into the stats.
 int collect_profile(hog_ctx *ctx) {
     if (!ctx->prof_pending) return HOG_OK;
-    CUDA_TRY(ctx, cudaEventSynchronize(ctx->prof_ev[2 * HOG_NSTAGES - 1]));
     for (int k = 0; k < HOG_NSTAGES; k++) {
+        if (!((ctx->prof_mask >> k) & 1u)) continue;
         float ms = 0.0f;
+        CUDA_TRY(ctx, cudaEventSynchronize(ctx->prof_ev[2 * k + 1]));
         CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->prof_ev[2 * k], ctx->prof_ev[2 * k + 1]));
         ctx->stats[k].ms += ms;
     }
     ctx->prof_pending = false;
+    ctx->prof_mask = 0;
     return HOG_OK;
 }
 
@@ -464,6 +552,7 @@ int upload_plan(hog_ctx *ctx, const PlanBuilder &pb, const PlanInfo &info, char 
     std::memcpy(h + L.hist, pb.hist.data(), pb.hist.size() * sizeof(Job));
     std::memcpy(h + L.feat, pb.feat.data(), pb.feat.size() * sizeof(Job));
     std::memcpy(h + L.corr, pb.corr.data(), pb.corr.size() * sizeof(Job));
+    std::memcpy(h + L.items, pb.items.data(), pb.items.size() * sizeof(FusedItem));
     CUDA_TRY(ctx, cudaMemcpyAsync(d_dst ? d_dst : ctx->d_plan, h, L.total, cudaMemcpyHostToDevice,
                                   stream));
     CUDA_TRY(ctx, cudaEventRecord(ctx->plan_done, stream));
@@ -505,6 +594,7 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
     CUDA_TRY(ctx, mark(9));
     if (ctx->prof) {
         ctx->prof_pending = true;
+        ctx->prof_mask = 0x1f;
         hog_stage_stat *st = ctx->stats;
         st[0].launches += npyr; st[0].units += info.px;
         st[1].launches += info.nhist > 0; st[1].units += info.nhist > 0 ? info.cells : 0;
@@ -528,7 +618,7 @@ int run_plan(hog_ctx *ctx, const PlanBuilder &pb, cudaStream_t stream) {
 // frames (pointer, size, pitch) and frame numbering: a repeated batch (a
 // ring of camera buffers, a benchmark loop) skips plan building and upload.
 int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, cudaStream_t stream,
-                const char **d_out, const PlanInfo **info_out) {
+                const char **d_out, const PlanInfo **info_out, CachedPlan **entry = nullptr) {
     std::vector<uint64_t> sig;
     sig.reserve(2 + 2 * (size_t)nb);
     sig.push_back((uint64_t)nb);
@@ -544,6 +634,7 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
             cp.used = ctx->plan_clock;
             *d_out = cp.d;
             *info_out = &cp.info;
+            if (entry) *entry = &cp;
             return HOG_OK;
         }
     PlanBuilder pb;
@@ -557,6 +648,7 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
         o.nms = g->npos > 0;
         add_frame(ctx, pb, *g, f, i, frame_base + i, o);
     }
+    build_fused_items(pb);
     PlanInfo info;
     layout_plan(pb, ctx->nf, info);
     // least recently used entry (or a free one)
@@ -564,6 +656,9 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
     CachedPlan *victim = &ctx->plans[0];
     for (auto &cp : ctx->plans)
         if (!cp.d || cp.used < victim->used) victim = &cp;
+    for (auto &g : victim->graph)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    victim->runs = 0;
     if (victim->cap < info.L.total) {
         if (victim->d) {
             CUDA_TRY(ctx, cudaStreamSynchronize(stream));
@@ -583,7 +678,96 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
     victim->used = ctx->plan_clock;
     *d_out = victim->d;
     *info_out = &victim->info;
+    if (entry) *entry = victim;
     return HOG_OK;
+}
+
+// Persistent fused launch of pyramid .. correlation, then suppression.
+int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t stream) {
+    const PlanLayout &L = info.L;
+    if ((size_t)info.nctr + 8 > ctx->fctr_cap)
+        return fail(ctx, HOG_EINTERNAL, "fused counter capacity %zu < %d", ctx->fctr_cap, info.nctr + 8);
+    int *head = ctx->d_fctr + info.nctr, *abort_flag = head + 1;
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_fctr, 0, sizeof(int) * ((size_t)info.nctr + 2), stream));
+    FusedArgs a;
+    a.items = reinterpret_cast<const FusedItem *>(d + L.items);
+    a.nitems = info.nitems;
+    a.descs = reinterpret_cast<const LevelDesc *>(d + L.descs);
+    a.jobs = reinterpret_cast<const Job *>(d + L.corr);
+    a.wchunks = ctx->d_w;
+    a.nf_real = ctx->nf;
+    a.threshold = ctx->p.threshold;
+    a.eps = ctx->p.eps;
+    a.tau = ctx->p.trunc;
+    a.ctr = ctx->d_fctr;
+    a.head = head;
+    a.abort = abort_flag;
+    a.flags = ctx->d_flags;
+    int rc = collect_profile(ctx);
+    if (rc) return rc;
+    auto mark = [&](int i) -> cudaError_t {
+        return ctx->prof ? cudaEventRecord(ctx->prof_ev[i], stream) : cudaSuccess;
+    };
+    CUDA_TRY(ctx, mark(10));
+    CUDA_TRY(ctx, launch_fused(a, ctx->nfk, ctx->fused_grid, stream));
+    CUDA_TRY(ctx, mark(11));
+    CUDA_TRY(ctx, mark(8));
+    if (info.nframes > 0)
+        CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.nframes,
+                                 info.max_npos, ctx->d_flags, stream));
+    CUDA_TRY(ctx, mark(9));
+    if (ctx->prof) {
+        ctx->prof_pending = true;
+        ctx->prof_mask = (1u << 4) | (1u << 5);
+        ctx->stats[5].launches += info.nitems > 0; ctx->stats[5].units += info.wins;
+        ctx->stats[4].launches += info.nframes > 0; ctx->stats[4].units += info.nframes;
+    }
+    return HOG_OK;
+}
+
+// Everything one detection batch enqueues before its outputs are packed.
+int enqueue_batch(hog_ctx *ctx, int mode, const char *d, const PlanInfo &info, int nb,
+                  cudaStream_t stream) {
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_counts, 0, sizeof(int32_t) * nb, stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), stream));
+    return mode == MODE_FUSED ? launch_fused_plan(ctx, d, info, stream)
+                              : launch_plan(ctx, d, info, stream);
+}
+
+// Run a batch eagerly, or -- from its second use on, with use_graph and no
+// profiling -- as a CUDA graph captured once per cached plan and mode.
+int run_batch(hog_ctx *ctx, int mode, CachedPlan *cp, int nb, bool use_graph, cudaStream_t stream) {
+    if (!use_graph || ctx->prof || cp->runs < 1) {
+        cp->runs++;
+        return enqueue_batch(ctx, mode, cp->d, cp->info, nb, stream);
+    }
+    if (!cp->graph[mode]) {
+        if (!ctx->cap_stream) CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_batch(ctx, mode, cp->d, cp->info, nb, ctx->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return fail(ctx, HOG_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&cp->graph[mode], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cp->graph[mode] = nullptr;
+            return fail(ctx, HOG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    CUDA_TRY(ctx, cudaGraphLaunch(cp->graph[mode], stream));
+    return HOG_OK;
+}
+
+// Drop every cached plan (and its graphs), e.g. after a tuning change.
+void clear_plans(hog_ctx *ctx) {
+    cudaDeviceSynchronize();
+    for (auto &cp : ctx->plans) {
+        if (cp.d) cudaFree(cp.d);
+        for (auto &g : cp.graph) if (g) cudaGraphExecDestroy(g);
+    }
+    ctx->plans.clear();
 }
 
 int check_frame(hog_ctx *ctx, const hog_frame *f, bool device) {
@@ -598,7 +782,8 @@ int check_frame(hog_ctx *ctx, const hog_frame *f, bool device) {
 }
 
 int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, hog_det *dets,
-                  int det_cap, int *written_out, int32_t *counts, cudaStream_t stream) {
+                  int det_cap, int *written_out, int32_t *counts, cudaStream_t stream,
+                  int mode = MODE_STAGED, bool use_graph = false) {
     int written = 0;
     bool truncated = false;
     // A pinned (page-locked, mapped) output buffer is written by the device
@@ -615,11 +800,10 @@ int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, 
         const int nb = std::min(ctx->p.max_batch, n - b0);
         const char *dplan = nullptr;
         const PlanInfo *info = nullptr;
-        int rc = cached_plan(ctx, frames + b0, nb, frame_base + b0, stream, &dplan, &info);
+        CachedPlan *cp = nullptr;
+        int rc = cached_plan(ctx, frames + b0, nb, frame_base + b0, stream, &dplan, &info, &cp);
         if (rc) return rc;
-        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_counts, 0, sizeof(int32_t) * nb, stream));
-        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, 2 * sizeof(int), stream));
-        rc = launch_plan(ctx, dplan, *info, stream);
+        rc = run_batch(ctx, mode, cp, nb, use_graph, stream);
         if (rc) return rc;
         // kept boxes of all frames, packed frame after frame into mapped
         // pinned host memory by one kernel, then one synchronisation
@@ -632,7 +816,11 @@ int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, 
             CUDA_TRY(ctx, launch_pack(ctx->d_dets, ctx->p.max_dets_per_frame, ctx->d_counts, nb,
                                       ctx->m_dets, (int)(D * ctx->p.max_batch), ctx->m_counts,
                                       stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, 4 * sizeof(int),
+                                      cudaMemcpyDeviceToHost, stream));
         CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        if (ctx->h_flags[2])
+            return fail(ctx, HOG_ETIMEOUT, "a bounded device wait gave up; results are invalid");
         size_t off = 0;
         for (int i = 0; i < nb; i++) {
             const int c = ctx->h_counts[i];
@@ -719,7 +907,7 @@ int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters
     M((void **)&ctx->d_hist, B * ctx->hist_slot * sizeof(float));
     M((void **)&ctx->d_feat, B * ctx->feat_slot * sizeof(float));
     M((void **)&ctx->d_keys, B * ctx->pos_slot * sizeof(uint64_t));
-    M((void **)&ctx->d_state, B * ctx->pos_slot);
+    M((void **)&ctx->d_nmsws, B * ctx->pos_slot * 4 * sizeof(uint32_t));
     M((void **)&ctx->d_dets, B * D * sizeof(hog_det));
     M((void **)&ctx->d_counts, B * sizeof(int32_t));
     M((void **)&ctx->d_flags, sizeof(int) * 4);
@@ -739,6 +927,20 @@ int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters
     }
     rc = ensure_plan_capacity(ctx, 1 << 20);
     if (rc) { g_create_error = ctx->err; free_ctx(ctx); return rc; }
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (ctx->num_sms <= 0) ctx->num_sms = 1;
+        ctx->fused_grid = ctx->num_sms * fused_max_ctas_per_sm(ctx->nfk);
+        ctx->fctr_cap = B * MAX_LEVELS * 3 + 16;
+        if (cudaMalloc(&ctx->d_fctr, ctx->fctr_cap * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            g_create_error = "counter allocation failed";
+            free_ctx(ctx);
+            return HOG_ENOMEM;
+        }
+    }
     *out = ctx;
     return HOG_OK;
 }
@@ -879,6 +1081,25 @@ int hog_detect(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det 
                          (cudaStream_t)stream_);
 }
 
+int hog_detect_batched(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
+                       int32_t det_cap, int32_t *counts, void *stream_) {
+    if (!ctx) return HOG_EINVAL;
+    if (n_frames < 0 || (n_frames > 0 && !frames) || det_cap < 0 || (det_cap > 0 && !dets))
+        return fail(ctx, HOG_EINVAL, "bad frames/dets arguments");
+    for (int i = 0; i < n_frames; i++) {
+        int rc = check_frame(ctx, &frames[i], true);
+        if (rc) return rc;
+    }
+    return detect_device(ctx, frames, n_frames, 0, dets, det_cap, nullptr, counts,
+                         (cudaStream_t)stream_, ctx->batched_mode, true);
+}
+
+int hog_set_batched_mode(hog_ctx *ctx, int32_t mode) {
+    if (!ctx || (mode != MODE_STAGED && mode != MODE_FUSED)) return HOG_EINVAL;
+    ctx->batched_mode = mode;
+    return HOG_OK;
+}
+
 int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
                     int32_t det_cap, int32_t *counts, void *stream_) {
     if (!ctx) return HOG_EINVAL;
@@ -921,12 +1142,143 @@ int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog
         const int cap = dets ? std::max(det_cap - total, 0) : 0;
         int wrote = 0;
         int rc = detect_device(ctx, dev.data(), nb, b0, dets ? dets + total : nullptr, cap, &wrote,
-                               counts ? counts + b0 : nullptr, stream);
+                               counts ? counts + b0 : nullptr, stream, ctx->batched_mode, true);
         if (rc == HOG_ECAPACITY) truncated = true;
         else if (rc) return rc;
         total += wrote;
     }
     return truncated ? fail(ctx, HOG_ECAPACITY, "detections truncated") : HOG_OK;
+}
+
+int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const char *cache_path,
+                 void *stream_) {
+    if (!ctx || n_frames < 1 || !frames) return HOG_EINVAL;
+    for (int i = 0; i < n_frames; i++) {
+        int rc = check_frame(ctx, &frames[i], true);
+        if (rc) return rc;
+    }
+    cudaStream_t stream = (cudaStream_t)stream_;
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    CUDA_TRY(ctx, cudaGetDeviceProperties(&prop, dev));
+    // key: device, SM count, filters, frame sizes of the sample
+    std::string key = std::string(prop.name) + "|" + std::to_string(prop.multiProcessorCount) +
+                      "|nf" + std::to_string(ctx->nf) + "|";
+    {   // distinct frame sizes with their counts, in first-seen order
+        std::vector<std::pair<std::pair<int, int>, int>> sizes;
+        for (int i = 0; i < n_frames; i++) {
+            bool found = false;
+            for (auto &sz : sizes)
+                if (sz.first.first == frames[i].w && sz.first.second == frames[i].h) { sz.second++; found = true; }
+            if (!found) sizes.push_back({{frames[i].w, frames[i].h}, 1});
+        }
+        for (auto &sz : sizes)
+            key += std::to_string(sz.first.first) + "x" + std::to_string(sz.first.second) + "*" +
+                   std::to_string(sz.second) + ",";
+    }
+    if (cache_path && *cache_path) {
+        FILE *f = std::fopen(cache_path, "r");
+        if (f) {
+            char buf[8192] = {0};
+            const size_t nread = std::fread(buf, 1, sizeof buf - 1, f);
+            std::fclose(f);
+            buf[nread] = 0;
+            const std::string txt(buf);
+            const std::string kq = "\"key\": \"" + key + "\"";
+            if (txt.find(kq) != std::string::npos) {
+                int mode = -1, pol = -1;
+                const size_t a = txt.find("\"batched_mode\": ");
+                const size_t b = txt.find("\"corr_policy\": ");
+                if (a != std::string::npos) mode = std::atoi(txt.c_str() + a + 16);
+                if (b != std::string::npos) pol = std::atoi(txt.c_str() + b + 15);
+                if ((mode == MODE_STAGED || mode == MODE_FUSED) && pol >= 0 && pol <= CORR_NSHAPE) {
+                    if (pol != ctx->corr_policy) { ctx->corr_policy = pol; clear_plans(ctx); }
+                    ctx->batched_mode = mode;
+                    return HOG_OK;
+                }
+            }
+        }
+    }
+    std::vector<hog_det> scratch((size_t)n_frames * ctx->p.max_dets_per_frame);
+    std::vector<int32_t> counts(n_frames);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(ctx, cudaEventCreate(&e0));
+    CUDA_TRY(ctx, cudaEventCreate(&e1));
+    auto timed = [&](int mode, bool graph, int reps, float *ms) -> int {
+        for (int r = 0; r < 2; r++) {   // eager run, then (for graphs) capture
+            int rc = detect_device(ctx, frames, n_frames, 0, scratch.data(), (int)scratch.size(), nullptr,
+                                   counts.data(), stream, mode, graph);
+            if (rc && rc != HOG_ECAPACITY) return rc;
+        }
+        CUDA_TRY(ctx, cudaEventRecord(e0, stream));
+        for (int r = 0; r < reps; r++) {
+            int rc = detect_device(ctx, frames, n_frames, 0, scratch.data(), (int)scratch.size(), nullptr,
+                                   counts.data(), stream, mode, graph);
+            if (rc && rc != HOG_ECAPACITY) return rc;
+        }
+        CUDA_TRY(ctx, cudaEventRecord(e1, stream));
+        CUDA_TRY(ctx, cudaEventSynchronize(e1));
+        CUDA_TRY(ctx, cudaEventElapsedTime(ms, e0, e1));
+        *ms /= reps;
+        return HOG_OK;
+    };
+    // 1. correlation tile-shape policy: time the correlation stage (events)
+    const bool was_prof = ctx->prof;
+    int rc = hog_set_profiling(ctx, 1);
+    double best_corr = 1e30;
+    int best_pol = 0;
+    double pol_ms[CORR_NSHAPE + 1];
+    for (int pol = 0; pol <= CORR_NSHAPE && rc == HOG_OK; pol++) {
+        pol_ms[pol] = -1.0;
+        if (pol >= 1 && !corr_shape_ok(pol - 1)) continue;
+        ctx->corr_policy = pol;
+        clear_plans(ctx);
+        float ms = 0.0f;
+        rc = timed(MODE_STAGED, false, 1, &ms);
+        hog_stage_stat st[HOG_NSTAGES];
+        hog_stage_stats(ctx, st, HOG_NSTAGES, 1);
+        if (rc) break;
+        rc = timed(MODE_STAGED, false, 3, &ms);
+        if (rc) break;
+        hog_stage_stats(ctx, st, HOG_NSTAGES, 1);
+        pol_ms[pol] = st[3].ms / 5.0;   // 2 warm + 3 timed calls
+        if (st[3].ms < best_corr) { best_corr = st[3].ms; best_pol = pol; }
+    }
+    hog_set_profiling(ctx, was_prof ? 1 : 0);
+    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+    ctx->corr_policy = best_pol;
+    clear_plans(ctx);
+    // 2. batched execution mode (both as graphs)
+    float ms_staged = 0.0f, ms_fused = 0.0f;
+    rc = timed(MODE_STAGED, true, 5, &ms_staged);
+    if (!rc) rc = timed(MODE_FUSED, true, 5, &ms_fused);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    ctx->batched_mode = ms_fused < ms_staged ? MODE_FUSED : MODE_STAGED;
+    if (cache_path && *cache_path) {
+        FILE *f = std::fopen(cache_path, "w");
+        if (f) {
+            std::fprintf(f, "{\n  \"key\": \"%s\",\n  \"batched_mode\": %d,\n  \"corr_policy\": %d,\n",
+                         key.c_str(), ctx->batched_mode, ctx->corr_policy);
+            std::fprintf(f, "  \"ms_per_batch\": {\"staged\": %.4f, \"fused\": %.4f},\n",
+                         ms_staged, ms_fused);
+            std::fprintf(f, "  \"corr_ms_by_policy\": [");
+            for (int pol = 0; pol <= CORR_NSHAPE; pol++)
+                std::fprintf(f, "%s%.4f", pol ? ", " : "", pol_ms[pol]);
+            std::fprintf(f, "]\n}\n");
+            std::fclose(f);
+        }
+    }
+    return HOG_OK;
+}
+
+int hog_get_tuning(const hog_ctx *ctx, int32_t *batched_mode, int32_t *corr_policy) {
+    if (!ctx) return HOG_EINVAL;
+    if (batched_mode) *batched_mode = ctx->batched_mode;
+    if (corr_policy) *corr_policy = ctx->corr_policy;
+    return HOG_OK;
 }
 
 }  // extern "C"

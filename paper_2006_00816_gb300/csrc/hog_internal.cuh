@@ -26,7 +26,13 @@ constexpr int HIST_TX = HIST_BX - 1, HIST_TY = HIST_BY - 1;   // 15 x 15 cells p
 constexpr int FEAT_TX = 32, FEAT_TY = 8;         // cells per CTA (256 threads)
 // Correlation warp tiles (windows): shape id 0: 8x16, 1: 4x32, 2: 16x8; the
 // shape is stored in bits 28..29 of the job's tile field.
+// CTAs per SM the correlation kernel is built for: 3 (all three shapes) or 4
+// (shapes 8x16 and 16x8 only, smaller staging buffers).
+#ifndef HOG_CORR_MINB
+#define HOG_CORR_MINB 3
+#endif
 constexpr int CORR_NSHAPE = 3;
+__host__ __device__ constexpr bool corr_shape_ok(int s) { return HOG_CORR_MINB < 4 || s != 1; }
 __host__ __device__ constexpr int corr_tu(int s) { return s == 0 ? 8 : (s == 1 ? 4 : 16); }
 __host__ __device__ constexpr int corr_tv(int s) { return s == 0 ? 16 : (s == 1 ? 32 : 8); }
 constexpr int CORR_WARPS = 4;                    // warps (independent tiles) per CTA
@@ -100,8 +106,8 @@ struct FrameDesc {
     int32_t lev_nu[MAX_LEVELS], lev_nv[MAX_LEVELS];
     int32_t lev_pos[MAX_LEVELS + 1];
     const uint64_t *keys;             // [npos]
-    uint8_t *state;                   // [npos]
-    const int32_t *nbr;               // [npos][MAXN]
+    uint32_t *ws;                     // suppression workspace (global mode), 5 B per position
+    const int32_t *nbr;               // [MAXN][npos] neighbour lists, slot-major
     const uint8_t *nbr_cnt;           // [npos]
     hog_det *out;                     // [out_cap]
     int32_t out_cap;
@@ -123,6 +129,34 @@ struct GeomDesc {
     int32_t lev_pos[MAX_LEVELS + 1];
     uint32_t pair_mask[MAX_LEVELS];   // bit m set: levels (l, m) can exceed the IoU
 };
+
+// ---- persistent fused launch (k_fused.cu) ---------------------------------
+enum FusedKind : int32_t { FUSED_PYR = 0, FUSED_HIST = 1, FUSED_FEAT = 2, FUSED_CORR = 3 };
+
+// One work item: PYR/HIST/FEAT: a = level descriptor, b = tile; CORR: a =
+// first job in the correlation job list, b = number of jobs (<= 8).  The item
+// starts once ctr[wait] >= target (wait < 0: no dependency) and adds 1 to
+// ctr[done] when it has finished (done < 0: nothing).
+struct FusedItem {
+    int32_t kind, a, b, wait, target, done;
+};
+
+struct FusedArgs {
+    const FusedItem *items;
+    int nitems;
+    const LevelDesc *descs;
+    const Job *jobs;               // correlation warp-tile jobs
+    const float *wchunks;
+    int nf_real;
+    float threshold, eps, tau;
+    int *ctr;                      // completion counters (zeroed before the launch)
+    int *head;                     // ticket counter (zeroed before the launch)
+    int *abort;                    // set when a bounded wait gave up (zeroed before)
+    int *flags;                    // flags[2] |= 1 on a timeout
+};
+
+cudaError_t launch_fused(const FusedArgs &a, int nf_kernel, int grid, cudaStream_t stream);
+int fused_max_ctas_per_sm(int nf_kernel);
 
 // ---- cp.async helpers (16-byte global -> shared copies, sm_80+) -----------
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -165,8 +199,9 @@ cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, uint8_t *cnt, i
 cudaError_t launch_pack(const hog_det *dets, int per_frame, const int32_t *counts, int nframes,
                         hog_det *out, int out_cap, int32_t *counts_out, cudaStream_t stream);
 
-// max_npos: largest npos of the frames (selects shared- or global-memory states).
-// flags[0] |= 1 on capacity overflow; flags[1] = max rounds taken by a frame.
+// max_npos: largest npos of the frames (selects the shared- or global-memory
+// workspace).  flags[0] |= 1 on capacity overflow; flags[2] |= 1 if a bounded
+// wait gave up.
 cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *flags,
                        cudaStream_t stream);
 

@@ -1,0 +1,620 @@
+// hog_stages.cuh -- the stages of the detection path as device functions.
+//
+// Each stage is written once and used by two callers: the stand-alone stage
+// kernels (one launch per stage over all frames of a batch, k_*.cu) and the
+// persistent fused kernel (k_fused.cu), which runs all stages of many frames
+// in one launch.  Template parameter COH ("coherent"): data produced earlier
+// in the same launch (pyramid levels, histograms, candidate keys) must be
+// read through L2 (ld.global.cg) rather than the non-coherent read-only path;
+// stand-alone kernels read data of earlier launches and may use __ldg.
+#pragma once
+
+#include "hog_internal.cuh"
+
+namespace hogk {
+
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_in(const T *p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
+// ===========================================================================
+// Pyramid (Section 4.1.1, first step; Section 5.1, image-scaling kernel).
+// Output pixel (x, y) of level l+1 samples level l at ((12x+1)/10,
+// (12y+1)/10) with exact weights in tenths, rounded half up (integer-exact).
+// 256 threads: 4 output pixels each, tile PYR_TX x PYR_TY.
+template <bool COH>
+__device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
+    const int ntx = (d.w + PYR_TX - 1) / PYR_TX;
+    const int tx = tile % ntx, ty = tile / ntx;
+    const int x = tx * PYR_TX + (threadIdx.x & 31) * 4;
+    const int y = ty * PYR_TY + (threadIdx.x >> 5);
+    if (y >= d.h || x >= d.w) return;
+    const int Y = 12 * y + 1;
+    const int y0 = Y / 10, fy = Y - 10 * (Y / 10);
+    const uint8_t *r0 = d.src + (size_t)y0 * d.spitch;
+    const uint8_t *r1 = r0 + d.spitch;
+    uint32_t packed = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int xx = x + k;
+        if (xx < d.w) {
+            const int X = 12 * xx + 1;
+            const int x0 = X / 10, fx = X - 10 * (X / 10);
+            const int p00 = ld_in<COH>(r0 + x0), p10 = ld_in<COH>(r0 + x0 + 1);
+            const int p01 = ld_in<COH>(r1 + x0), p11 = ld_in<COH>(r1 + x0 + 1);
+            const int acc = (10 - fx) * (10 - fy) * p00 + fx * (10 - fy) * p10 +
+                            (10 - fx) * fy * p01 + fx * fy * p11;
+            packed |= (uint32_t)((acc + 50) / 100) << (8 * k);
+        }
+    }
+    uint8_t *out = d.dst + (size_t)y * d.pitch + x;
+    if (x + 3 < d.w) {
+        *reinterpret_cast<uint32_t *>(out) = packed;   // pitch and x are multiples of 4
+    } else {
+        for (int k = 0; k < 4 && x + k < d.w; k++) out[k] = (uint8_t)(packed >> (8 * k));
+    }
+}
+
+// ===========================================================================
+// Gradient, orientation binning, cell histograms (Section 4.1.1: gradient
+// computation and histogramisation).
+//
+// Per pixel: central differences for 1 <= x <= min(w-2, 8cx-1),
+// 1 <= y <= min(h-2, 8cy-1); magnitude sqrt(dx^2+dy^2); one of 18 signed
+// orientations (nearest centre at 20 b degrees).  Each pixel votes
+// magnitude x tent weight into the four nearest 8x8 cells.
+//
+// The pixels between four neighbouring cell centres form an 8x8 "block"
+// (block (bi, bj) spans x in [8bj-4, 8bj+4), y in [8bi-4, 8bi+4)); all of a
+// block's pixels vote into the same four cells.  One thread owns one block:
+// it computes its 64 pixels from the staged bytes and accumulates four
+// private partial histograms (one per corner cell) in shared memory, laid
+// out [corner][bin][thread] so a warp's lanes hit 32 banks.  A cell is the
+// fixed-order sum of its four blocks' partials: deterministic, no atomics,
+// no sum longer than 64 terms.  256 threads own 16x16 blocks and emit the
+// 15x15 cells whose four blocks they hold.
+//
+// Orientation in exact integer arithmetic: fold (dx, dy) into the first
+// quadrant; the sector is the number of bin boundaries (10, 30, 50, 70
+// degrees) the vector lies beyond, tested as |dy| C - |dx| S > 0 with
+// C, S = round(2^20 cos, 2^20 sin).  For every 8-bit gradient this equals
+// the exact test (smallest |dy cos - dx sin| on the grid 1.3e-3 = 1340 units
+// at 2^20, against at most 255 units of rounding); products fit in int32.
+// dx == 0 (the only exact tie) goes to bin 4 (dy > 0) or 13.
+namespace hist_cfg {
+constexpr int NT = HIST_BX * HIST_BY;          // 256 threads, one per block
+constexpr int PX = HIST_BX * CELL + 2;         // 130 staged columns (blocks + 1-px halo)
+constexpr int PY = HIST_BY * CELL + 2;         // 130 staged rows
+constexpr int NCH = 10;                        // 16-byte chunks per staged row (130 + 15 <= 160)
+constexpr int SROWB = NCH * 16;                // 160 bytes per staged row
+constexpr size_t SMEM_SRC = (size_t)PY * SROWB;                     // 20,800
+constexpr size_t SMEM_PART = sizeof(float) * 4 * NBIN * NT;         // 73,728
+constexpr size_t SMEM_XB = sizeof(int) * 132;
+constexpr size_t SMEM = SMEM_PART + SMEM_SRC + SMEM_XB;             // 95,056
+}  // namespace hist_cfg
+
+__device__ __forceinline__ int orientation_bin_i(int dx, int dy) {
+    if (dx == 0) return dy > 0 ? 4 : 13;
+    const int ax = dx < 0 ? -dx : dx;
+    const int ay = dy < 0 ? -dy : dy;
+    const int q = (ay * 1032646 - ax * 182083 > 0) + (ay * 908093 - ax * 524288 > 0) +
+                  (ay * 674012 - ax * 803256 > 0) + (ay * 358634 - ax * 985339 > 0);
+    if (dx > 0) return dy >= 0 ? q : (q == 0 ? 0 : 18 - q);
+    return dy >= 0 ? 9 - q : 9 + q;
+}
+
+// Tent weight of footprint offset t (0..15) in sixteenths: 16 - |2t - 15|.
+__host__ __device__ constexpr float tent16(int t) {
+    return (float)(16 - (2 * t - 15 < 0 ? 15 - 2 * t : 2 * t - 15)) * (1.0f / 16.0f);
+}
+
+// 256 threads; smem >= hist_cfg::SMEM, 16-byte aligned.  Reads the level
+// image with cp.async.cg (through L2), so it is coherent within a launch.
+__device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned char *smem) {
+    using namespace hist_cfg;
+    float *part = reinterpret_cast<float *>(smem);             // [4][18][NT]
+    uint8_t *srcS = smem + SMEM_PART;                          // [PY][SROWB]
+    int *xbase = reinterpret_cast<int *>(smem + SMEM_PART + SMEM_SRC);
+
+    const int ntx = (d.cx + HIST_TX - 1) / HIST_TX;
+    const int j0 = (tile % ntx) * HIST_TX, i0 = (tile / ntx) * HIST_TY;
+    const int t = threadIdx.x;
+    const int xmax = min(d.w - 2, CELL * d.cx - 1);
+    const int ymax = min(d.h - 2, CELL * d.cy - 1);
+
+    // Stage rows Ys .. Ys+PY-1, columns Xs .. Xs+PX-1 (clipped to the image)
+    // with 16-byte cp.async copies of the aligned chunks covering them.  A
+    // 16-byte-aligned chunk holding at least one byte of the frame lies on
+    // that byte's memory page, so the copies stay in mapped memory even
+    // where they reach past the clipped range; those bytes are never read.
+    // xbase[r] = image column of staged byte 0 of staged row r.
+    const int Xs = CELL * j0 - 5, Ys = CELL * i0 - 5;
+    const int xa = max(Xs, 0), xb = min(Xs + PX, d.w);
+    for (int idx = t; idx < PY * NCH; idx += NT) {
+        const int r = idx / NCH, ci = idx - r * NCH;
+        const int Y = Ys + r;
+        if (Y < 0 || Y >= d.h || xa >= xb) continue;
+        const uintptr_t rp = (uintptr_t)(d.img + (size_t)Y * d.pitch);
+        const uintptr_t c0 = (rp + (uintptr_t)xa) & ~(uintptr_t)15;
+        const uintptr_t a = c0 + 16 * (uintptr_t)ci;
+        if (ci == 0) xbase[r] = (int)((intptr_t)c0 - (intptr_t)rp);
+        if (a <= rp + (uintptr_t)(xb - 1)) cp_async16(srcS + r * SROWB + 16 * ci, (const void *)a);
+    }
+    for (int k = t; k < 4 * NBIN * NT; k += NT) part[k] = 0.0f;
+    cp_async_wait_all();
+    __syncthreads();
+
+    // one 8x8 block per thread: pixels X = 8 bj - 4 + ox, Y = 8 bi - 4 + oy
+    const int by = t / HIST_BX, bx = t - by * HIST_BX;
+    const int X0 = CELL * (j0 + bx) - 4, Y0 = CELL * (i0 + by) - 4;
+    float *p0 = part + t;
+#pragma unroll 1
+    for (int oy = 0; oy < 8; oy++) {
+        const int Y = Y0 + oy;
+        if (Y < 1 || Y > ymax) continue;
+        const int r = Y - Ys;                       // staged row of Y
+        const uint8_t *up = srcS + (r - 1) * SROWB - xbase[r - 1];
+        const uint8_t *mid = srcS + r * SROWB - xbase[r];
+        const uint8_t *dn = srcS + (r + 1) * SROWB - xbase[r + 1];
+        const float wy1 = tent16(oy), wy0 = tent16(oy + 8);   // to cell rows bi, bi-1
+#pragma unroll
+        for (int ox = 0; ox < 8; ox++) {
+            const int X = X0 + ox;
+            if (X < 1 || X > xmax) continue;
+            const int dx = (int)mid[X + 1] - (int)mid[X - 1];
+            const int dy = (int)dn[X] - (int)up[X];
+            if ((dx | dy) == 0) continue;
+            const int b = orientation_bin_i(dx, dy);
+            const float m = sqrtf((float)(dx * dx + dy * dy));
+            const float wx1 = tent16(ox), wx0 = tent16(ox + 8);   // to cell cols bj, bj-1
+            float *pb = p0 + b * NT;
+            pb[0 * NBIN * NT] += m * (wy0 * wx0);   // cell (bi-1, bj-1)
+            pb[1 * NBIN * NT] += m * (wy0 * wx1);   // cell (bi-1, bj)
+            pb[2 * NBIN * NT] += m * (wy1 * wx0);   // cell (bi,   bj-1)
+            pb[3 * NBIN * NT] += m * (wy1 * wx1);   // cell (bi,   bj)
+        }
+    }
+    __syncthreads();
+
+    // cell (ci, cj) = blocks (ci,cj) corner 3 + (ci,cj+1) corner 2 + (ci+1,cj)
+    // corner 1 + (ci+1,cj+1) corner 0; staged for a coalesced store
+    float *outS = reinterpret_cast<float *>(srcS);   // [15*15][18] = 16,200 bytes
+    if (t < HIST_TX * HIST_TY) {
+        const int ci = t / HIST_TX, cj = t - ci * HIST_TX;
+        const int b00 = ci * HIST_BX + cj;
+#pragma unroll
+        for (int b = 0; b < NBIN; b++) {
+            const float s3 = part[(3 * NBIN + b) * NT + b00];
+            const float s2 = part[(2 * NBIN + b) * NT + b00 + 1];
+            const float s1 = part[(1 * NBIN + b) * NT + b00 + HIST_BX];
+            const float s0 = part[(0 * NBIN + b) * NT + b00 + HIST_BX + 1];
+            outS[t * NBIN + b] = (s3 + s2) + (s1 + s0);
+        }
+    }
+    __syncthreads();
+    const int ncol = min(HIST_TX, d.cx - j0);
+    for (int r = 0; r < HIST_TY; r++) {
+        const int i = i0 + r;
+        if (i >= d.cy) break;
+        float *dst = d.hist + ((size_t)i * d.cx + j0) * NBIN;
+        const float *srcr = outS + r * HIST_TX * NBIN;
+        for (int k = t; k < ncol * NBIN; k += NT) dst[k] = srcr[k];
+    }
+    __syncthreads();   // shared memory may be reused by the caller's next tile
+}
+
+// ===========================================================================
+// Energy, block normalisation, truncation, 31 features (Section 4.1.1:
+// normalisation and feature computation; the paper's energy and feature
+// kernels fused).  E = sum_{n<9} (h_n + h_{n+9})^2, zero outside the grid;
+// blocks k toward (-1,-1), (+1,-1), (-1,+1), (+1,+1); N_k = 1/sqrt(S_k+eps);
+//   f[o] = 1/2 sum_k min(h_o N_k, tau)                  o < 18
+//   f[18+o] = 1/2 sum_k min((h_o + h_{o+9}) N_k, tau)    o < 9
+//   f[27+k] = 0.2357 sum_o min(h_o N_k, tau)             k < 4
+// Output: internal layout [4][cy][cx][8] (channel 31 = 0) and optionally
+// the user layout [cy][cx][31].  256 threads, 32x8 cells.
+namespace feat_cfg {
+constexpr int HX = FEAT_TX + 2;   // 34 halo columns
+constexpr int HY = FEAT_TY + 2;   // 10 halo rows
+constexpr int CS = NBIN + 1;      // padded cell stride in shared memory
+constexpr int NT = FEAT_TX * FEAT_TY;
+constexpr size_t SMEM = sizeof(float) * (HY * HX * CS + HY * HX);   // 27,200
+}  // namespace feat_cfg
+
+template <bool COH>
+__device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float eps, float tau,
+                                          unsigned char *smem) {
+    using namespace feat_cfg;
+    float *hS = reinterpret_cast<float *>(smem);
+    float *eS = hS + HY * HX * CS;
+    const int ntx = (d.cx + FEAT_TX - 1) / FEAT_TX;
+    const int j0 = (tile % ntx) * FEAT_TX, i0 = (tile / ntx) * FEAT_TY;
+    const int t = threadIdx.x;
+
+    for (int k = t; k < HY * HX * NBIN; k += NT) {
+        const int r = k / (HX * NBIN);
+        const int rem = k - r * HX * NBIN;
+        const int c = rem / NBIN, b = rem - c * NBIN;
+        const int i = i0 - 1 + r, j = j0 - 1 + c;
+        float v = 0.0f;
+        if (i >= 0 && i < d.cy && j >= 0 && j < d.cx)
+            v = ld_in<COH>(d.hist + ((size_t)i * d.cx + j) * NBIN + b);
+        hS[(r * HX + c) * CS + b] = v;
+    }
+    __syncthreads();
+    for (int k = t; k < HY * HX; k += NT) {
+        const float *h = hS + k * CS;
+        float e = 0.0f;
+#pragma unroll
+        for (int n = 0; n < 9; n++) {
+            const float s = h[n] + h[n + 9];
+            e += s * s;
+        }
+        eS[k] = e;
+    }
+    __syncthreads();
+
+    const int ti = t / FEAT_TX, tj = t - ti * FEAT_TX;
+    const int i = i0 + ti, j = j0 + tj;
+    if (i < d.cy && j < d.cx) {
+        const int r = ti + 1, c = tj + 1;
+        const float *h = hS + (r * HX + c) * CS;
+        float hv[NBIN];
+#pragma unroll
+        for (int b = 0; b < NBIN; b++) hv[b] = h[b];
+        const float e00 = eS[r * HX + c];
+        const float S0 = e00 + eS[r * HX + c - 1] + eS[(r - 1) * HX + c] + eS[(r - 1) * HX + c - 1];
+        const float S1 = e00 + eS[r * HX + c + 1] + eS[(r - 1) * HX + c] + eS[(r - 1) * HX + c + 1];
+        const float S2 = e00 + eS[r * HX + c - 1] + eS[(r + 1) * HX + c] + eS[(r + 1) * HX + c - 1];
+        const float S3 = e00 + eS[r * HX + c + 1] + eS[(r + 1) * HX + c] + eS[(r + 1) * HX + c + 1];
+        const float N0 = 1.0f / sqrtf(S0 + eps), N1 = 1.0f / sqrtf(S1 + eps);
+        const float N2 = 1.0f / sqrtf(S2 + eps), N3 = 1.0f / sqrtf(S3 + eps);
+
+        float f[32];
+        float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+#pragma unroll
+        for (int o = 0; o < NBIN; o++) {
+            const float a0 = fminf(hv[o] * N0, tau), a1 = fminf(hv[o] * N1, tau);
+            const float a2 = fminf(hv[o] * N2, tau), a3 = fminf(hv[o] * N3, tau);
+            f[o] = 0.5f * (((a0 + a1) + a2) + a3);
+            t0 += a0; t1 += a1; t2 += a2; t3 += a3;
+        }
+#pragma unroll
+        for (int o = 0; o < 9; o++) {
+            const float s = hv[o] + hv[o + 9];
+            const float a0 = fminf(s * N0, tau), a1 = fminf(s * N1, tau);
+            const float a2 = fminf(s * N2, tau), a3 = fminf(s * N3, tau);
+            f[NBIN + o] = 0.5f * (((a0 + a1) + a2) + a3);
+        }
+        f[27] = 0.2357f * t0;
+        f[28] = 0.2357f * t1;
+        f[29] = 0.2357f * t2;
+        f[30] = 0.2357f * t3;
+        f[31] = 0.0f;
+
+        const size_t plane = (size_t)d.cy * d.cx * CHUNK;
+        const size_t cell = (size_t)i * d.cx + j;
+#pragma unroll
+        for (int ch = 0; ch < NCHUNK; ch++) {
+            float4 *dst = reinterpret_cast<float4 *>(d.feat + ch * plane + cell * CHUNK);
+            dst[0] = make_float4(f[8 * ch + 0], f[8 * ch + 1], f[8 * ch + 2], f[8 * ch + 3]);
+            dst[1] = make_float4(f[8 * ch + 4], f[8 * ch + 5], f[8 * ch + 6], f[8 * ch + 7]);
+        }
+        if (d.feat_user) {
+            float *u = d.feat_user + cell * NFEAT;
+#pragma unroll
+            for (int o = 0; o < NFEAT; o++) u[o] = f[o];
+        }
+    }
+    __syncthreads();   // shared memory may be reused by the caller's next tile
+}
+
+// ===========================================================================
+// Multi-filter correlation, threshold and candidate key of one warp tile
+// (Section 4.1.1: linear classification filter and detection; Section 5.1,
+// classifier and detection kernels fused).
+//
+// score_f(u, v) = sum_{a<10, b<10, c<31} W_f[a][b][c] feat[u+a][v+b][c].  A
+// window is a candidate when its best score over the filters is strictly
+// greater than the threshold; its key ranks (score desc, level, filter, u,
+// v).  Windows at one position share one box, so only the best filter of a
+// position can survive greedy suppression; the key carries that filter
+// (equal scores: the lowest index).
+//
+// One warp owns one tile of 128 windows (8x16, 4x32 or 16x8, chosen per
+// level on the host); a lane owns 4 consecutive windows of one row for all
+// filters.  Features stream in half-chunks of 4 channels (one float4 per
+// cell of the internal layout): the warp copies the (TU+9) x (TV+9) region
+// of the next half-chunk with cp.async.cg while computing the current one
+// (double buffer, 2 x CORR_BUF4 float4 of warp-private shared memory).  The
+// region's row stride TV+9 is odd, so a quarter-warp's float4 loads fall on
+// distinct bank groups.  For a filter row, a lane loads its 13 float4 once
+// and slides over the 10 filter columns in registers; filter weights are
+// warp-uniform loads through L1.
+constexpr int CORR_WPT = 4;
+constexpr int CORR_BUF4 = HOG_CORR_MINB >= 4 ? 432 : 544;   // 13x41 = 533 needs the 4x32 shape
+
+template <int NF>
+__device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ descs, Job jb,
+                                              const float *__restrict__ wchunks, int nf_real,
+                                              float threshold, float4 *buf0) {
+    const int lane = threadIdx.x & 31;
+    const LevelDesc &d = descs[jb.desc];
+    const int shape = (jb.tile >> 28) & 3, tile = jb.tile & 0x0fffffff;
+    const int TU = corr_tu(shape), TV = corr_tv(shape);
+    const int RU = TU + WIN - 1, RV = TV + WIN - 1;
+    const int ntv = (d.nv + TV - 1) / TV;
+    const int u0 = (tile / ntv) * TU, v0 = (tile % ntv) * TV;
+    const int lr = lane % TU, lc = (lane / TU) * CORR_WPT;   // window row / first column in tile
+
+    const float4 *feat4 = reinterpret_cast<const float4 *>(d.feat);
+    const size_t plane4 = (size_t)d.cy * d.cx * 2;           // float4 per chunk plane
+    const float4 *w4 = reinterpret_cast<const float4 *>(wchunks);
+
+    // copy half-chunk h (chunk h/2, channels 4*(h&1)..+3) of the tile region
+    auto stage = [&](int h, float4 *dst) {
+        const float4 *src = feat4 + (size_t)(h >> 1) * plane4 + (h & 1);
+        for (int k = lane; k < RU * RV; k += 32) {
+            const int rr = k / RV, cc = k - rr * RV;
+            const int i = u0 + rr, j = v0 + cc;
+            const bool ok = i < d.cy && j < d.cx;
+            cp_async16_zfill(dst + k, ok ? (const void *)(src + ((size_t)i * d.cx + j) * 2)
+                                         : (const void *)src, ok);
+        }
+        cp_async_commit();
+    };
+
+    float acc[CORR_WPT][NF];
+#pragma unroll
+    for (int j = 0; j < CORR_WPT; j++)
+#pragma unroll
+        for (int f = 0; f < NF; f++) acc[j][f] = 0.0f;
+
+    stage(0, buf0);
+#pragma unroll 1
+    for (int h = 0; h < 2 * NCHUNK; h++) {
+        float4 *cur = buf0 + (h & 1) * CORR_BUF4;
+        if (h + 1 < 2 * NCHUNK) {
+            stage(h + 1, buf0 + ((h + 1) & 1) * CORR_BUF4);
+            cp_async_wait_group<1>();
+        } else {
+            cp_async_wait_group<0>();
+        }
+        __syncwarp();
+        const int ch = h >> 1, c4 = h & 1;
+        const float4 *wch = w4 + (size_t)ch * NF * 200 + c4;
+#pragma unroll 1
+        for (int a = 0; a < WIN; a++) {
+            const float4 *frow = cur + (lr + a) * RV + lc;
+            float4 fv[CORR_WPT + WIN - 1];
+#pragma unroll
+            for (int j = 0; j < CORR_WPT + WIN - 1; j++) fv[j] = frow[j];
+#pragma unroll
+            for (int b = 0; b < WIN; b++) {
+                float4 wv[NF];
+#pragma unroll
+                for (int f = 0; f < NF; f++) wv[f] = __ldg(wch + ((f * WIN + a) * WIN + b) * 2);
+#pragma unroll
+                for (int j = 0; j < CORR_WPT; j++) {
+                    const float4 x = fv[j + b];
+#pragma unroll
+                    for (int f = 0; f < NF; f++) {
+                        float s = acc[j][f];
+                        s = fmaf(wv[f].x, x.x, s);
+                        s = fmaf(wv[f].y, x.y, s);
+                        s = fmaf(wv[f].z, x.z, s);
+                        s = fmaf(wv[f].w, x.w, s);
+                        acc[j][f] = s;
+                    }
+                }
+            }
+        }
+        __syncwarp();   // every lane is done with `cur` before it is refilled
+    }
+
+    const int u = u0 + lr;
+    if (u >= d.nu) return;
+#pragma unroll
+    for (int j = 0; j < CORR_WPT; j++) {
+        const int v = v0 + lc + j;
+        if (v >= d.nv) break;
+        float best = acc[j][0];
+        int fb = 0;
+#pragma unroll
+        for (int f = 1; f < NF; f++)
+            if (f < nf_real && acc[j][f] > best) { best = acc[j][f]; fb = f; }
+        if (d.scores_user) {
+#pragma unroll
+            for (int f = 0; f < NF; f++)
+                if (f < nf_real)
+                    d.scores_user[((size_t)f * d.nu + u) * d.nv + v] = acc[j][f];
+        }
+        if (d.keys)
+            d.keys[(size_t)u * d.nv + v] =
+                (d.scan && best > threshold) ? make_key(best, d.level, fb, u, v) : KEY_NONE;
+    }
+}
+
+// ===========================================================================
+// Non-maximum suppression of one frame (Section 4.1.1, last step).
+//
+// Greedy definition: rank candidates by (score desc, level, filter, u, v);
+// keep a box unless a kept, higher-ranked box overlaps it with IoU >
+// nms_iou.  The greedy result is the unique set K with "p in K iff no member
+// of K ranked above p overlaps p", reached here by rounds in which every
+// undecided candidate looks at its higher-ranked overlapping neighbours: one
+// of them kept -> suppressed; all of them suppressed -> kept; otherwise it
+// waits.  The best undecided candidate always decides, so the rounds end
+// (about ten rounds on 640x480 frames); decisions are final, so a thread may
+// read a neighbour's state while it changes within a round.
+//
+// Overlap lists (IoU > nms_iou, FP64) come from the per-frame-size geometry
+// in slot-major order nbr[s * npos + p]: one thread per candidate, so a
+// warp's load of slot s reads consecutive entries, and eight slots are
+// loaded before they are used.  Each round walks a compacted list of the
+// still-undecided candidates, so sparse late rounds cost little.  Ranks compare the key's high word (the
+// score order) held in shared memory; equal high words fall back to the full
+// key in global memory.  Workspace: 5 bytes per window position, in shared
+// memory (SM) or in fd.ws.  NT threads.
+constexpr uint8_t NMS_ALIVE = 1, NMS_KEPT = 2, NMS_DEAD = 0;
+constexpr uint32_t NMS_NOKEY = 0xffffffffu;   // key high word of a non-candidate
+
+struct WinBox {
+    double x, y, w, h;
+};
+
+__device__ __forceinline__ WinBox window_box(int W0, int H0, int Wl, int Hl, int u, int v) {
+    const double rx = __ddiv_rn((double)W0, (double)Wl);
+    const double ry = __ddiv_rn((double)H0, (double)Hl);
+    WinBox b;
+    b.x = __dmul_rn((double)(CELL * v), rx);
+    b.y = __dmul_rn((double)(CELL * u), ry);
+    b.w = __dmul_rn((double)(CELL * WIN), rx);
+    b.h = __dmul_rn((double)(CELL * WIN), ry);
+    return b;
+}
+
+__host__ __device__ constexpr size_t nms_ws_bytes(int npos) { return (size_t)npos * 13 + 64; }
+
+template <bool SM, int NT, bool COH>
+__device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *smem, int *flags,
+                                          int *sh /* NT/32 + 4 ints of shared memory */) {
+    const int t = threadIdx.x;
+    const int npos = fd.npos;
+    unsigned char *base = SM ? smem : reinterpret_cast<unsigned char *>(fd.ws);
+    uint32_t *khi = reinterpret_cast<uint32_t *>(base);              // key high words
+    int32_t *list[2] = {reinterpret_cast<int32_t *>(base) + npos,    // undecided candidates,
+                        reinterpret_cast<int32_t *>(base) + 2 * (size_t)npos};   // double buffer
+    volatile uint8_t *state = base + (size_t)npos * 12;
+    const uint64_t *gkeys = fd.keys;
+    const int32_t *__restrict__ nbr = fd.nbr;                        // [slot][npos]
+    const uint8_t *__restrict__ nbr_cnt = fd.nbr_cnt;
+    const int lane = t & 31;
+    int *s_n = sh + NT / 32 + 1;                                     // list sizes [2]
+
+    // q ranked above p (smaller key)
+    auto above = [&](int q, int p, uint32_t hq, uint32_t hp) -> bool {
+        if (hq != hp) return hq < hp;
+        return ld_in<COH>(gkeys + q) < ld_in<COH>(gkeys + p);
+    };
+    // warp-aggregated append of p (when flag) to list[which]
+    auto append = [&](bool flag, int p, int which) {
+        const unsigned m = __ballot_sync(0xffffffffu, flag);
+        if (!m) return;
+        int b0 = 0;
+        if (lane == __ffs(m) - 1) b0 = atomicAdd(s_n + which, __popc(m));
+        b0 = __shfl_sync(0xffffffffu, b0, __ffs(m) - 1);
+        if (flag) list[which][b0 + __popc(m & ((1u << lane) - 1))] = p;
+    };
+
+    if (t == 0) { s_n[0] = 0; s_n[1] = 0; }
+    __syncthreads();
+    for (int p0 = 0; p0 < npos; p0 += NT) {          // whole warps iterate together
+        const int p = p0 + t;
+        uint32_t h = NMS_NOKEY;
+        if (p < npos) {
+            h = (uint32_t)(ld_in<COH>(gkeys + p) >> 32);
+            khi[p] = h;
+            state[p] = h != NMS_NOKEY ? NMS_ALIVE : NMS_DEAD;
+        }
+        append(h != NMS_NOKEY, p, 0);
+    }
+    __syncthreads();
+
+    int cur = 0, round = 0;
+    for (; round <= npos; round++) {
+        const int n_cur = s_n[cur];
+        if (n_cur == 0) break;
+        if (t == 0) s_n[cur ^ 1] = 0;
+        __syncthreads();
+        for (int i0 = 0; i0 < n_cur; i0 += NT) {     // whole warps iterate together
+            const int i = i0 + t;
+            bool undecided = false;
+            int p = -1;
+            if (i < n_cur) {
+                p = list[cur][i];
+                const uint32_t hp = khi[p];
+                const int n = __ldg(nbr_cnt + p);
+                bool dead = false, wait = false;
+                for (int s0 = 0; s0 < n && !dead; s0 += 8) {
+                    int q[8];
+#pragma unroll
+                    for (int k = 0; k < 8; k++)
+                        q[k] = s0 + k < n ? __ldg(nbr + (size_t)(s0 + k) * npos + p) : -1;
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        if (q[k] < 0) continue;
+                        const uint32_t hq = khi[q[k]];
+                        if (hq == NMS_NOKEY || !above(q[k], p, hq, hp)) continue;
+                        const uint8_t sq = state[q[k]];
+                        if (sq == NMS_KEPT) dead = true;
+                        else if (sq == NMS_ALIVE) wait = true;
+                    }
+                }
+                if (dead) state[p] = NMS_DEAD;
+                else if (!wait) state[p] = NMS_KEPT;
+                else undecided = true;
+            }
+            append(undecided, p, cur ^ 1);
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+
+    // compact kept positions in position order
+    const int wid = t >> 5;
+    int *s_total = sh + NT / 32;
+    const int per = (npos + NT - 1) / NT;
+    const int beg = min(t * per, npos), end = min(beg + per, npos);
+    int mine = 0;
+    for (int p = beg; p < end; p++) mine += state[p] == NMS_KEPT;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh[wid] = incl;
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int k = 0; k < NT / 32; k++) {
+            const int x = sh[k];
+            sh[k] = run;
+            run += x;
+        }
+        *s_total = run;
+    }
+    __syncthreads();
+    const int total = *s_total;
+    int pos = sh[wid] + incl - mine;
+    for (int p = beg; p < end; p++) {
+        if (state[p] != NMS_KEPT) continue;
+        if (pos < fd.out_cap) {
+            const uint64_t k = ld_in<COH>(gkeys + p);
+            const int l = key_level(k);
+            const int u = key_u(k), v = key_v(k);
+            const WinBox b = window_box(fd.W, fd.H, fd.lev_w[l], fd.lev_h[l], u, v);
+            hog_det det;
+            det.frame = fd.frame;
+            det.level = l;
+            det.filter = key_filter(k);
+            det.u = u;
+            det.v = v;
+            det.score = key_score(k);
+            det.x = b.x; det.y = b.y; det.w = b.w; det.h = b.h;
+            fd.out[pos] = det;
+        }
+        pos++;
+    }
+    if (t == 0) {
+        *fd.count = total;
+        if (total > fd.out_cap) atomicOr(flags, 1);
+        atomicMax(flags + 1, round + 1);
+    }
+    __syncthreads();   // shared memory may be reused by the caller's next item
+}
+
+}  // namespace hogk

@@ -47,7 +47,7 @@ class StageStat(C.Structure):
     _fields_ = [("ms", C.c_double), ("launches", C.c_int64), ("units", C.c_int64)]
 
 
-STAGES = ("pyramid", "hist", "feat", "corr", "nms")
+STAGES = ("pyramid", "hist", "feat", "corr", "nms", "fused")
 
 
 class Level(C.Structure):
@@ -73,6 +73,10 @@ _SIGS = {
     "hog_scores": (C.c_int, [_vp, _P(Frame), _vp, C.c_size_t, _P(Level), _i32, _P(_i32), _vp]),
     "hog_detect": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
     "hog_detect_host": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
+    "hog_detect_batched": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
+    "hog_set_batched_mode": (C.c_int, [_vp, _i32]),
+    "hog_autotune": (C.c_int, [_vp, _P(Frame), _i32, C.c_char_p, _vp]),
+    "hog_get_tuning": (C.c_int, [_vp, _P(_i32), _P(_i32)]),
     "hog_features_static": (C.c_int, [_P(Params), _P(Frame), _vp, C.c_size_t, _P(Level), _i32,
                                       _P(_i32), C.c_char_p, C.c_size_t, _vp]),
     "hog_set_profiling": (C.c_int, [_vp, _i32]),
@@ -197,6 +201,23 @@ class Detector:
         self._check(_lib.hog_stage_stats(self._h, st, len(STAGES), int(bool(reset))))
         return {n: (st[i].ms, st[i].launches, st[i].units) for i, n in enumerate(STAGES)}
 
+    def set_batched_mode(self, mode):
+        """1: persistent fused launch, 0: one launch per stage."""
+        self._check(_lib.hog_set_batched_mode(self._h, int(mode)))
+
+    def autotune(self, frames, cache_path=None, stream=None):
+        """Run the autotuner on a sample batch of device frames; returns
+        (batched_mode, corr_policy)."""
+        arr = (Frame * len(frames))(*[_frame_of(f) for f in frames])
+        path = cache_path.encode() if cache_path else None
+        self._check(_lib.hog_autotune(self._h, arr, len(frames), path, _stream_ptr(stream)))
+        return self.tuning()
+
+    def tuning(self):
+        m, p = _i32(0), _i32(0)
+        self._check(_lib.hog_get_tuning(self._h, C.byref(m), C.byref(p)))
+        return m.value, p.value
+
     def set_filters(self, filters):
         w = np.ascontiguousarray(np.asarray(filters, dtype=np.float32))
         self._check(_lib.hog_set_filters(self._h, w.ctypes.data_as(_vp), w.shape[0]))
@@ -253,11 +274,14 @@ class Detector:
             res.append(out[lv[i].offset:lv[i].offset + F * nu * nv].view(F, nu, nv))
         return res
 
-    def detect(self, frames, det_cap=None, stream=None, allow_capacity=False, out=None):
+    def detect(self, frames, det_cap=None, stream=None, allow_capacity=False, out=None,
+               batched=False):
         """Detect on a list of device uint8 frames.  Returns (dets, counts):
         dets a numpy structured array (DET_DTYPE), counts int32 per frame.
         With ``out`` (a DET_DTYPE array, e.g. a view of pinned memory, which
-        the device then fills directly), dets is a view of ``out``."""
+        the device then fills directly), dets is a view of ``out``.
+        ``batched``: hog_detect_batched (persistent fused launch, graphs)."""
+        fn = _lib.hog_detect_batched if batched else _lib.hog_detect
         n = len(frames)
         arr = (Frame * max(n, 1))(*[_frame_of(f) for f in frames])
         if out is not None:
@@ -269,8 +293,8 @@ class Detector:
                 det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
             dets = np.empty(max(det_cap, 1), DET_DTYPE)
         counts = np.zeros(max(n, 1), np.int32)
-        rc = _lib.hog_detect(self._h, arr, n, dets.ctypes.data_as(_vp), det_cap,
-                             counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
+        rc = fn(self._h, arr, n, dets.ctypes.data_as(_vp), det_cap,
+                counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
         self._check(rc, allow=(HOG_ECAPACITY,) if allow_capacity else ())
         total = min(int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum()), det_cap)
         if out is not None:

@@ -129,10 +129,13 @@ def _kept_set(rows):
                    float(np.float32(r["score"]))) for r in rows)
 
 
-@pytest.mark.parametrize("case", ["cfg1", "eyeblink5", "skip1"])
+@pytest.mark.parametrize("case", ["cfg1", "eyeblink5", "skip1", "hd720"])
 def test_nms_exact_on_gpu_scores(H, oracle, synth, case):
+    """hd720 has 35k window positions: its workspace lives in global memory."""
     if case == "cfg1":
         f, W, skip = synth.single_frame(320, 240), synth.filters(1, config=1), 0
+    elif case == "hd720":
+        f, W, skip = synth.eyeblink_frame(2, 1280, 720, config=3), synth.filters(5), 0
     else:
         f, W = synth.eyeblink_frame(7), synth.filters(5)
         skip = 1 if case == "skip1" else 0
