@@ -81,6 +81,9 @@ def lib():
             "hgo_detect": (i, [u8p, i, i, i, i, i, d, d, d, d, dp, i, P(Det), i, i32p]),
             "hgo_detect_many": (i, [u8p, i, sz, i, i, i, i, i, d, d, d, d, dp, i, P(Det), i,
                                     i32p, i]),
+            "hgo_hinge_loss": (d, [dp, i, i, i, dp, i, d, d, dp, dp, i32p]),
+            "hgo_hinge_backward": (d, [dp, i, i, i, dp, i, d, d, dp, dp, dp]),
+            "hgo_forward_signature": (C.c_uint64, [dp, i, i, i, d, d, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -289,3 +292,43 @@ def detect_many(frames, filt, n_threads=1, min_size=80, skip_levels=0, eps=EPS, 
     res = [out[i * cap_per_frame:i * cap_per_frame + min(counts[i], cap_per_frame)].copy()
            for i in range(n)]
     return res, used
+
+
+# --------------------------------------------------------------------------
+# training adjoint (float pyramid, hinge loss on the best window of a filter)
+
+
+def hinge_loss(imgs, labels, filt, min_size=80, eps=EPS, tau=TAU):
+    """(loss, best scores [n], best windows [n, 3] as (level, u, v))."""
+    imgs = np.ascontiguousarray(imgs, dtype=np.float64)
+    labels = np.ascontiguousarray(labels, dtype=np.float64)
+    filt = np.ascontiguousarray(filt, dtype=np.float64).reshape(10, 10, 31)
+    n, h, w = imgs.shape
+    sc = np.zeros(n, np.float64)
+    win = np.zeros((n, 3), np.int32)
+    loss = lib().hgo_hinge_loss(_p(imgs, C.c_double), n, w, h, _p(labels, C.c_double), min_size,
+                                eps, tau, _p(filt, C.c_double), _p(sc, C.c_double),
+                                _p(win, C.c_int32))
+    return loss, sc, win
+
+
+def hinge_backward(imgs, labels, filt, min_size=80, eps=EPS, tau=TAU, with_image=True):
+    """(loss, dW [10,10,31], dI [n,h,w] or None)."""
+    imgs = np.ascontiguousarray(imgs, dtype=np.float64)
+    labels = np.ascontiguousarray(labels, dtype=np.float64)
+    filt = np.ascontiguousarray(filt, dtype=np.float64).reshape(10, 10, 31)
+    n, h, w = imgs.shape
+    dW = np.zeros((10, 10, 31), np.float64)
+    dI = np.zeros((n, h, w), np.float64) if with_image else None
+    loss = lib().hgo_hinge_backward(_p(imgs, C.c_double), n, w, h, _p(labels, C.c_double),
+                                    min_size, eps, tau, _p(filt, C.c_double), _p(dW, C.c_double),
+                                    _p(dI, C.c_double) if with_image else None)
+    return loss, dW, dI
+
+
+def forward_signature(img, filt, min_size=80, eps=EPS, tau=TAU):
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    filt = np.ascontiguousarray(filt, dtype=np.float64).reshape(10, 10, 31)
+    h, w = img.shape
+    return lib().hgo_forward_signature(_p(img, C.c_double), w, h, min_size, eps, tau,
+                                       _p(filt, C.c_double))

@@ -518,3 +518,277 @@ int hgo_detect_many(const uint8_t *frames, int n_frames, size_t frame_bytes, int
 #endif
     return used;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Training adjoint (hinge loss on the best window score of one filter).
+ *
+ * Float mode: the pyramid is real-valued (hgo_downscale_f64, no rounding).
+ * For crop i with label y_i in {-1, +1}: s_i = max over all windows of all
+ * levels of the filter's score (ties: the first in (level, u, v) order);
+ * L = (1/B) sum_i max(0, 1 - y_i s_i), subgradient 0 at the kink.
+ * dL/dW = (1/B) sum_{active i} (-y_i) feat_i[window_i]; dL/dI follows the
+ * chain feature -> (truncation, N_k(S_k), E) -> histogram -> magnitude ->
+ * central differences -> pyramid, with orientation bins, the argmax window,
+ * the truncation set (min(x, tau) passes the gradient iff x < tau) and the
+ * hinge activity held fixed.                                               */
+
+typedef struct {
+    int L;
+    int ws[64], hs[64];
+    double *pyr;            /* all levels, [h_l][w_l] back to back */
+    size_t off[64];
+} hgo_fpyr;
+
+static void fpyr_build(const double *img, int w, int h, int min_size, hgo_fpyr *P)
+{
+    P->L = hgo_level_sizes(w, h, min_size, P->ws, P->hs, 64);
+    size_t n = 0;
+    for (int l = 0; l < P->L; l++) { P->off[l] = n; n += (size_t)P->ws[l] * P->hs[l]; }
+    P->pyr = (double *)malloc(sizeof(double) * (n + 1));
+    if (P->L > 0) hgo_pyramid_f64(img, w, h, min_size, P->pyr, n);
+}
+
+/* Best window of one filter over all levels (float mode). Returns s. */
+static double best_window(const hgo_fpyr *P, double eps, double tau, const double *filt,
+                          int *bl, int *bu, int *bv)
+{
+    double best = 0.0;
+    int have = 0;
+    *bl = *bu = *bv = -1;
+    for (int l = 0; l < P->L; l++) {
+        int w = P->ws[l], h = P->hs[l], cx = w / CELL, cy = h / CELL;
+        int nu = cy - WIN + 1, nv = cx - WIN + 1;
+        if (nu <= 0 || nv <= 0) continue;
+        double *hist = (double *)malloc(sizeof(double) * ((size_t)cx * cy * NBIN + 1));
+        double *feat = (double *)malloc(sizeof(double) * ((size_t)cx * cy * NFEAT + 1));
+        double *sc = (double *)malloc(sizeof(double) * ((size_t)nu * nv + 1));
+        hgo_cell_hist(P->pyr + P->off[l], w, h, hist);
+        hgo_features(hist, cx, cy, eps, tau, feat);
+        hgo_correlate(feat, cx, cy, filt, 1, sc);
+        for (int u = 0; u < nu; u++)
+            for (int v = 0; v < nv; v++) {
+                double s = sc[(size_t)u * nv + v];
+                if (!have || s > best) { best = s; have = 1; *bl = l; *bu = u; *bv = v; }
+            }
+        free(hist); free(feat); free(sc);
+    }
+    return best;
+}
+
+/* Forward only: loss of a batch (float mode), best scores and windows. */
+double hgo_hinge_loss(const double *imgs, int n, int w, int h, const double *labels, int min_size,
+                      double eps, double tau, const double *filt, double *scores, int32_t *wins)
+{
+    double loss = 0.0;
+    for (int i = 0; i < n; i++) {
+        hgo_fpyr P;
+        fpyr_build(imgs + (size_t)i * w * h, w, h, min_size, &P);
+        int l, u, v;
+        double s = best_window(&P, eps, tau, filt, &l, &u, &v);
+        if (scores) scores[i] = s;
+        if (wins) { wins[3 * i] = l; wins[3 * i + 1] = u; wins[3 * i + 2] = v; }
+        double m = 1.0 - labels[i] * s;
+        if (l >= 0 && m > 0.0) loss += m;
+        free(P.pyr);
+    }
+    return loss / n;
+}
+
+/* Loss, dL/dW (3100, [a][b][c]) and optionally dL/dI ([n][h][w]). */
+double hgo_hinge_backward(const double *imgs, int n, int w, int h, const double *labels,
+                          int min_size, double eps, double tau, const double *filt,
+                          double *dW, double *dI)
+{
+    double loss = 0.0;
+    memset(dW, 0, sizeof(double) * WIN * WIN * NFEAT);
+    if (dI) memset(dI, 0, sizeof(double) * (size_t)n * w * h);
+    static const int bdx[4] = {-1, +1, -1, +1};
+    static const int bdy[4] = {-1, -1, +1, +1};
+    for (int i = 0; i < n; i++) {
+        hgo_fpyr P;
+        fpyr_build(imgs + (size_t)i * w * h, w, h, min_size, &P);
+        int l, u0, v0;
+        double s = best_window(&P, eps, tau, filt, &l, &u0, &v0);
+        double m = 1.0 - labels[i] * s;
+        if (l < 0 || !(m > 0.0)) { free(P.pyr); continue; }
+        loss += m;
+        const double g = -labels[i] / n;       /* dL/ds_i */
+        int lw = P.ws[l], lh = P.hs[l], cx = lw / CELL, cy = lh / CELL;
+        const double *img = P.pyr + P.off[l];
+        double *hist = (double *)malloc(sizeof(double) * ((size_t)cx * cy * NBIN + 1));
+        double *feat = (double *)malloc(sizeof(double) * ((size_t)cx * cy * NFEAT + 1));
+        hgo_cell_hist(img, lw, lh, hist);
+        hgo_features(hist, cx, cy, eps, tau, feat);
+        for (int a = 0; a < WIN; a++)
+            for (int b = 0; b < WIN; b++)
+                for (int c = 0; c < NFEAT; c++)
+                    dW[(a * WIN + b) * NFEAT + c] +=
+                        g * feat[((size_t)(u0 + a) * cx + (v0 + b)) * NFEAT + c];
+        if (dI) {
+            /* energies and normalisers of every cell */
+            double *E = (double *)calloc((size_t)cx * cy + 1, sizeof(double));
+            for (int c = 0; c < cx * cy; c++) {
+                const double *hc = hist + (size_t)c * NBIN;
+                for (int o = 0; o < 9; o++) E[c] += (hc[o] + hc[o + 9]) * (hc[o] + hc[o + 9]);
+            }
+            double *dh = (double *)calloc((size_t)cx * cy * NBIN + 1, sizeof(double));
+            double *dE = (double *)calloc((size_t)cx * cy + 1, sizeof(double));
+            for (int a = 0; a < WIN; a++)
+                for (int b = 0; b < WIN; b++) {
+                    int ci = u0 + a, cj = v0 + b;
+                    const double *hc = hist + ((size_t)ci * cx + cj) * NBIN;
+                    const double *Wc = filt + (a * WIN + b) * NFEAT;
+                    double *dhc = dh + ((size_t)ci * cx + cj) * NBIN;
+                    double S[4], N[4], dN[4] = {0, 0, 0, 0};
+                    for (int k = 0; k < 4; k++) {
+                        S[k] = energy_at(E, cx, cy, ci, cj) + energy_at(E, cx, cy, ci, cj + bdx[k])
+                             + energy_at(E, cx, cy, ci + bdy[k], cj)
+                             + energy_at(E, cx, cy, ci + bdy[k], cj + bdx[k]);
+                        N[k] = 1.0 / sqrt(S[k] + eps);
+                    }
+                    for (int o = 0; o < NBIN; o++)
+                        for (int k = 0; k < 4; k++)
+                            if (hc[o] * N[k] < tau) {
+                                double coef = 0.5 * g * Wc[o] + TEXTURE_W * g * Wc[27 + k];
+                                dhc[o] += coef * N[k];
+                                dN[k] += coef * hc[o];
+                            }
+                    for (int o = 0; o < 9; o++) {
+                        double su = hc[o] + hc[o + 9];
+                        for (int k = 0; k < 4; k++)
+                            if (su * N[k] < tau) {
+                                double coef = 0.5 * g * Wc[NBIN + o];
+                                dhc[o] += coef * N[k];
+                                dhc[o + 9] += coef * N[k];
+                                dN[k] += coef * su;
+                            }
+                    }
+                    for (int k = 0; k < 4; k++) {
+                        double dS = dN[k] * (-0.5) * pow(S[k] + eps, -1.5);
+                        int cells[4][2] = {{ci, cj}, {ci, cj + bdx[k]}, {ci + bdy[k], cj},
+                                           {ci + bdy[k], cj + bdx[k]}};
+                        for (int q = 0; q < 4; q++) {
+                            int ii = cells[q][0], jj = cells[q][1];
+                            if (ii >= 0 && jj >= 0 && ii < cy && jj < cx) dE[(size_t)ii * cx + jj] += dS;
+                        }
+                    }
+                }
+            for (int c = 0; c < cx * cy; c++) {
+                if (dE[c] == 0.0) continue;
+                const double *hc = hist + (size_t)c * NBIN;
+                for (int o = 0; o < 9; o++) {
+                    double t2 = 2.0 * dE[c] * (hc[o] + hc[o + 9]);
+                    dh[(size_t)c * NBIN + o] += t2;
+                    dh[(size_t)c * NBIN + o + 9] += t2;
+                }
+            }
+            /* histogram -> magnitude -> central differences -> level pixels */
+            size_t npx = 0;
+            for (int q = 0; q <= l; q++) npx += (size_t)P.ws[q] * P.hs[q];
+            double *dP = (double *)calloc(npx + 1, sizeof(double));
+            double *dl = dP + P.off[l];
+            int xmax = lw - 2 < CELL * cx - 1 ? lw - 2 : CELL * cx - 1;
+            int ymax = lh - 2 < CELL * cy - 1 ? lh - 2 : CELL * cy - 1;
+            for (int y = 1; y <= ymax; y++)
+                for (int x = 1; x <= xmax; x++) {
+                    double dx = img[y * lw + x + 1] - img[y * lw + x - 1];
+                    double dy = img[(y + 1) * lw + x] - img[(y - 1) * lw + x];
+                    int bb = hgo_orientation_bin(dx, dy);
+                    if (bb < 0) continue;
+                    double mag = sqrt(dx * dx + dy * dy);
+                    double xp = (x + 0.5) / CELL - 0.5, yp = (y + 0.5) / CELL - 0.5;
+                    int ix = (int)floor(xp), iy = (int)floor(yp);
+                    double ax = xp - ix, ay = yp - iy, dmag = 0.0;
+                    for (int di = 0; di < 2; di++) {
+                        int ii = iy + di;
+                        if (ii < 0 || ii >= cy) continue;
+                        double wy = di ? ay : 1.0 - ay;
+                        for (int dj = 0; dj < 2; dj++) {
+                            int jj = ix + dj;
+                            if (jj < 0 || jj >= cx) continue;
+                            double wx = dj ? ax : 1.0 - ax;
+                            dmag += wx * wy * dh[((size_t)ii * cx + jj) * NBIN + bb];
+                        }
+                    }
+                    if (dmag == 0.0) continue;
+                    double ddx = dmag * dx / mag, ddy = dmag * dy / mag;
+                    dl[y * lw + x + 1] += ddx;
+                    dl[y * lw + x - 1] -= ddx;
+                    dl[(y + 1) * lw + x] += ddy;
+                    dl[(y - 1) * lw + x] -= ddy;
+                }
+            /* pyramid transpose: level q+1 pixel = sum of 4 taps of level q / 100 */
+            for (int q = l - 1; q >= 0; q--) {
+                int w1 = P.ws[q + 1], h1 = P.hs[q + 1], w0 = P.ws[q];
+                const double *d1 = dP + P.off[q + 1];
+                double *d0 = dP + P.off[q];
+                for (int y = 0; y < h1; y++) {
+                    int Y = 12 * y + 1, y0 = Y / 10, fy = Y % 10;
+                    for (int x = 0; x < w1; x++) {
+                        int X = 12 * x + 1, x0 = X / 10, fx = X % 10;
+                        double gpx = d1[(size_t)y * w1 + x] / 100.0;
+                        if (gpx == 0.0) continue;
+                        d0[(size_t)y0 * w0 + x0] += (10 - fx) * (10 - fy) * gpx;
+                        d0[(size_t)y0 * w0 + x0 + 1] += fx * (10 - fy) * gpx;
+                        d0[(size_t)(y0 + 1) * w0 + x0] += (10 - fx) * fy * gpx;
+                        d0[(size_t)(y0 + 1) * w0 + x0 + 1] += fx * fy * gpx;
+                    }
+                }
+            }
+            double *di_out = dI + (size_t)i * w * h;
+            for (size_t k = 0; k < (size_t)w * h; k++) di_out[k] = dP[k];
+            free(dP); free(dE); free(dh); free(E);
+        }
+        free(hist); free(feat);
+        free(P.pyr);
+    }
+    return loss / n;
+}
+
+/* Discrete state of a crop's forward pass: argmax window, orientation bins
+ * of the argmax level, truncation flags of the window cells -- as a hash,
+ * so a finite-difference test can skip perturbations that change it.      */
+uint64_t hgo_forward_signature(const double *img, int w, int h, int min_size, double eps,
+                               double tau, const double *filt)
+{
+    hgo_fpyr P;
+    fpyr_build(img, w, h, min_size, &P);
+    int l, u0, v0;
+    best_window(&P, eps, tau, filt, &l, &u0, &v0);
+    uint64_t hsh = 1469598103934665603ull;
+#define MIX(x) do { hsh ^= (uint64_t)(int64_t)(x); hsh *= 1099511628211ull; } while (0)
+    MIX(l); MIX(u0); MIX(v0);
+    if (l >= 0) {
+        int lw = P.ws[l], lh = P.hs[l], cx = lw / CELL, cy = lh / CELL;
+        const double *img2 = P.pyr + P.off[l];
+        for (int y = 1; y < lh - 1; y++)
+            for (int x = 1; x < lw - 1; x++)
+                MIX(hgo_orientation_bin(img2[y * lw + x + 1] - img2[y * lw + x - 1],
+                                        img2[(y + 1) * lw + x] - img2[(y - 1) * lw + x]));
+        double *hist = (double *)malloc(sizeof(double) * ((size_t)cx * cy * NBIN + 1));
+        hgo_cell_hist(img2, lw, lh, hist);
+        double *E = (double *)calloc((size_t)cx * cy + 1, sizeof(double));
+        for (int c = 0; c < cx * cy; c++)
+            for (int o = 0; o < 9; o++) E[c] += (hist[c * NBIN + o] + hist[c * NBIN + o + 9]) *
+                                                (hist[c * NBIN + o] + hist[c * NBIN + o + 9]);
+        static const int bdx[4] = {-1, +1, -1, +1};
+        static const int bdy[4] = {-1, -1, +1, +1};
+        for (int a = 0; a < WIN; a++)
+            for (int b = 0; b < WIN; b++) {
+                int ci = u0 + a, cj = v0 + b;
+                const double *hc = hist + ((size_t)ci * cx + cj) * NBIN;
+                for (int k = 0; k < 4; k++) {
+                    double S = energy_at(E, cx, cy, ci, cj) + energy_at(E, cx, cy, ci, cj + bdx[k])
+                             + energy_at(E, cx, cy, ci + bdy[k], cj)
+                             + energy_at(E, cx, cy, ci + bdy[k], cj + bdx[k]);
+                    double N = 1.0 / sqrt(S + eps);
+                    for (int o = 0; o < NBIN; o++) MIX(hc[o] * N < tau);
+                    for (int o = 0; o < 9; o++) MIX((hc[o] + hc[o + 9]) * N < tau);
+                }
+            }
+        free(hist); free(E);
+    }
+#undef MIX
+    free(P.pyr);
+    return hsh;
+}
