@@ -218,6 +218,26 @@ int hog_features_static(const hog_params *p, const hog_frame *frame, float *feat
                         size_t cap_floats, hog_level *levels, int32_t cap_levels,
                         int32_t *n_levels, char *err, size_t err_cap, void *stream);
 
+/* Training adjoint (the paper's filters are trained offline with Dlib; this
+ * entry point has no counterpart there): for n crops images (device float
+ * [n][h][w], 8-bit values as floats), labels (device float [n], +1 / -1) and
+ * one filter weights (device float [10][10][31], layout [row][col][channel]),
+ * the hinge loss on each crop's best window score,
+ *   L = (1/n) sum_i max(0, 1 - y_i s_i),  s_i = max over all windows of all
+ *   levels (ties: the first in (level, u, v) order),
+ * computed on a real-valued pyramid (the same exact bilinear weights, no
+ * rounding) with orientation bins from the largest |dot| with the 9
+ * unsigned directions.  Writes dL/dW (device float [10][10][31]) and, if dI
+ * is not NULL, dL/dI (device float [n][h][w]), holding bins, best windows,
+ * truncation set and hinge activity fixed (subgradient 0 at every kink);
+ * *loss (host, may be NULL) gets L.  recompute = 1 rebuilds the best
+ * window's histograms from the pyramid in the adjoint instead of reading
+ * the forward's (same result).  Synchronises the stream when loss != NULL.
+ * Deterministic: every reduction is a fixed-order gather. */
+int hog_backward(hog_ctx *ctx, const float *images, int32_t n, int32_t w, int32_t h,
+                 const float *labels, const float *weights, float *dW, float *dI, float *loss,
+                 int32_t recompute, void *stream);
+
 /* ---- stage timing (tracing; no counterpart in the paper, which reads its
  * kernel times from a profiler, Section 5.1) ------------------------------ */
 #define HOG_NSTAGES 6   /* 0 pyramid, 1 gradient+histogram, 2 normalisation+

@@ -160,6 +160,9 @@ struct hog_ctx {
     int batched_mode = MODE_FUSED;  // chosen by the autotuner
     int corr_policy = 0;            // 0: least padding; 1 + s: prefer warp-tile shape s
     cudaStream_t cap_stream = nullptr;
+    // training arena (hog_backward), grown on demand
+    char *d_train = nullptr;
+    size_t train_cap = 0;
     std::string err;
 };
 
@@ -243,6 +246,7 @@ void free_ctx(hog_ctx *ctx) {
         for (auto &g : cp.graph) if (g) cudaGraphExecDestroy(g);
     }
     F(ctx->d_fctr);
+    F(ctx->d_train);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (Geometry *g : ctx->geoms) {
         F(g->d_nbr);
@@ -1278,6 +1282,135 @@ int hog_get_tuning(const hog_ctx *ctx, int32_t *batched_mode, int32_t *corr_poli
     if (!ctx) return HOG_EINVAL;
     if (batched_mode) *batched_mode = ctx->batched_mode;
     if (corr_policy) *corr_policy = ctx->corr_policy;
+    return HOG_OK;
+}
+
+int hog_backward(hog_ctx *ctx, const float *images, int32_t n, int32_t w, int32_t h,
+                 const float *labels, const float *weights, float *dW, float *dI, float *loss,
+                 int32_t recompute, void *stream_) {
+    if (!ctx) return HOG_EINVAL;
+    if (n < 1 || !images || !labels || !weights || !dW)
+        return fail(ctx, HOG_EINVAL, "hog_backward: NULL argument or n < 1");
+    if (w < ctx->p.min_size || h < ctx->p.min_size || w > ctx->p.max_w || h > ctx->p.max_h)
+        return fail(ctx, HOG_EINVAL, "hog_backward: crop %dx%d outside %d..%dx%d", w, h,
+                    ctx->p.min_size, ctx->p.max_w, ctx->p.max_h);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    Geometry g;
+    if (compute_geometry(ctx->p, w, h, g)) return fail(ctx, HOG_EINVAL, "too many levels");
+    TrainLevels lv;
+    std::memset(&lv, 0, sizeof lv);
+    lv.nlev = g.nlev;
+    size_t pyr = 0, hist = 0, featu = 0;
+    int nwin = 0;
+    for (int l = 0; l < g.nlev; l++) {
+        lv.w[l] = g.lw[l]; lv.h[l] = g.lh[l]; lv.cx[l] = g.cx[l]; lv.cy[l] = g.cy[l];
+        lv.nu[l] = g.nu[l]; lv.nv[l] = g.nv[l];
+        lv.pyr_off[l] = pyr;
+        pyr += (size_t)g.lw[l] * g.lh[l];
+        lv.hist_off[l] = hist;
+        hist += (size_t)g.cx[l] * g.cy[l] * NBIN;
+        lv.feat_off[l] = featu;
+        featu += (size_t)g.cx[l] * g.cy[l] * NFEAT;
+        lv.win_off[l] = nwin;
+        nwin += g.nu[l] * g.nv[l];
+    }
+    lv.win_off[g.nlev] = nwin;
+    lv.nwin = nwin;
+    // per-crop slot sizes (floats), each rounded to keep 16-byte alignment
+    const size_t s_pyr = align_up(pyr, 4), s_hist = align_up(hist, 4), s_featu = align_up(featu, 4);
+    const size_t s_feati = g.feat_floats, s_sc = align_up((size_t)nwin, 4);
+    const size_t N = (size_t)n;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    const size_t o_pyr = take(4 * N * s_pyr), o_dp = take(4 * N * s_pyr), o_hist = take(4 * N * s_hist);
+    const size_t o_fi = take(4 * N * s_feati), o_fu = take(4 * N * s_featu), o_sc = take(4 * N * s_sc);
+    const size_t o_best = take(sizeof(int4) * N), o_marg = take(4 * N), o_wch = take(4 * NCHUNK * WIN * WIN * CHUNK);
+    const size_t o_descs = take(sizeof(LevelDesc) * N * g.nlev);
+    std::vector<LevelDesc> descs;
+    std::vector<Job> fjobs, cjobs;
+    for (int i = 0; i < n; i++)
+        for (int l = 0; l < g.nlev; l++) {
+            const int di = (int)descs.size();
+            const int nf = ((g.cx[l] + FEAT_TX - 1) / FEAT_TX) * ((g.cy[l] + FEAT_TY - 1) / FEAT_TY);
+            for (int k = 0; k < nf; k++) fjobs.push_back({di, k});
+            if (g.nu[l] > 0 && g.nv[l] > 0) {
+                const int nc = ((g.nu[l] + corr_tu(0) - 1) / corr_tu(0)) * ((g.nv[l] + corr_tv(0) - 1) / corr_tv(0));
+                for (int k = 0; k < nc; k++) cjobs.push_back({di, k});
+            }
+            descs.push_back(LevelDesc());
+        }
+    const size_t o_fj = take(sizeof(Job) * fjobs.size()), o_cj = take(sizeof(Job) * cjobs.size());
+    if (off > ctx->train_cap) {
+        if (ctx->d_train) { cudaStreamSynchronize(stream); cudaFree(ctx->d_train); }
+        ctx->d_train = nullptr;
+        ctx->train_cap = 0;
+        CUDA_TRY(ctx, cudaMalloc(&ctx->d_train, off));
+        ctx->train_cap = off;
+    }
+    char *T = ctx->d_train;
+    float *d_pyr = reinterpret_cast<float *>(T + o_pyr), *d_dp = reinterpret_cast<float *>(T + o_dp);
+    float *d_hist = reinterpret_cast<float *>(T + o_hist), *d_fi = reinterpret_cast<float *>(T + o_fi);
+    float *d_fu = reinterpret_cast<float *>(T + o_fu), *d_sc = reinterpret_cast<float *>(T + o_sc);
+    int4 *d_best = reinterpret_cast<int4 *>(T + o_best);
+    float *d_marg = reinterpret_cast<float *>(T + o_marg), *d_wch = reinterpret_cast<float *>(T + o_wch);
+    for (int i = 0, di = 0; i < n; i++)
+        for (int l = 0; l < g.nlev; l++, di++) {
+            LevelDesc &d = descs[di];
+            std::memset(&d, 0, sizeof d);
+            d.w = g.lw[l]; d.h = g.lh[l]; d.cx = g.cx[l]; d.cy = g.cy[l]; d.nu = g.nu[l]; d.nv = g.nv[l];
+            d.frame = i; d.level = l;
+            d.hist = d_hist + (size_t)i * s_hist + lv.hist_off[l];
+            d.feat = d_fi + (size_t)i * s_feati + g.feat_off[l];
+            d.feat_user = d_fu + (size_t)i * s_featu + lv.feat_off[l];
+            d.scores_user = d_sc + (size_t)i * s_sc + lv.win_off[l];
+        }
+    // tables: descriptors and jobs through the pinned staging buffer
+    const size_t tbytes = o_cj + sizeof(Job) * cjobs.size() - o_descs;
+    int rc = ensure_plan_capacity(ctx, tbytes);
+    if (rc) return rc;
+    CUDA_TRY(ctx, cudaEventSynchronize(ctx->plan_done));
+    std::memcpy(ctx->h_plan, descs.data(), sizeof(LevelDesc) * descs.size());
+    std::memcpy(ctx->h_plan + (o_fj - o_descs), fjobs.data(), sizeof(Job) * fjobs.size());
+    std::memcpy(ctx->h_plan + (o_cj - o_descs), cjobs.data(), sizeof(Job) * cjobs.size());
+    CUDA_TRY(ctx, cudaMemcpyAsync(T + o_descs, ctx->h_plan, tbytes, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->plan_done, stream));
+    const LevelDesc *dd = reinterpret_cast<const LevelDesc *>(T + o_descs);
+
+    // forward: float pyramid, histograms, features, scores of the filter, best windows
+    CUDA_TRY(ctx, cudaMemcpy2DAsync(d_pyr, s_pyr * 4, images, (size_t)w * h * 4, (size_t)w * h * 4, N,
+                                    cudaMemcpyDeviceToDevice, stream));
+    for (int l = 1; l < g.nlev; l++)
+        CUDA_TRY(ctx, launch_fpyr_step(d_pyr + lv.pyr_off[l - 1], d_pyr + lv.pyr_off[l], g.lw[l - 1],
+                                       g.lw[l], g.lh[l], s_pyr, n, stream));
+    for (int l = 0; l < g.nlev; l++)
+        CUDA_TRY(ctx, launch_fhist(d_pyr + lv.pyr_off[l], g.lw[l], g.lh[l], s_pyr, d_hist + lv.hist_off[l],
+                                   s_hist, n, stream));
+    CUDA_TRY(ctx, launch_feat(dd, reinterpret_cast<const Job *>(T + o_fj), (int)fjobs.size(),
+                              ctx->p.eps, ctx->p.trunc, stream));
+    CUDA_TRY(ctx, launch_filter_chunks(weights, d_wch, stream));
+    CUDA_TRY(ctx, launch_corr(dd, reinterpret_cast<const Job *>(T + o_cj), (int)cjobs.size(), d_wch, 1, 1,
+                              0.0f, stream));
+    CUDA_TRY(ctx, launch_argmax(d_sc, s_sc, lv, labels, d_best, d_marg, n, stream));
+    // adjoint
+    CUDA_TRY(ctx, launch_dw(d_fu, s_featu, lv, d_best, d_marg, labels, n, dW, stream));
+    if (dI) {
+        CUDA_TRY(ctx, cudaMemsetAsync(d_dp, 0, sizeof(float) * N * s_pyr, stream));
+        CUDA_TRY(ctx, launch_window_adjoint(d_pyr, s_pyr, d_hist, s_hist, lv, d_best, d_marg, labels, n,
+                                            weights, ctx->p.eps, ctx->p.trunc, recompute ? 1 : 0,
+                                            d_dp, stream));
+        for (int q = g.nlev - 2; q >= 0; q--)
+            CUDA_TRY(ctx, launch_fpyr_adjoint(d_dp, s_pyr, lv, q, d_best, d_marg, n, stream));
+        CUDA_TRY(ctx, cudaMemcpy2DAsync(dI, (size_t)w * h * 4, d_dp, s_pyr * 4, (size_t)w * h * 4, N,
+                                        cudaMemcpyDeviceToDevice, stream));
+    }
+    if (loss) {
+        std::vector<float> m(n);
+        CUDA_TRY(ctx, cudaMemcpyAsync(m.data(), d_marg, sizeof(float) * n, cudaMemcpyDeviceToHost, stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        double acc = 0.0;
+        for (int i = 0; i < n; i++) acc += m[i];
+        *loss = (float)(acc / n);
+    }
     return HOG_OK;
 }
 

@@ -158,6 +158,33 @@ struct FusedArgs {
 cudaError_t launch_fused(const FusedArgs &a, int nf_kernel, int grid, cudaStream_t stream);
 int fused_max_ctas_per_sm(int nf_kernel);
 
+// ---- training (k_train.cu): geometry of a crop size, per-crop layouts ----
+struct TrainLevels {
+    int nlev, nwin;
+    int w[MAX_LEVELS], h[MAX_LEVELS], cx[MAX_LEVELS], cy[MAX_LEVELS], nu[MAX_LEVELS], nv[MAX_LEVELS];
+    size_t pyr_off[MAX_LEVELS];    // floats, in a crop's pyramid (and pyramid-gradient) slot
+    size_t hist_off[MAX_LEVELS];   // floats, [cy][cx][18]
+    size_t feat_off[MAX_LEVELS];   // floats, user layout [cy][cx][31]
+    int win_off[MAX_LEVELS + 1];   // windows (one filter), [nu][nv] per level
+};
+
+cudaError_t launch_fpyr_step(const float *src, float *dst, int sw, int dw, int dh, size_t crop_stride,
+                             int n, cudaStream_t s);
+cudaError_t launch_fhist(const float *lvl, int w, int h, size_t crop_stride, float *hist,
+                         size_t hist_stride, int n, cudaStream_t s);
+cudaError_t launch_argmax(const float *scores, size_t crop_stride, const TrainLevels &lv,
+                          const float *labels, int4 *best, float *margin, int n, cudaStream_t s);
+cudaError_t launch_dw(const float *feat, size_t crop_stride, const TrainLevels &lv, const int4 *best,
+                      const float *margin, const float *labels, int n, float *dW, cudaStream_t s);
+cudaError_t launch_window_adjoint(const float *pyr, size_t pyr_stride, const float *hist,
+                                  size_t hist_stride, const TrainLevels &lv, const int4 *best,
+                                  const float *margin, const float *labels, int n,
+                                  const float *wuser, float eps, float tau, int recompute,
+                                  float *dP, cudaStream_t s);
+cudaError_t launch_fpyr_adjoint(float *dP, size_t pyr_stride, const TrainLevels &lv, int q,
+                                const int4 *best, const float *margin, int n, cudaStream_t s);
+cudaError_t launch_filter_chunks(const float *wuser, float *wch, cudaStream_t s);
+
 // ---- cp.async helpers (16-byte global -> shared copies, sm_80+) -----------
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);

@@ -79,6 +79,8 @@ _SIGS = {
     "hog_get_tuning": (C.c_int, [_vp, _P(_i32), _P(_i32)]),
     "hog_features_static": (C.c_int, [_P(Params), _P(Frame), _vp, C.c_size_t, _P(Level), _i32,
                                       _P(_i32), C.c_char_p, C.c_size_t, _vp]),
+    "hog_backward": (C.c_int, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _P(C.c_float),
+                               _i32, _vp]),
     "hog_set_profiling": (C.c_int, [_vp, _i32]),
     "hog_stage_stats": (C.c_int, [_vp, _vp, _i32, _i32]),
 }
@@ -200,6 +202,24 @@ class Detector:
         st = (StageStat * len(STAGES))()
         self._check(_lib.hog_stage_stats(self._h, st, len(STAGES), int(bool(reset))))
         return {n: (st[i].ms, st[i].launches, st[i].units) for i, n in enumerate(STAGES)}
+
+    def backward(self, images, labels, weights, with_image=True, recompute=False, stream=None):
+        """hog_backward on device tensors: images float32 [n,h,w], labels
+        float32 [n], weights float32 [10,10,31].  Returns (loss, dW, dI)."""
+        import torch
+        assert images.is_cuda and images.dtype == torch.float32 and images.is_contiguous()
+        n, h, w = images.shape
+        labels = labels.contiguous()
+        weights = weights.contiguous()
+        dW = torch.empty((10, 10, NFEAT), dtype=torch.float32, device=images.device)
+        dI = torch.empty_like(images) if with_image else None
+        loss = C.c_float(0.0)
+        self._check(_lib.hog_backward(self._h, C.c_void_p(images.data_ptr()), n, w, h,
+                                      C.c_void_p(labels.data_ptr()), C.c_void_p(weights.data_ptr()),
+                                      C.c_void_p(dW.data_ptr()),
+                                      C.c_void_p(dI.data_ptr()) if dI is not None else None,
+                                      C.byref(loss), int(bool(recompute)), _stream_ptr(stream)))
+        return loss.value, dW, dI
 
     def set_batched_mode(self, mode):
         """1: persistent fused launch, 0: one launch per stage."""
@@ -323,3 +343,45 @@ class Detector:
         if out is not None:
             return dets[:total], counts[:n].copy()
         return dets[:total].copy(), counts[:n].copy()
+
+
+def hinge_loss(detector, images, labels, weights, recompute=False):
+    """Differentiable hinge loss on the best window score (torch autograd):
+    the adjoint is libhog's hand-written hog_backward."""
+    return _HingeLoss.apply(images, weights, labels, detector, recompute)
+
+
+def _make_autograd():
+    import torch
+
+    class HingeLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, images, weights, labels, detector, recompute):
+            need_dI = bool(ctx.needs_input_grad[0])
+            loss, dW, dI = detector.backward(images.detach().float().contiguous(),
+                                             labels.detach().float().contiguous(),
+                                             weights.detach().float().contiguous(),
+                                             with_image=need_dI, recompute=recompute)
+            ctx.save_for_backward(dW, dI if dI is not None else dW.new_empty(0))
+            ctx.need_dI = need_dI
+            return images.new_tensor(loss)
+
+        @staticmethod
+        def backward(ctx, grad):
+            dW, dI = ctx.saved_tensors
+            gI = (grad * dI) if ctx.need_dI else None
+            return gI, grad * dW, None, None, None
+
+    return HingeLoss
+
+
+class _Lazy:
+    fn = None
+
+    def apply(self, *a):
+        if _Lazy.fn is None:
+            _Lazy.fn = _make_autograd()
+        return _Lazy.fn.apply(*a)
+
+
+_HingeLoss = _Lazy()
