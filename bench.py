@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--plain-frames", type=int, default=200)
     ap.add_argument("--cpu-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-warmup", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -153,6 +155,83 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- native arm
+def run_serving(hog, synth, W, seconds, warm, mode, lanes=4, max_batch=16, cameras=None):
+    """Serving workload: 8 camera threads (four 640x480, four 1280x1024) each
+    submit at 500 frames/s with seeded exponential jitter to one
+    continuous-batching server; the main thread polls results.  Requests of
+    the first ``warm`` seconds (plans and graphs being built) are not
+    counted.  A submit refused because the queue is full is a dropped frame."""
+    ids = list(range(8)) if cameras is None else list(cameras)
+    cams = [synth.serving_cameras()[c] for c in ids]
+    nc = len(cams)
+    pool = {i: [synth.camera_frame(c, k) for k in range(8)] for i, c in enumerate(ids)}
+    arr = synth.arrivals(n_cameras=8, seconds=seconds + warm)
+    arr = [arr[c] for c in ids]
+    cfg = hog.default_server_config(max_batch=max_batch, max_lanes=lanes, queue_cap=256,
+                                    batched_mode=mode)
+    srv = hog.Server(W, cfg, max_w=1280, max_h=1024)
+    dropped = [0] * nc
+    accepted = [0] * nc
+    done = threading.Event()
+    base = time.perf_counter() + 0.05
+
+    def camera(c):
+        for k, ta in enumerate(arr[c]):
+            delay = base + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            if srv.submit(pool[c][k % 8], tag=(c << 32) | k) is None:
+                dropped[c] += 1 if ta >= warm else 0
+            else:
+                accepted[c] += 1
+
+    th = [threading.Thread(target=camera, args=(c,)) for c in range(nc)]
+    for t in th:
+        t.start()
+    lat = {0: [], 1: []}
+    queue_ms, dev_ms, got, failed = [], [], 0, 0
+    t_first = t_last = None
+    while True:
+        res = srv.poll(cap=256, det_cap=256 * 64, wait_us=2000)
+        now = time.perf_counter()
+        for r in res:
+            got += 1
+            c, k = r["tag"] >> 32, r["tag"] & 0xFFFFFFFF
+            failed += r["status"] != 0
+            if arr[c][k] < warm:
+                continue
+            t_first = now if t_first is None else t_first
+            t_last = now
+            lat[int(cams[c][0] > 640)].append(r["latency_ms"])
+            queue_ms.append(r["queue_ms"])
+            dev_ms.append(r["device_ms"])
+        if not res and all(not t.is_alive() for t in th) and got >= sum(accepted):
+            break
+    st = srv.stats()
+    srv.close()
+    all_lat = lat[0] + lat[1]
+    n = len(all_lat)
+    pct = lambda a, q: float(np.percentile(a, q)) if a else None
+    return {
+        "workload": "%d cameras x 500 frames/s (%s uint8 eyeblink streams), exponential "
+                    "arrival jitter 0.2 ms, %.0f s after %.0f s warm-up"
+                    % (nc, ", ".join("%dx%d" % c for c in cams), seconds, warm),
+        "offered_frames_per_s": sum(len(a) for a in arr) / (seconds + warm),
+        "frames_per_s": n / seconds, "frames": n, "dropped": sum(dropped), "failed": failed,
+        "p50_ms": pct(all_lat, 50), "p99_ms": pct(all_lat, 99),
+        "max_ms": max(all_lat) if all_lat else None,
+        "p50_ms_640x480": pct(lat[0], 50), "p99_ms_640x480": pct(lat[0], 99),
+        "p50_ms_1280x1024": pct(lat[1], 50), "p99_ms_1280x1024": pct(lat[1], 99),
+        "queue_p50_ms": pct(queue_ms, 50), "queue_p99_ms": pct(queue_ms, 99),
+        "device_p50_ms": pct(dev_ms, 50), "device_p99_ms": pct(dev_ms, 99),
+        "lanes": st["lanes"], "lane_mb": st["lane_bytes"] / 2**20,
+        "mean_batch": st["batched_frames"] / max(st["batches"], 1),
+        "max_inflight": st["max_inflight"], "batches": st["batches"],
+        "mode": "fused" if mode == 1 else "per-stage",
+        "latency": "host clock, submit (frame copied in) -> boxes in host memory",
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -307,6 +386,12 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
 
+    # ---- serving: continuous batching over 8 camera streams (rank 0 of a
+    # replica job serves its own GPU like every other rank)
+    serving = None
+    if args.serve_seconds > 0:
+        serving = run_serving(hog, synth, W, args.serve_seconds, args.serve_warmup, mode)
+
     # ---- CPU baseline: the FP64 oracle on a bounded sample, all host cores
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -339,6 +424,7 @@ def main():
             "plain": {"frames_per_s": plain_fps, "p50_ms": statistics.median(lat),
                       "p99_ms": float(np.percentile(lat, 99)), "frames": nplain,
                       "stage_ms_per_frame": plain_stages},
+            "serving": serving,
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roofline,

@@ -46,6 +46,7 @@ extern "C" {
 #define HOG_ECAPACITY  (-4)  /* output truncated to its capacity; counts exact */
 #define HOG_ETIMEOUT   (-5)  /* a bounded device wait gave up                  */
 #define HOG_EINTERNAL  (-6)  /* a kernel's own consistency check failed        */
+#define HOG_EBUSY      (-7)  /* the server's request queue is full; retry      */
 
 /* ---- fixed sizes of the method (Section 4.1.1) ------------------------- */
 #define HOG_CELL        8    /* 8x8-pixel cells                               */
@@ -179,6 +180,19 @@ int hog_detect_batched(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, 
  * fused launch (default), 0 = one launch per stage (both as graphs). */
 int hog_set_batched_mode(hog_ctx *ctx, int32_t mode);
 
+/* Suppression launch shape.  c = 1: one CTA per frame; c = 2, 4, 8 or 16:
+ * each frame's suppression on a thread-block cluster of c CTAs (positions
+ * split across the CTAs' shared memory, neighbour states read through
+ * distributed shared memory); c = 0 (default): automatic -- clusters of
+ * about SMs / frames CTAs, and at least the size whose state fits in shared
+ * memory.  The kept boxes are the same for every c.  Drops cached plans and
+ * graphs when c changes.  HOG_EINVAL for other values. */
+int hog_set_nms_cluster(hog_ctx *ctx, int32_t c);
+
+/* The cluster size the suppression of a batch of n_frames frames of w x h
+ * would use under the current setting (1 = one CTA per frame). */
+int hog_nms_cluster_size(hog_ctx *ctx, int32_t n_frames, int32_t w, int32_t h, int32_t *c);
+
 /* Autotuner (no counterpart in the paper, which picks block sizes by hand,
  * Section 5.1 block-size table).  On the given sample batch (device frames)
  * it times the correlation stage under each warp-tile shape policy (least
@@ -257,6 +271,87 @@ int hog_set_profiling(hog_ctx *ctx, int32_t on);
 /* Copy the accumulated per-stage stats (HOG_NSTAGES entries) into out
  * (host); waits for the last profiled work.  reset != 0 clears them. */
 int hog_stage_stats(hog_ctx *ctx, hog_stage_stat *out, int32_t cap, int32_t reset);
+
+
+/* ---- serving loop (no counterpart in the paper: it processes recorded
+ * videos in groups of 16 frames and leaves online processing of camera
+ * batches to future work, Section 6.6; its real-time target is 500 frames/s
+ * per camera) ----------------------------------------------------------- */
+typedef struct hog_server hog_server;   /* opaque, owned by the library */
+
+/* Server configuration.  hog_default_server_config() fills the defaults. */
+typedef struct {
+    int32_t max_batch;    /* frames per device batch, 1..1024 (default 8)     */
+    int32_t max_lanes;    /* batches in flight at once, 1..16 (default 3):
+                             each lane is a context + stream + frame slots   */
+    int32_t queue_cap;    /* frames held between submit and dispatch
+                             (pinned host slots), >= max_batch (default 64)  */
+    int32_t batched_mode; /* -1 context default, 0 per-stage, 1 fused       */
+    int64_t mem_reserve;  /* lanes after the first are created only while
+                             free device memory stays above this many bytes
+                             (default 1 GiB)                                 */
+} hog_server_config;
+
+/* One finished request, returned by hog_server_poll. */
+typedef struct {
+    uint64_t id;          /* the id hog_server_submit returned                */
+    int64_t  tag;         /* the caller's tag (e.g. camera << 32 | frame no)  */
+    int32_t  status;      /* HOG_OK or the HOG_E* code of its batch           */
+    int32_t  count;       /* kept detections (exact)                          */
+    int32_t  stored;      /* of which copied into the poll's dets buffer      */
+    int32_t  pad;
+    double   latency_ms;  /* submit -> result ready (host clock)              */
+    double   queue_ms;    /* submit -> dispatched to a lane                   */
+    double   device_ms;   /* its batch on the lane's stream: copy-in ..
+                             boxes packed (CUDA events; lanes overlap)      */
+    int32_t  batch;       /* frames in its batch                              */
+    int32_t  lane;        /* lane that ran it                                 */
+} hog_result;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t rejected;       /* submits refused with HOG_EBUSY                 */
+    int64_t batches, batched_frames;
+    int64_t max_inflight;   /* most frames dispatched and not yet finished    */
+    int64_t lanes;          /* lanes created (admission by free memory)       */
+    int64_t lane_bytes;     /* device bytes the first lane took               */
+    int64_t pending;        /* frames waiting for a lane right now            */
+} hog_server_stats;
+
+void hog_default_server_config(hog_server_config *c);
+
+/* Create a server for frames up to p->max_w x p->max_h (p->max_batch is
+ * replaced by c->max_batch) with F filters (host float [F][10][10][31]).
+ * Starts one worker thread.  HOG_EINVAL for a bad configuration (message in
+ * hog_server_last_error(NULL)), HOG_ENOMEM if not even one lane fits. */
+int hog_server_create(const hog_params *p, const float *filters_host, int32_t n_filters,
+                      const hog_server_config *c, hog_server **out);
+
+/* Queue one 8-bit frame (HOST memory, row pitch in bytes); the frame is
+ * copied before the call returns.  *id_out (may be NULL) gets the request
+ * id.  HOG_EBUSY when queue_cap frames are already waiting or in flight.
+ * Thread-safe: several camera threads may submit at once.  Each result is
+ * bit-identical to hog_detect on that frame alone; its boxes have frame 0. */
+int hog_server_submit(hog_server *s, const uint8_t *frame, int32_t w, int32_t h, int32_t pitch,
+                      int64_t tag, uint64_t *id_out);
+
+/* Take up to cap finished results in completion order (res, host) and their
+ * boxes, concatenated in result order, into dets (host, det_cap entries;
+ * may be NULL with det_cap 0; each result's stored says how many of its
+ * boxes were copied).  Waits up to wait_us microseconds when none is ready.
+ * *n_out = results returned.  Thread-safe. */
+int hog_server_poll(hog_server *s, hog_result *res, int32_t cap, hog_det *dets, int32_t det_cap,
+                    int32_t *n_out, int32_t wait_us);
+
+int hog_server_get_stats(hog_server *s, hog_server_stats *out);
+
+/* Finish every queued request, stop the worker, free everything.  Results
+ * not yet polled are dropped. */
+void hog_server_destroy(hog_server *s);
+
+/* Message of the last failure of s, or of the calling thread's last
+ * hog_server_create when s is NULL. */
+const char *hog_server_last_error(const hog_server *s);
 
 #ifdef __cplusplus
 }

@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     raise RuntimeError("nvcc failed on %s:\n%s" % (futs[fu], r.stdout + r.stderr))
     if jobs or not os.path.exists(LIB) or force:
         tmp = LIB + ".tmp%d" % os.getpid()
-        r = subprocess.run([nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs + ["-lcudart"],
+        r = subprocess.run([nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs + ["-lcudart", "-lpthread"],
                            capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

@@ -159,6 +159,8 @@ struct hog_ctx {
     int num_sms = 0, fused_grid = 0;
     int batched_mode = MODE_FUSED;  // chosen by the autotuner
     int corr_policy = 0;            // 0: least padding; 1 + s: prefer warp-tile shape s
+    int nms_cluster = 0;            // 0: automatic; 1: one CTA per frame; 2..16: cluster size
+    int plan_cache_max = 8;         // cached batch plans (a server raises it)
     cudaStream_t cap_stream = nullptr;
     // training arena (hog_backward), grown on demand
     char *d_train = nullptr;
@@ -594,7 +596,7 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
     CUDA_TRY(ctx, mark(8));
     if (info.nframes > 0)
         CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.nframes,
-                                 info.max_npos, ctx->d_flags, stream));
+                                 info.max_npos, ctx->d_flags, stream, ctx->nms_cluster));
     CUDA_TRY(ctx, mark(9));
     if (ctx->prof) {
         ctx->prof_pending = true;
@@ -656,7 +658,7 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
     PlanInfo info;
     layout_plan(pb, ctx->nf, info);
     // least recently used entry (or a free one)
-    if (ctx->plans.size() < 8) ctx->plans.emplace_back();
+    if ((int)ctx->plans.size() < ctx->plan_cache_max) ctx->plans.emplace_back();
     CachedPlan *victim = &ctx->plans[0];
     for (auto &cp : ctx->plans)
         if (!cp.d || cp.used < victim->used) victim = &cp;
@@ -718,7 +720,7 @@ int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStr
     CUDA_TRY(ctx, mark(8));
     if (info.nframes > 0)
         CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.nframes,
-                                 info.max_npos, ctx->d_flags, stream));
+                                 info.max_npos, ctx->d_flags, stream, ctx->nms_cluster));
     CUDA_TRY(ctx, mark(9));
     if (ctx->prof) {
         ctx->prof_pending = true;
@@ -845,6 +847,45 @@ int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, 
 }
 
 }  // namespace
+
+namespace hogk {
+
+// Enqueue the detection of nb <= max_batch device frames on `stream`
+// without waiting: plan (cached), launches, and the packing of kept boxes
+// and counts into the context's mapped pinned buffers.
+int detect_enqueue(hog_ctx *ctx, const hog_frame *frames, int nb, cudaStream_t stream, int mode,
+                   bool use_graph) {
+    if (nb < 1 || nb > ctx->p.max_batch) return fail(ctx, HOG_EINVAL, "batch of %d frames", nb);
+    const char *dplan = nullptr;
+    const PlanInfo *info = nullptr;
+    CachedPlan *cp = nullptr;
+    int rc = cached_plan(ctx, frames, nb, 0, stream, &dplan, &info, &cp);
+    if (rc) return rc;
+    rc = run_batch(ctx, mode, cp, nb, use_graph, stream);
+    if (rc) return rc;
+    const size_t D = (size_t)ctx->p.max_dets_per_frame;
+    CUDA_TRY(ctx, launch_pack(ctx->d_dets, ctx->p.max_dets_per_frame, ctx->d_counts, nb, ctx->m_dets,
+                              (int)(D * ctx->p.max_batch), ctx->m_counts, stream));
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                                  stream));
+    return HOG_OK;
+}
+
+// After the enqueued work has completed: the packed boxes of frame i start
+// at *first + (sum of earlier frames' stored counts).
+int detect_results(hog_ctx *ctx, const int32_t **counts, const hog_det **dets) {
+    if (ctx->h_flags[2]) return fail(ctx, HOG_ETIMEOUT, "a bounded device wait gave up");
+    *counts = ctx->h_counts;
+    *dets = ctx->h_dets;
+    return HOG_OK;
+}
+
+int ctx_max_dets(const hog_ctx *ctx) { return ctx->p.max_dets_per_frame; }
+int ctx_batched_mode(const hog_ctx *ctx) { return ctx->batched_mode; }
+void ctx_set_plan_cache(hog_ctx *ctx, int n) { ctx->plan_cache_max = n < 1 ? 1 : n; }
+const char *ctx_error(const hog_ctx *ctx) { return ctx->err.c_str(); }
+
+}  // namespace hogk
 
 // ==== C ABI ===============================================================
 
@@ -1096,6 +1137,23 @@ int hog_detect_batched(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, 
     }
     return detect_device(ctx, frames, n_frames, 0, dets, det_cap, nullptr, counts,
                          (cudaStream_t)stream_, ctx->batched_mode, true);
+}
+
+int hog_set_nms_cluster(hog_ctx *ctx, int32_t c) {
+    if (!ctx || !(c == 0 || c == 1 || c == 2 || c == 4 || c == 8 || c == 16)) return HOG_EINVAL;
+    if (c != ctx->nms_cluster) {
+        clear_plans(ctx);   // captured graphs hold the old launch shape
+        ctx->nms_cluster = c;
+    }
+    return HOG_OK;
+}
+
+int hog_nms_cluster_size(hog_ctx *ctx, int32_t n_frames, int32_t w, int32_t h, int32_t *c) {
+    if (!ctx || !c || n_frames < 1 || w < 0 || h < 0) return HOG_EINVAL;
+    Geometry g;   // host-side level geometry only
+    if (compute_geometry(ctx->p, w, h, g)) return HOG_EINVAL;
+    *c = nms_cluster_size(n_frames, g.npos, ctx->nms_cluster);
+    return HOG_OK;
 }
 
 int hog_set_batched_mode(hog_ctx *ctx, int32_t mode) {

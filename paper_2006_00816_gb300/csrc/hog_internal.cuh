@@ -185,6 +185,15 @@ cudaError_t launch_fpyr_adjoint(float *dP, size_t pyr_stride, const TrainLevels 
                                 const int4 *best, const float *margin, int n, cudaStream_t s);
 cudaError_t launch_filter_chunks(const float *wuser, float *wch, cudaStream_t s);
 
+// ---- asynchronous detection for the serving runtime (hog_api.cu) ---------
+int detect_enqueue(hog_ctx *ctx, const hog_frame *frames, int nb, cudaStream_t stream, int mode,
+                   bool use_graph);
+int detect_results(hog_ctx *ctx, const int32_t **counts, const hog_det **dets);
+int ctx_max_dets(const hog_ctx *ctx);
+int ctx_batched_mode(const hog_ctx *ctx);
+void ctx_set_plan_cache(hog_ctx *ctx, int n);
+const char *ctx_error(const hog_ctx *ctx);
+
 // ---- cp.async helpers (16-byte global -> shared copies, sm_80+) -----------
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -230,6 +239,8 @@ cudaError_t launch_pack(const hog_det *dets, int per_frame, const int32_t *count
 // workspace).  flags[0] |= 1 on capacity overflow; flags[2] |= 1 if a bounded
 // wait gave up.
 cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *flags,
-                       cudaStream_t stream);
+                       cudaStream_t stream, int cluster_request);
+// Cluster size launch_nms uses for such a batch (1 = one CTA per frame).
+int nms_cluster_size(int nframes, int max_npos, int request);
 
 }  // namespace hogk

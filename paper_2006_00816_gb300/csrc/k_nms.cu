@@ -136,8 +136,306 @@ cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, uint8_t *cnt, i
     return cudaGetLastError();
 }
 
+// ---- cluster form --------------------------------------------------------
+// One frame's suppression spread over a thread-block cluster of C CTAs
+// (C = 2..16, one CTA per SM): CTA r owns the contiguous position range
+// [r*P, r*P + P), P = ceil(npos / C), and keeps the key high words, states
+// and candidate lists of its range in its own shared memory.  A neighbour's
+// key and state are read from the owning CTA's shared memory through the
+// cluster's distributed shared memory (mapa + ld.shared::cluster).  Each CTA
+// only writes the states of its own positions; the rounds are the same as
+// in the one-CTA form, with a cluster barrier (release/acquire) closing each
+// round, after which every CTA reads the cluster's count of undecided
+// candidates from CTA 0.  Within a round a remote state may be read stale,
+// which can only make a candidate wait one more round: the kept set is the
+// same for every C.  This gives one frame the shared memory and L2
+// bandwidth of C SMs (a 1280x1024 frame has about 55K positions, 715 KB of
+// state: more than one SM holds), and cuts the latency of small batches.
+namespace {
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_id() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of `p` (a shared variable) in CTA `rank`
+__device__ __forceinline__ uint32_t cl_map(const void *p, uint32_t rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_ld_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t cl_ld_u8(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u8 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cl_st_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+}  // namespace
+
+constexpr int NMS_MAX_CLUSTER = 16;
+__host__ __device__ constexpr size_t nms_cluster_ws_bytes(int npos, int c) {
+    return (size_t)((npos + c - 1) / c) * 13 + 64;
+}
+
+__global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc *__restrict__ frames,
+                                                                int *flags) {
+    extern __shared__ __align__(16) unsigned char nsm[];
+    __shared__ int sh[NMS_NT / 32 + 4];
+    __shared__ int s_cnt[2][NMS_MAX_CLUSTER];     // read in CTA 0: undecided per CTA
+    __shared__ int s_kept[NMS_MAX_CLUSTER];       // read in CTA 0: kept per CTA
+    __shared__ uint32_t s_rkhi[NMS_MAX_CLUSTER], s_rstate[NMS_MAX_CLUSTER];
+    __shared__ int s_total;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int C = (int)cl_size(), rank = (int)cl_rank();
+    const FrameDesc &fd = frames[cl_id()];
+    const int npos = fd.npos;
+    const int P = (npos + C - 1) / C;
+    const int lo = min(rank * P, npos), nmine = min(lo + P, npos) - lo;
+    uint32_t *khi = reinterpret_cast<uint32_t *>(nsm);                       // [P]
+    int32_t *list[2] = {reinterpret_cast<int32_t *>(nsm) + P,                  // local indices
+                        reinterpret_cast<int32_t *>(nsm) + 2 * (size_t)P};
+    volatile uint8_t *state = nsm + (size_t)P * 12;
+    const uint64_t *gkeys = fd.keys;
+    const int32_t *__restrict__ nbr = fd.nbr;
+    const uint8_t *__restrict__ nbr_cnt = fd.nbr_cnt;
+    int *s_n = sh + NMS_NT / 32 + 1;
+    const float invP = P > 0 ? 1.0f / (float)P : 0.f;
+
+    auto append = [&](bool flag, int i, int which) {
+        const unsigned m = __ballot_sync(0xffffffffu, flag);
+        if (!m) return;
+        int b0 = 0;
+        if (lane == __ffs(m) - 1) b0 = atomicAdd(s_n + which, __popc(m));
+        b0 = __shfl_sync(0xffffffffu, b0, __ffs(m) - 1);
+        if (flag) list[which][b0 + __popc(m & ((1u << lane) - 1))] = i;
+    };
+
+    if (t < C) {
+        s_rkhi[t] = cl_map(khi, t);
+        s_rstate[t] = cl_map((const void *)state, t);
+    }
+    if (t == 0) { s_n[0] = 0; s_n[1] = 0; }
+    __syncthreads();
+    for (int i0 = 0; i0 < nmine; i0 += NMS_NT) {
+        const int i = i0 + t;
+        uint32_t h = NMS_NOKEY;
+        if (i < nmine) {
+            h = (uint32_t)(__ldg(gkeys + lo + i) >> 32);
+            khi[i] = h;
+            state[i] = h != NMS_NOKEY ? NMS_ALIVE : NMS_DEAD;
+        }
+        append(h != NMS_NOKEY, i, 0);
+    }
+    cl_sync();   // every CTA's keys and states are initialised
+
+    int cur = 0, round = 0;
+    for (; round <= npos; round++) {
+        const int n_cur = s_n[cur];
+        for (int i0 = 0; i0 < n_cur; i0 += NMS_NT) {
+            const int i = i0 + t;
+            bool undecided = false;
+            int li = -1;
+            if (i < n_cur) {
+                li = list[cur][i];
+                const int p = lo + li;
+                const uint32_t hp = khi[li];
+                const int n = __ldg(nbr_cnt + p);
+                bool dead = false, wait = false;
+                for (int s0 = 0; s0 < n && !dead; s0 += 8) {
+                    int q[8];
+#pragma unroll
+                    for (int k = 0; k < 8; k++)
+                        q[k] = s0 + k < n ? __ldg(nbr + (size_t)(s0 + k) * npos + p) : -1;
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        if (q[k] < 0) continue;
+                        // owner CTA and local index of q (float estimate, corrected)
+                        int o = __float2int_rz((float)q[k] * invP);
+                        int b = o * P;
+                        if (b > q[k]) { o--; b -= P; }
+                        else if (q[k] - b >= P) { o++; b += P; }
+                        const int lq = q[k] - b;
+                        const uint32_t hq = cl_ld_u32(s_rkhi[o] + 4u * (uint32_t)lq);
+                        if (hq == NMS_NOKEY) continue;
+                        if (hq != hp ? !(hq < hp) : !(__ldg(gkeys + q[k]) < __ldg(gkeys + p))) continue;
+                        const uint32_t sq = cl_ld_u8(s_rstate[o] + (uint32_t)lq);
+                        if (sq == NMS_KEPT) dead = true;
+                        else if (sq == NMS_ALIVE) wait = true;
+                    }
+                }
+                if (dead) state[li] = NMS_DEAD;
+                else if (!wait) state[li] = NMS_KEPT;
+                else undecided = true;
+            }
+            append(undecided, li, cur ^ 1);
+        }
+        __syncthreads();
+        // publish this CTA's undecided count to CTA 0 (slot by round parity:
+        // slot r&1 is rewritten two rounds later, after every CTA read it)
+        if (t == 0) cl_st_u32(cl_map(&s_cnt[round & 1][rank], 0), (uint32_t)s_n[cur ^ 1]);
+        cl_sync();
+        if (wid == 0) {
+            int c = lane < C ? (int)cl_ld_u32(cl_map(&s_cnt[round & 1][lane], 0)) : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0) {
+                s_total = c;
+                s_n[cur] = 0;     // the list just processed becomes next round's output
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+        if (s_total == 0) break;
+    }
+
+    // kept positions in position order: CTA r's before CTA r+1's
+    int *s_warp = sh;
+    const int per = (nmine + NMS_NT - 1) / NMS_NT;
+    const int beg = min(t * per, nmine), end = min(beg + per, nmine);
+    int mine = 0;
+    for (int i = beg; i < end; i++) mine += state[i] == NMS_KEPT;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int k = 0; k < NMS_NT / 32; k++) {
+            const int x = s_warp[k];
+            s_warp[k] = run;
+            run += x;
+        }
+        cl_st_u32(cl_map(&s_kept[rank], 0), (uint32_t)run);
+    }
+    cl_sync();
+    if (wid == 0) {
+        const int c = lane < C ? (int)cl_ld_u32(cl_map(&s_kept[lane], 0)) : 0;
+        int before = lane < rank ? c : 0, all = c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            before += __shfl_xor_sync(0xffffffffu, before, o);
+            all += __shfl_xor_sync(0xffffffffu, all, o);
+        }
+        if (lane == 0) { sh[NMS_NT / 32] = before; s_total = all; }
+    }
+    __syncthreads();
+    const int total = s_total;
+    int pos = sh[NMS_NT / 32] + s_warp[wid] + incl - mine;
+    for (int i = beg; i < end; i++) {
+        if (state[i] != NMS_KEPT) continue;
+        if (pos < fd.out_cap) {
+            const uint64_t k = __ldg(gkeys + lo + i);
+            const int l = key_level(k);
+            const int u = key_u(k), v = key_v(k);
+            const WinBox b = window_box(fd.W, fd.H, fd.lev_w[l], fd.lev_h[l], u, v);
+            hog_det det;
+            det.frame = fd.frame;
+            det.level = l;
+            det.filter = key_filter(k);
+            det.u = u;
+            det.v = v;
+            det.score = key_score(k);
+            det.x = b.x; det.y = b.y; det.w = b.w; det.h = b.h;
+            fd.out[pos] = det;
+        }
+        pos++;
+    }
+    if (rank == 0 && t == 0) {
+        *fd.count = total;
+        if (total > fd.out_cap) atomicOr(flags, 1);
+        atomicMax(flags + 1, round + 1);
+    }
+    cl_sync();   // no CTA leaves while another may still read its shared memory
+}
+
+namespace {
+int g_nsm = 0;             // SM count of the device
+int g_cluster_max = -1;    // largest cluster size the device can run (1 = none)
+
+int nms_cluster_max() {
+    if (g_cluster_max >= 0) return g_cluster_max;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
+    g_cluster_max = 1;
+    if (cudaFuncSetAttribute(nms_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             NMS_SMEM_MAX) != cudaSuccess ||
+        cudaFuncSetAttribute(nms_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return g_cluster_max;
+    }
+    for (int c = NMS_MAX_CLUSTER; c >= 2; c >>= 1) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = c;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(NMS_NT);
+        cfg.dynamicSmemBytes = NMS_SMEM_MAX;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, nms_cluster_kernel, &cfg) == cudaSuccess && n > 0) {
+            g_cluster_max = c;
+            break;
+        }
+        cudaGetLastError();
+    }
+    return g_cluster_max;
+}
+}  // namespace
+
+// Cluster size for a batch: `request` 1 = one CTA per frame, 2..16 = that
+// size, 0 = automatic -- spread the batch over the SMs (SMs / frames, a
+// power of two), and at least the size whose per-CTA state fits in shared
+// memory.  Returns 1 for the one-CTA form.
+int nms_cluster_size(int nframes, int max_npos, int request) {
+    const int cmax = nms_cluster_max();
+    if (cmax < 2 || request == 1 || nframes <= 0) return 1;
+    int c;
+    if (request >= 2) {
+        c = request > cmax ? cmax : request;
+    } else {
+        const int want = g_nsm / nframes;
+        c = 1;
+        while (c * 2 <= want && c * 2 <= cmax) c *= 2;
+        if (nms_ws_bytes(max_npos) > (size_t)NMS_SMEM_MAX && c < 2) c = 2;
+    }
+    while (c < cmax && nms_cluster_ws_bytes(max_npos, c) > (size_t)NMS_SMEM_MAX) c *= 2;
+    if (c >= 2 && nms_cluster_ws_bytes(max_npos, c) > (size_t)NMS_SMEM_MAX) return 1;
+    return c;
+}
+
 cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *flags,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, int cluster_request) {
     if (nframes <= 0) return cudaSuccess;
     static bool configured = false;
     if (!configured) {
@@ -145,6 +443,22 @@ cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, NMS_SMEM_MAX);
         if (e != cudaSuccess) return e;
         configured = true;
+    }
+    const int c = nms_cluster_size(nframes, max_npos, cluster_request);
+    if (c >= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = c;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(nframes * c);
+        cfg.blockDim = dim3(NMS_NT);
+        cfg.dynamicSmemBytes = nms_cluster_ws_bytes(max_npos, c);
+        cfg.stream = stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, nms_cluster_kernel, frames, flags);
     }
     const size_t ws = nms_ws_bytes(max_npos);
     if (ws <= (size_t)NMS_SMEM_MAX)

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libhog.so")
 
 HOG_OK, HOG_EINVAL, HOG_ENOMEM, HOG_ECUDA, HOG_ECAPACITY, HOG_ETIMEOUT, HOG_EINTERNAL = (
     0, -1, -2, -3, -4, -5, -6)
+HOG_EBUSY = -7
 NFEAT, NBIN, CELL, WIN = 31, 18, 8, 10
 
 if not os.path.exists(LIB_PATH):
@@ -55,6 +56,24 @@ class Level(C.Structure):
                 ("offset", C.c_int64)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("max_lanes", C.c_int32), ("queue_cap", C.c_int32),
+                ("batched_mode", C.c_int32), ("mem_reserve", C.c_int64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("tag", C.c_int64), ("status", C.c_int32),
+                ("count", C.c_int32), ("stored", C.c_int32), ("pad", C.c_int32),
+                ("latency_ms", C.c_double), ("queue_ms", C.c_double),
+                ("device_ms", C.c_double), ("batch", C.c_int32), ("lane", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("submitted", "completed", "failed", "rejected", "batches",
+                                         "batched_frames", "max_inflight", "lanes", "lane_bytes",
+                                         "pending")]
+
+
 DET_DTYPE = np.dtype([("frame", "<i4"), ("level", "<i4"), ("filter", "<i4"), ("u", "<i4"),
                       ("v", "<i4"), ("score", "<f4"), ("x", "<f8"), ("y", "<f8"), ("w", "<f8"),
                       ("h", "<f8")], align=True)
@@ -75,6 +94,8 @@ _SIGS = {
     "hog_detect_host": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
     "hog_detect_batched": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
     "hog_set_batched_mode": (C.c_int, [_vp, _i32]),
+    "hog_set_nms_cluster": (C.c_int, [_vp, _i32]),
+    "hog_nms_cluster_size": (C.c_int, [_vp, _i32, _i32, _i32, _P(_i32)]),
     "hog_autotune": (C.c_int, [_vp, _P(Frame), _i32, C.c_char_p, _vp]),
     "hog_get_tuning": (C.c_int, [_vp, _P(_i32), _P(_i32)]),
     "hog_features_static": (C.c_int, [_P(Params), _P(Frame), _vp, C.c_size_t, _P(Level), _i32,
@@ -83,6 +104,13 @@ _SIGS = {
                                _i32, _vp]),
     "hog_set_profiling": (C.c_int, [_vp, _i32]),
     "hog_stage_stats": (C.c_int, [_vp, _vp, _i32, _i32]),
+    "hog_default_server_config": (None, [_P(ServerConfig)]),
+    "hog_server_create": (C.c_int, [_P(Params), _vp, _i32, _P(ServerConfig), _P(_vp)]),
+    "hog_server_submit": (C.c_int, [_vp, _vp, _i32, _i32, _i32, C.c_int64, _P(C.c_uint64)]),
+    "hog_server_poll": (C.c_int, [_vp, _P(Result), _i32, _vp, _i32, _P(_i32), _i32]),
+    "hog_server_get_stats": (C.c_int, [_vp, _P(ServerStats)]),
+    "hog_server_destroy": (None, [_vp]),
+    "hog_server_last_error": (C.c_char_p, [_vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -225,6 +253,16 @@ class Detector:
         """1: persistent fused launch, 0: one launch per stage."""
         self._check(_lib.hog_set_batched_mode(self._h, int(mode)))
 
+    def set_nms_cluster(self, c):
+        """Suppression launch: 1 one CTA per frame, 2/4/8/16 cluster size,
+        0 automatic (default)."""
+        self._check(_lib.hog_set_nms_cluster(self._h, int(c)))
+
+    def nms_cluster_size(self, n_frames, w, h):
+        c = _i32(0)
+        self._check(_lib.hog_nms_cluster_size(self._h, int(n_frames), int(w), int(h), C.byref(c)))
+        return c.value
+
     def autotune(self, frames, cache_path=None, stream=None):
         """Run the autotuner on a sample batch of device frames; returns
         (batched_mode, corr_policy)."""
@@ -343,6 +381,88 @@ class Detector:
         if out is not None:
             return dets[:total], counts[:n].copy()
         return dets[:total].copy(), counts[:n].copy()
+
+
+def default_server_config(**kw) -> ServerConfig:
+    c = ServerConfig()
+    _lib.hog_default_server_config(C.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError(k)
+        setattr(c, k, v)
+    return c
+
+
+class Server:
+    """Continuous-batching detection server (hog_server_*): camera threads
+    ``submit`` host frames, a native worker batches whatever has arrived onto
+    several in-flight lanes, ``poll`` returns finished results with their
+    submit-to-result latency."""
+
+    def __init__(self, filters, config: ServerConfig | None = None, **params):
+        f = np.ascontiguousarray(filters, dtype=np.float32)
+        assert f.ndim == 4 and f.shape[1:] == (WIN, WIN, NFEAT)
+        self.params = default_params(**params)
+        self.config = config or default_server_config()
+        h = _vp()
+        rc = _lib.hog_server_create(C.byref(self.params), f.ctypes.data_as(_vp), f.shape[0],
+                                    C.byref(self.config), C.byref(h))
+        if rc:
+            raise HogError(rc, (_lib.hog_server_last_error(None) or b"").decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hog_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, frame, tag=0):
+        """Queue one host uint8 frame [h, w]; returns the request id, or None
+        when the queue is full (HOG_EBUSY)."""
+        f = np.ascontiguousarray(frame, dtype=np.uint8)
+        rid = C.c_uint64(0)
+        rc = _lib.hog_server_submit(self._h, f.ctypes.data_as(_vp), f.shape[1], f.shape[0],
+                                    f.strides[0], int(tag), C.byref(rid))
+        if rc == HOG_EBUSY:
+            return None
+        if rc:
+            raise HogError(rc, "submit %dx%d" % (f.shape[1], f.shape[0]))
+        return rid.value
+
+    def poll(self, cap=64, det_cap=None, wait_us=0):
+        """Up to cap finished results: a list of dicts (id, tag, status, count,
+        latency_ms, queue_ms, dets: DET_DTYPE array)."""
+        if det_cap is None:
+            det_cap = cap * int(self.params.max_dets_per_frame)
+        res = (Result * cap)()
+        dets = np.empty(max(det_cap, 1), DET_DTYPE)
+        n = _i32(0)
+        rc = _lib.hog_server_poll(self._h, res, cap, dets.ctypes.data_as(_vp), det_cap, C.byref(n),
+                                  int(wait_us))
+        if rc:
+            raise HogError(rc, "poll")
+        out, off = [], 0
+        for i in range(n.value):
+            r = res[i]
+            out.append(dict(id=r.id, tag=r.tag, status=r.status, count=r.count,
+                            latency_ms=r.latency_ms, queue_ms=r.queue_ms,
+                            device_ms=r.device_ms, batch=r.batch, lane=r.lane,
+                            dets=dets[off:off + r.stored].copy()))
+            off += r.stored
+        return out
+
+    def stats(self):
+        st = ServerStats()
+        _lib.hog_server_get_stats(self._h, C.byref(st))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
 
 
 def hinge_loss(detector, images, labels, weights, recompute=False):

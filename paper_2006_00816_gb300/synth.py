@@ -184,3 +184,10 @@ def arrivals(n_cameras: int = 8, seconds: float = 10.0, period_ms: float = 2.0,
 def serving_cameras():
     """The 8-camera serving mix: four 640x480 and four 1280x1024 streams."""
     return [(640, 480)] * 4 + [(1280, 1024)] * 4
+
+
+def camera_frame(cam: int, index: int, config: int = 5) -> np.ndarray:
+    """Frame ``index`` of camera ``cam`` of the serving mix: an eyeblink
+    stream at that camera's resolution, seeded per camera."""
+    w, h = serving_cameras()[cam]
+    return eyeblink_frame(index, w, h, config=10 * config + cam)

@@ -81,3 +81,37 @@ def test_null_safety(hog):
     hog._lib.hog_destroy(None)
     assert hog._lib.hog_detect(None, None, 0, None, 0, None, None) == hog.HOG_EINVAL
     assert hog._lib.hog_level_geometry(None, 10, 10, None, 0, None) == hog.HOG_EINVAL
+
+
+@pytest.mark.parametrize("field,value", [("max_batch", 0), ("max_batch", 1025), ("max_lanes", 0),
+                                         ("max_lanes", 17), ("queue_cap", 4),
+                                         ("batched_mode", 2), ("mem_reserve", -1)])
+def test_server_rejects_bad_config(hog, field, value):
+    import numpy as np
+    c = hog.default_server_config(**{field: value})
+    if field == "queue_cap":
+        c.max_batch = 8
+    p = hog.default_params()
+    w = np.zeros((1, 10, 10, 31), np.float32)
+    h = C.c_void_p()
+    rc = hog._lib.hog_server_create(C.byref(p), w.ctypes.data_as(C.c_void_p), 1, C.byref(c),
+                                    C.byref(h))
+    assert rc == hog.HOG_EINVAL and not h.value
+    assert field.split("_")[-1] in hog._lib.hog_server_last_error(None).decode()
+
+
+def test_server_rejects_bad_params_and_nulls(hog):
+    import numpy as np
+    c = hog.default_server_config()
+    assert (c.max_batch, c.max_lanes, c.queue_cap, c.batched_mode) == (8, 3, 64, -1)
+    p = hog.default_params(cell=4)
+    w = np.zeros((1, 10, 10, 31), np.float32)
+    h = C.c_void_p()
+    rc = hog._lib.hog_server_create(C.byref(p), w.ctypes.data_as(C.c_void_p), 1, C.byref(c),
+                                    C.byref(h))
+    assert rc == hog.HOG_EINVAL and not h.value
+    assert hog._lib.hog_server_create(C.byref(p), None, 1, None, C.byref(h)) == hog.HOG_EINVAL
+    n = C.c_int32(5)
+    assert hog._lib.hog_server_submit(None, None, 1, 1, 1, 0, None) == hog.HOG_EINVAL
+    assert hog._lib.hog_server_poll(None, None, 0, None, 0, C.byref(n), 0) == hog.HOG_EINVAL
+    hog._lib.hog_server_destroy(None)

@@ -129,13 +129,18 @@ def _kept_set(rows):
                    float(np.float32(r["score"]))) for r in rows)
 
 
-@pytest.mark.parametrize("case", ["cfg1", "eyeblink5", "skip1", "hd720"])
+@pytest.mark.parametrize("case", ["cfg1", "eyeblink5", "skip1", "hd720", "sxga"])
 def test_nms_exact_on_gpu_scores(H, oracle, synth, case):
-    """hd720 has 35k window positions: its workspace lives in global memory."""
+    """Every suppression launch shape (one CTA per frame, clusters of 2..16
+    CTAs, automatic) keeps exactly the oracle's greedy set.  hd720 (35k
+    window positions) and sxga (55k) do not fit one CTA's shared memory: the
+    one-CTA form runs from global memory there."""
     if case == "cfg1":
         f, W, skip = synth.single_frame(320, 240), synth.filters(1, config=1), 0
     elif case == "hd720":
         f, W, skip = synth.eyeblink_frame(2, 1280, 720, config=3), synth.filters(5), 0
+    elif case == "sxga":
+        f, W, skip = synth.camera_frame(4, 3), synth.filters(5), 0
     else:
         f, W = synth.eyeblink_frame(7), synth.filters(5)
         skip = 1 if case == "skip1" else 0
@@ -145,17 +150,43 @@ def test_nms_exact_on_gpu_scores(H, oracle, synth, case):
     scores = det.scores(ft)
     cands = _gpu_candidates(oracle, scores, w, h, skip=skip)
     srt, keep = oracle.nms(cands, 0.5)
-    dets, counts = det.detect([ft])
-    assert counts[0] == keep.sum() == len(dets)
-    assert _kept_set(dets) == _kept_set(srt[keep])
-    # boxes are the FP64 mapping, bit for bit
     ob = {(int(r["level"]), int(r["u"]), int(r["v"])): (r["x"], r["y"], r["w"], r["h"])
           for r in srt[keep]}
-    for r in dets:
-        assert ob[(int(r["level"]), int(r["u"]), int(r["v"]))] == (r["x"], r["y"], r["w"], r["h"])
-    # output order: (level, u, v)
-    key = [(int(r["level"]), int(r["u"]), int(r["v"])) for r in dets]
-    assert key == sorted(key)
+    for c in (1, 2, 4, 8, 16, 0):
+        det.set_nms_cluster(c)
+        dets, counts = det.detect([ft])
+        assert counts[0] == keep.sum() == len(dets), c
+        assert _kept_set(dets) == _kept_set(srt[keep]), c
+        # boxes are the FP64 mapping, bit for bit
+        for r in dets:
+            assert ob[(int(r["level"]), int(r["u"]), int(r["v"]))] == (r["x"], r["y"], r["w"], r["h"])
+        # output order: (level, u, v)
+        key = [(int(r["level"]), int(r["u"]), int(r["v"])) for r in dets]
+        assert key == sorted(key), c
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_nms_cluster_sizes_agree_on_batches(H, synth, batched):
+    """Mixed batches (including frames with no level and single-level
+    frames): every cluster size gives the one-CTA result bit for bit."""
+    frames = [dev(f) for f in synth.mixed_frames(7)] + [
+        dev(synth.camera_frame(5, 1)), dev(np.full((60, 300), 7, np.uint8)),
+        dev(synth.single_frame(100, 90))]
+    det = H.Detector(synth.filters(5), max_w=1280, max_h=1024, max_batch=10)
+    det.set_nms_cluster(1)
+    ref, rc = det.detect(frames, batched=batched)
+    assert det.nms_cluster_size(10, 1280, 1024) == 1
+    for c in (2, 4, 8, 16, 0):
+        det.set_nms_cluster(c)
+        for _ in range(2):                      # eager, then graph capture when batched
+            got, gc = det.detect(frames, batched=batched)
+            assert gc.tolist() == rc.tolist(), c
+            assert got.tobytes() == ref.tobytes(), c
+    det.set_nms_cluster(0)
+    assert det.nms_cluster_size(1, 1280, 1024) >= 2
+    assert det.nms_cluster_size(152, 640, 480) == 1
+    with pytest.raises(H.HogError):
+        det.set_nms_cluster(3)
 
 
 def test_candidates_match_oracle(H, oracle, synth):
