@@ -46,7 +46,7 @@ PAPER_CONTEXT = {"ms_per_frame": 0.333, "frames_per_s": 3003,
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--frames", type=int, default=1000)
@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-warmup", type=float, default=1.0)
+    ap.add_argument("--mixed-frames", type=int, default=256)
+    ap.add_argument("--backward-reps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -64,6 +66,30 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x, device=None):
+    """The largest x over all ranks (every rank gets it); x itself when no
+    process group is running.  Replicas share no data: this is the only
+    collective, used for timing."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_frames(rank, n):
+    """First frame index of a replica's own slice of the seeded stream."""
+    return rank * n
+
+
+def whole_job_rate(ws, units_per_rank, slowest_s):
+    """Units per second of the whole job: every rank's units over the
+    slowest rank's time."""
+    return ws * units_per_rank / slowest_s
 
 
 # ---------------------------------------------------------------- clocks
@@ -81,7 +107,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -90,9 +116,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, window=None):
+        """Median clocks over the samples that arrived inside window
+        (t0, t1) of time.perf_counter() (all samples when None)."""
         if not self.proc:
             return None
         self.proc.terminate()
@@ -102,7 +130,9 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if window is not None and not (window[0] <= ts <= window[1] + 0.1):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -232,6 +262,91 @@ def run_serving(hog, synth, W, seconds, warm, mode, lanes=4, max_batch=16, camer
     }
 
 
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def run_mixed(hog, synth, W, n, reps, dev, barrier):
+    """Mixed-resolution batch (seeded uniform mix of 320x240, 640x480,
+    1280x720, 1280x1024): the batched call (autotuned mode, graphs) against
+    the plain path (one call per frame)."""
+    import torch
+    host = synth.mixed_frames(n)
+    frames = [torch.from_numpy(f).to(dev) for f in host]
+    det = hog.Detector(W, max_w=1280, max_h=1024, max_batch=n)
+    mode, policy = det.autotune(frames)
+    out_np, _keep = hog.pinned_dets(n * 4096)
+    for _ in range(3):
+        det.detect(frames, out=out_np, batched=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        det.detect(frames, out=out_np, batched=True)
+    barrier()
+    batched_s = (time.perf_counter() - t0) / reps
+    det.close()
+    plain = hog.Detector(W, max_w=1280, max_h=1024, max_batch=1)
+    for f in frames[:8]:
+        plain.detect([f], out=out_np)
+    barrier()
+    lat = []
+    t0 = time.perf_counter()
+    for f in frames:
+        s = time.perf_counter()
+        plain.detect([f], out=out_np)
+        lat.append((time.perf_counter() - s) * 1e3)
+    plain_s = time.perf_counter() - t0
+    plain.close()
+    px = sum(f.size for f in host)
+    return {"workload": "%d frames, seeded uniform mix of 320x240/640x480/1280x720/1280x1024, "
+                        "5 filters" % n,
+            "batched_frames_per_s": n / batched_s, "batched_ms_per_batch": batched_s * 1e3,
+            "plain_frames_per_s": n / plain_s, "plain_p50_ms": statistics.median(lat),
+            "plain_p99_ms": float(np.percentile(lat, 99)), "speedup": plain_s / batched_s,
+            "mode": "fused" if mode == 1 else "per-stage", "corr_tile_policy": policy,
+            "megapixels_per_s": px / batched_s / 1e6}
+
+
+def run_backward(hog, synth, reps, dev, barrier):
+    """Adjoint: hinge loss on the best window of one filter over 64 seeded
+    128x128 crops; time per hog_backward call (loss, dW and dI)."""
+    import torch
+    imgs, labels = synth.crops(64, size=128, config=4)
+    W = synth.filters(1, config=4)[0]
+    det = hog.Detector(W[None], max_w=128, max_h=128, max_batch=1)
+    ti = torch.from_numpy(imgs.astype(np.float32)).to(dev)
+    tl = torch.from_numpy(labels.astype(np.float32)).to(dev)
+    tw = torch.from_numpy(W).to(dev)
+    out = {}
+    for name, rec in (("stored", False), ("recompute", True)):
+        for _ in range(3):
+            det.backward(ti, tl, tw, recompute=rec)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            det.backward(ti, tl, tw, recompute=rec)
+        barrier()
+        out[name + "_ms"] = (time.perf_counter() - t0) / reps * 1e3
+    det.close()
+    out["crops_per_s"] = 64 / (out["stored_ms"] / 1e3)
+    out["workload"] = "64 crops 128x128, 1 filter, loss + dW + dI per call"
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -253,7 +368,7 @@ def main():
     from paper_2006_00816_gb300 import hog
 
     nfr = args.frames
-    host = synth.eyeblink_stream(nfr, start=rank * nfr)          # replica r: its own frames
+    host = synth.eyeblink_stream(nfr, start=replica_frames(rank, nfr))   # replica r: own frames
     W = synth.filters(NF)
     frames_dev = torch.from_numpy(host).to(dev)
     frames = [frames_dev[i] for i in range(nfr)]
@@ -270,13 +385,6 @@ def main():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
-
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
 
     # ---- autotune on the first batch (tile-shape policy, fused vs per-stage)
     tune_path = os.path.join("/tmp", "hog_gb300_tune_%d.json" % os.getpid())
@@ -296,19 +404,23 @@ def main():
             dets += int(c.sum())
         return ms, dets
 
-    # ---- batched path (autotuned mode, CUDA graphs): warm-up, then K timed steps
-    run_steps(args.warmup)
+    # ---- batched path (autotuned mode, CUDA graphs): warm-up, then K timed
+    # steps; clocks are sampled from before the warm-up and kept for the
+    # samples that arrive inside the timed region
     sampler = ClockSampler(dev.index)
     sampler.start()
+    run_steps(args.warmup)
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
     ev0.record(stream)
     chunk_ms, total_dets = run_steps(args.steps)
     ev1.record(stream)
     barrier()
-    clocks = sampler.stop()
-    step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
-    fps = ws * nfr / (step_ms / 1e3)
+    w1 = time.perf_counter()
+    clocks = sampler.stop(window=(w0, w1))
+    step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev)
+    fps = whole_job_rate(ws, nfr, step_ms / 1e3)
 
     # ---- the other batched mode, for comparison
     other = 1 - mode
@@ -318,7 +430,7 @@ def main():
     t0 = time.perf_counter()
     run_steps(args.steps)
     barrier()
-    other_fps = ws * nfr * args.steps / max_over_ranks(time.perf_counter() - t0)
+    other_fps = whole_job_rate(ws, nfr * args.steps, max_over_ranks(time.perf_counter() - t0, dev))
     det.set_batched_mode(mode)
 
     # ---- profiled pass of the same workload: CUDA events around each stage
@@ -372,8 +484,8 @@ def main():
     for _ in range(args.steps):
         d, c = det.detect_host(host_frames, out=out_np)
         e2e_dets += int(c.sum())
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_fps = ws * nfr * args.steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_fps = whole_job_rate(ws, nfr * args.steps, e2e_s)
     h2d = nfr * W0 * H0
     d2h = (e2e_dets // args.steps) * 56 + nfr * 4
 
@@ -385,6 +497,12 @@ def main():
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+
+    # ---- mixed-resolution batches and the adjoint
+    mixed = run_mixed(hog, synth, W, args.mixed_frames, args.steps, dev, barrier) \
+        if args.mixed_frames > 0 else None
+    backward = run_backward(hog, synth, args.backward_reps, dev, barrier) \
+        if args.backward_reps > 0 else None
 
     # ---- serving: continuous batching over 8 camera streams (rank 0 of a
     # replica job serves its own GPU like every other rank)
@@ -402,8 +520,12 @@ def main():
         t0 = time.perf_counter()
         _, used = oracle.detect_many(host[:ns], W, n_threads=cores)
         dt = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.detect_many(host[:2], W, n_threads=1)
+        dt1 = time.perf_counter() - t0
         cpu = {"value": ns / dt, "unit": "frames/s", "cores": used, "kind": "oracle",
-               "sample": "first %d frames of the stream, FP64, OpenMP over frames" % ns}
+               "sample": "first %d frames of the stream, FP64, OpenMP over frames" % ns,
+               "single_thread_frames_per_s": 2 / dt1, "cpu_model": cpu_model()}
 
     if rank == 0:
         line = {
@@ -424,6 +546,8 @@ def main():
             "plain": {"frames_per_s": plain_fps, "p50_ms": statistics.median(lat),
                       "p99_ms": float(np.percentile(lat, 99)), "frames": nplain,
                       "stage_ms_per_frame": plain_stages},
+            "mixed_batch": mixed,
+            "backward": backward,
             "serving": serving,
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -31,6 +31,11 @@ constexpr int FEAT_TX = 32, FEAT_TY = 8;         // cells per CTA (256 threads)
 #ifndef HOG_CORR_MINB
 #define HOG_CORR_MINB 3
 #endif
+// Correlation accumulators: 1 = (even, odd) channel pairs updated by packed
+// FP32 FMAs, 0 = one FP32 sum per window and filter (fewer registers).
+#ifndef HOG_CORR_PACKED
+#define HOG_CORR_PACKED 0
+#endif
 constexpr int CORR_NSHAPE = 3;
 __host__ __device__ constexpr bool corr_shape_ok(int s) { return HOG_CORR_MINB < 4 || s != 1; }
 __host__ __device__ constexpr int corr_tu(int s) { return s == 0 ? 8 : (s == 1 ? 4 : 16); }

@@ -6,11 +6,11 @@
 // frames as they arrive from several cameras:
 //   - hog_server_submit copies a frame into a pinned host slot (the queue
 //     holds queue_cap frames; a full queue refuses with HOG_EBUSY);
-//   - a worker thread forms a batch from whatever is waiting whenever a
-//     lane is free, copies it to that lane's device frame slots and
-//     enqueues the detection on the lane's stream; several lanes (each a
-//     context with its own arenas and stream) keep batches in flight at
-//     once, so requests that arrive while others are on the GPU join the
+//   - a worker thread forms a batch whenever a lane is free: the oldest
+//     waiting frame and the other waiting frames of its size, copied to
+//     that lane's device frame slots, detection enqueued on the lane's
+//     stream; several lanes (each a context with its own arenas and
+//     stream) keep batches in flight at once, so requests that arrive while others are on the GPU join the
 //     next batch and their work overlaps on the device;
 //   - completion is signalled by a host callback on the lane's stream; the
 //     worker moves the lane's results to the completed queue, frees the
@@ -150,10 +150,6 @@ void harvest(hog_server *s, Lane *ln) {
 }
 
 void dispatch(hog_server *s, Lane *ln, std::vector<Request> &&batch) {
-    // canonical order (by size) so that the lane's cached plans and graphs hit
-    std::stable_sort(batch.begin(), batch.end(), [](const Request &a, const Request &b) {
-        return a.w != b.w ? a.w < b.w : a.h < b.h;
-    });
     const int nb = (int)batch.size();
     std::vector<hog_frame> frames(nb);
     const double t = now_ms();
@@ -217,10 +213,20 @@ void worker_loop(hog_server *s) {
         for (Lane *ln : s->lanes)
             if (!ln->busy) { free_lane = ln; break; }
         if (free_lane && !s->pending.empty()) {
+            // the oldest request and the waiting requests of its frame size,
+            // in arrival order: one size per batch, so a lane's cached plans
+            // and graphs stay few (size x count) and small frames never wait
+            // for a large frame's suppression in the same batch
             std::vector<Request> batch;
-            while (!s->pending.empty() && (int)batch.size() < s->cfg.max_batch) {
-                batch.push_back(s->pending.front());
-                s->pending.pop_front();
+            const int bw = s->pending.front().w, bh = s->pending.front().h;
+            for (auto it = s->pending.begin();
+                 it != s->pending.end() && (int)batch.size() < s->cfg.max_batch;) {
+                if (it->w == bw && it->h == bh) {
+                    batch.push_back(*it);
+                    it = s->pending.erase(it);
+                } else {
+                    ++it;
+                }
             }
             int inflight = 0;
             for (Lane *ln : s->lanes) inflight += ln->busy ? (int)ln->batch.size() : 0;

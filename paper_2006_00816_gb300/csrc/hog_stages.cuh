@@ -82,7 +82,8 @@ __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
 // C, S = round(2^20 cos, 2^20 sin).  For every 8-bit gradient this equals
 // the exact test (smallest |dy cos - dx sin| on the grid 1.3e-3 = 1340 units
 // at 2^20, against at most 255 units of rounding); products fit in int32.
-// dx == 0 (the only exact tie) goes to bin 4 (dy > 0) or 13.
+// dx == 0 (the only exact tie) goes to bin 4 (dy > 0) or 13.  Branch-free:
+// the quadrant is resolved with selects.
 namespace hist_cfg {
 constexpr int NT = HIST_BX * HIST_BY;          // 256 threads, one per block
 constexpr int PX = HIST_BX * CELL + 2;         // 130 staged columns (blocks + 1-px halo)
@@ -96,13 +97,16 @@ constexpr size_t SMEM = SMEM_PART + SMEM_SRC + SMEM_XB;             // 95,056
 }  // namespace hist_cfg
 
 __device__ __forceinline__ int orientation_bin_i(int dx, int dy) {
-    if (dx == 0) return dy > 0 ? 4 : 13;
     const int ax = dx < 0 ? -dx : dx;
     const int ay = dy < 0 ? -dy : dy;
     const int q = (ay * 1032646 - ax * 182083 > 0) + (ay * 908093 - ax * 524288 > 0) +
                   (ay * 674012 - ax * 803256 > 0) + (ay * 358634 - ax * 985339 > 0);
-    if (dx > 0) return dy >= 0 ? q : (q == 0 ? 0 : 18 - q);
-    return dy >= 0 ? 9 - q : 9 + q;
+    // dx == 0 (q = 4 when dy != 0) is placed on the right half-plane for
+    // dy > 0 (bin 4) and on the left one for dy < 0 (bin 13); selects only
+    const bool right = dx > 0 || (dx == 0 && dy > 0);
+    const int up = right ? q : 9 - q;
+    const int dn = right ? (q == 0 ? 0 : 18 - q) : 9 + q;
+    return dy >= 0 ? up : dn;
 }
 
 // Tent weight of footprint offset t (0..15) in sixteenths: 16 - |2t - 15|.
@@ -146,7 +150,11 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
     cp_async_wait_all();
     __syncthreads();
 
-    // one 8x8 block per thread: pixels X = 8 bj - 4 + ox, Y = 8 bi - 4 + oy
+    // one 8x8 block per thread: pixels X = 8 bj - 4 + ox, Y = 8 bi - 4 + oy.
+    // Pixels outside the voting range (X < 1, X > xmax) read staged bytes
+    // that exist but vote with magnitude 0; zero gradients vote 0 as well
+    // (adding +0 leaves the non-negative partials unchanged).  Magnitude
+    // sqrt(s) of the exact integer s = dx^2 + dy^2 as s * rsqrt(s).
     const int by = t / HIST_BX, bx = t - by * HIST_BX;
     const int X0 = CELL * (j0 + bx) - 4, Y0 = CELL * (i0 + by) - 4;
     float *p0 = part + t;
@@ -162,18 +170,18 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
 #pragma unroll
         for (int ox = 0; ox < 8; ox++) {
             const int X = X0 + ox;
-            if (X < 1 || X > xmax) continue;
             const int dx = (int)mid[X + 1] - (int)mid[X - 1];
             const int dy = (int)dn[X] - (int)up[X];
-            if ((dx | dy) == 0) continue;
             const int b = orientation_bin_i(dx, dy);
-            const float m = sqrtf((float)(dx * dx + dy * dy));
+            const int s2 = dx * dx + dy * dy;
+            float m = (float)s2 * rsqrtf((float)max(s2, 1));
+            m = (X >= 1 && X <= xmax) ? m : 0.0f;
             const float wx1 = tent16(ox), wx0 = tent16(ox + 8);   // to cell cols bj, bj-1
             float *pb = p0 + b * NT;
-            pb[0 * NBIN * NT] += m * (wy0 * wx0);   // cell (bi-1, bj-1)
-            pb[1 * NBIN * NT] += m * (wy0 * wx1);   // cell (bi-1, bj)
-            pb[2 * NBIN * NT] += m * (wy1 * wx0);   // cell (bi,   bj-1)
-            pb[3 * NBIN * NT] += m * (wy1 * wx1);   // cell (bi,   bj)
+            pb[0 * NBIN * NT] = fmaf(m, wy0 * wx0, pb[0 * NBIN * NT]);   // cell (bi-1, bj-1)
+            pb[1 * NBIN * NT] = fmaf(m, wy0 * wx1, pb[1 * NBIN * NT]);   // cell (bi-1, bj)
+            pb[2 * NBIN * NT] = fmaf(m, wy1 * wx0, pb[2 * NBIN * NT]);   // cell (bi,   bj-1)
+            pb[3 * NBIN * NT] = fmaf(m, wy1 * wx1, pb[3 * NBIN * NT]);   // cell (bi,   bj)
         }
     }
     __syncthreads();
@@ -324,17 +332,34 @@ __device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float ep
 // (equal scores: the lowest index).
 //
 // One warp owns one tile of 128 windows (8x16, 4x32 or 16x8, chosen per
-// level on the host); a lane owns 4 consecutive windows of one row for all
-// filters.  Features stream in half-chunks of 4 channels (one float4 per
-// cell of the internal layout): the warp copies the (TU+9) x (TV+9) region
-// of the next half-chunk with cp.async.cg while computing the current one
-// (double buffer, 2 x CORR_BUF4 float4 of warp-private shared memory).  The
-// region's row stride TV+9 is odd, so a quarter-warp's float4 loads fall on
-// distinct bank groups.  For a filter row, a lane loads its 13 float4 once
-// and slides over the 10 filter columns in registers; filter weights are
-// warp-uniform loads through L1.
-constexpr int CORR_WPT = 4;
+// level on the host).  Features stream in half-chunks of 4 channels (one
+// float4 per cell of the internal layout): the warp copies the (TU+9) x
+// (TV+9) region of the next half-chunk with cp.async.cg while computing the
+// current one (double buffer, 2 x CORR_BUF4 float4 of warp-private shared
+// memory).  The half-warps split the channels: lanes 0-15 take channels
+// 0-1 of every float4, lanes 16-31 channels 2-3; within a half-warp a lane
+// owns 8 consecutive windows of one row for all filters, and the two halves'
+// partial scores are added with one shuffle at the end.  For a filter row a
+// lane loads its 17 channel pairs once and slides over the 10 filter
+// columns in registers; each filter weight pair (a half-warp-uniform load
+// through L1) feeds 8 windows, and each accumulator is a (channel 0, channel
+// 1) pair updated by one packed FMA.  Register traffic per FMA from L1 is
+// what bounds this loop: 8 windows per lane halve the weight bytes written
+// back per FMA against 4 windows of all 4 channels.
+constexpr int CORR_WPT = 8;
 constexpr int CORR_BUF4 = HOG_CORR_MINB >= 4 ? 432 : 544;   // 13x41 = 533 needs the 4x32 shape
+
+// acc += (w0 * x0, w1 * x1), one packed FP32 FMA (two IEEE fmas, RN)
+__device__ __forceinline__ void ffma2(float2 &acc, float w0, float w1, float x0, float x1) {
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pc, {%0, %1};\n\t"
+        "fma.rn.f32x2 pc, pa, pb, pc;\n\t"
+        "mov.b64 {%0, %1}, pc;\n\t}"
+        : "+f"(acc.x), "+f"(acc.y)
+        : "f"(w0), "f"(w1), "f"(x0), "f"(x1));
+}
 
 template <int NF>
 __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ descs, Job jb,
@@ -347,11 +372,12 @@ __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ desc
     const int RU = TU + WIN - 1, RV = TV + WIN - 1;
     const int ntv = (d.nv + TV - 1) / TV;
     const int u0 = (tile / ntv) * TU, v0 = (tile % ntv) * TV;
-    const int lr = lane % TU, lc = (lane / TU) * CORR_WPT;   // window row / first column in tile
+    const int half = lane >> 4, l16 = lane & 15;               // channel pair, lane in half
+    const int lr = l16 % TU, lc = (l16 / TU) * CORR_WPT;      // window row / first column in tile
 
     const float4 *feat4 = reinterpret_cast<const float4 *>(d.feat);
     const size_t plane4 = (size_t)d.cy * d.cx * 2;           // float4 per chunk plane
-    const float4 *w4 = reinterpret_cast<const float4 *>(wchunks);
+    const float2 *w2 = reinterpret_cast<const float2 *>(wchunks);
 
     // copy half-chunk h (chunk h/2, channels 4*(h&1)..+3) of the tile region
     auto stage = [&](int h, float4 *dst) {
@@ -366,11 +392,21 @@ __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ desc
         cp_async_commit();
     };
 
+#if HOG_CORR_PACKED
+    // acc[j][f] = (channel 2*half, channel 2*half + 1) partial sums
+    float2 acc[CORR_WPT][NF];
+#pragma unroll
+    for (int j = 0; j < CORR_WPT; j++)
+#pragma unroll
+        for (int f = 0; f < NF; f++) acc[j][f] = make_float2(0.0f, 0.0f);
+#else
+    // acc[j][f] = partial sum over this half's two channels
     float acc[CORR_WPT][NF];
 #pragma unroll
     for (int j = 0; j < CORR_WPT; j++)
 #pragma unroll
         for (int f = 0; f < NF; f++) acc[j][f] = 0.0f;
+#endif
 
     stage(0, buf0);
 #pragma unroll 1
@@ -384,29 +420,31 @@ __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ desc
         }
         __syncwarp();
         const int ch = h >> 1, c4 = h & 1;
-        const float4 *wch = w4 + (size_t)ch * NF * 200 + c4;
+        // weights: float4 index ((chunk*NF + f)*100 + a*10 + b)*2 + c4, as
+        // float2 pairs: twice that plus the half
+        const float2 *wch = w2 + ((size_t)ch * NF * 200 + c4) * 2 + half;
 #pragma unroll 1
         for (int a = 0; a < WIN; a++) {
-            const float4 *frow = cur + (lr + a) * RV + lc;
-            float4 fv[CORR_WPT + WIN - 1];
+            const float2 *frow =
+                reinterpret_cast<const float2 *>(cur + (lr + a) * RV + lc) + half;
+            float2 fv[CORR_WPT + WIN - 1];
 #pragma unroll
-            for (int j = 0; j < CORR_WPT + WIN - 1; j++) fv[j] = frow[j];
+            for (int j = 0; j < CORR_WPT + WIN - 1; j++) fv[j] = frow[2 * j];
 #pragma unroll
             for (int b = 0; b < WIN; b++) {
-                float4 wv[NF];
+                float2 wv[NF];
 #pragma unroll
-                for (int f = 0; f < NF; f++) wv[f] = __ldg(wch + ((f * WIN + a) * WIN + b) * 2);
+                for (int f = 0; f < NF; f++) wv[f] = __ldg(wch + ((f * WIN + a) * WIN + b) * 4);
 #pragma unroll
                 for (int j = 0; j < CORR_WPT; j++) {
-                    const float4 x = fv[j + b];
+                    const float2 x = fv[j + b];
 #pragma unroll
                     for (int f = 0; f < NF; f++) {
-                        float s = acc[j][f];
-                        s = fmaf(wv[f].x, x.x, s);
-                        s = fmaf(wv[f].y, x.y, s);
-                        s = fmaf(wv[f].z, x.z, s);
-                        s = fmaf(wv[f].w, x.w, s);
-                        acc[j][f] = s;
+#if HOG_CORR_PACKED
+                        ffma2(acc[j][f], wv[f].x, wv[f].y, x.x, x.y);
+#else
+                        acc[j][f] = fmaf(wv[f].y, x.y, fmaf(wv[f].x, x.x, acc[j][f]));
+#endif
                     }
                 }
             }
@@ -414,22 +452,36 @@ __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ desc
         __syncwarp();   // every lane is done with `cur` before it is refilled
     }
 
+    // score = this half's two channels + the other half's (lane ^ 16)
+    float sc[CORR_WPT][NF];
+#pragma unroll
+    for (int j = 0; j < CORR_WPT; j++)
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+#if HOG_CORR_PACKED
+            const float mine = acc[j][f].x + acc[j][f].y;
+#else
+            const float mine = acc[j][f];
+#endif
+            const float other = __shfl_xor_sync(0xffffffffu, mine, 16);
+            sc[j][f] = half == 0 ? mine + other : other + mine;
+        }
     const int u = u0 + lr;
-    if (u >= d.nu) return;
+    if (half != 0 || u >= d.nu) return;
 #pragma unroll
     for (int j = 0; j < CORR_WPT; j++) {
         const int v = v0 + lc + j;
         if (v >= d.nv) break;
-        float best = acc[j][0];
+        float best = sc[j][0];
         int fb = 0;
 #pragma unroll
         for (int f = 1; f < NF; f++)
-            if (f < nf_real && acc[j][f] > best) { best = acc[j][f]; fb = f; }
+            if (f < nf_real && sc[j][f] > best) { best = sc[j][f]; fb = f; }
         if (d.scores_user) {
 #pragma unroll
             for (int f = 0; f < NF; f++)
                 if (f < nf_real)
-                    d.scores_user[((size_t)f * d.nu + u) * d.nv + v] = acc[j][f];
+                    d.scores_user[((size_t)f * d.nu + u) * d.nv + v] = sc[j][f];
         }
         if (d.keys)
             d.keys[(size_t)u * d.nv + v] =

@@ -9,10 +9,12 @@ namespace hogk {
 namespace {
 constexpr int NT = 32 * CORR_WARPS;
 constexpr size_t SMEM = sizeof(float4) * CORR_BUF4 * 2 * CORR_WARPS;
+// 8 filters need 128 accumulator registers per lane: two CTAs per SM
+constexpr int corr_minb(int nf) { return nf > 5 ? 2 : HOG_CORR_MINB; }
 }  // namespace
 
 template <int NF>
-__global__ void __launch_bounds__(NT, HOG_CORR_MINB) corr_kernel(const LevelDesc *__restrict__ descs,
+__global__ void __launch_bounds__(NT, corr_minb(NF)) corr_kernel(const LevelDesc *__restrict__ descs,
                                                                  const Job *__restrict__ jobs,
                                                                  int njobs,
                                                                  const float *__restrict__ wchunks,
