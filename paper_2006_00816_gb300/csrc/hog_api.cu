@@ -94,7 +94,7 @@ int compute_geometry(const hog_params &p, int W, int H, Geometry &g) {
 namespace {
 struct PlanLayout {
     size_t items = 0;
-    size_t descs = 0, frames = 0, hist = 0, feat = 0, corr = 0, total = 0;
+    size_t descs = 0, frames = 0, hist = 0, feat = 0, corr = 0, corrf = 0, total = 0;
     std::vector<size_t> pyr;
     std::vector<int> npyr;
 };
@@ -325,6 +325,7 @@ struct PlanBuilder {
     std::vector<FrameDesc> frames;
     std::vector<std::vector<Job>> pyr;   // per step (target level)
     std::vector<Job> hist, feat, corr;
+    std::vector<Job> corrf;              // correlation jobs of the fused launch (8x16, 16x8 tiles)
     std::vector<FusedItem> items;        // persistent fused launch (built on demand)
     int nctr = 0;
 };
@@ -342,7 +343,7 @@ void build_fused_items(PlanBuilder &pb) {
     for (const Job &j : pb.feat) nfeat[j.desc]++;
     struct Keyed { int depth, kind, desc, tile; FusedItem it; };
     std::vector<Keyed> v;
-    v.reserve(pb.hist.size() + pb.feat.size() + pb.corr.size() / 4 + 1024);
+    v.reserve(pb.hist.size() + pb.feat.size() + pb.corrf.size() / 4 + 1024);
     for (const auto &seg : pb.pyr)
         for (const Job &j : seg) {
             const LevelDesc &d = pb.descs[j.desc];
@@ -361,10 +362,10 @@ void build_fused_items(PlanBuilder &pb) {
         FusedItem it{FUSED_FEAT, j.desc, j.tile, 3 * j.desc + 1, nhist[j.desc], 3 * j.desc + 2};
         v.push_back({d.level + 2, FUSED_FEAT, j.desc, j.tile, it});
     }
-    for (size_t k = 0; k < pb.corr.size();) {
-        const int desc = pb.corr[k].desc;
+    for (size_t k = 0; k < pb.corrf.size();) {
+        const int desc = pb.corrf[k].desc;
         size_t e = k;
-        while (e < pb.corr.size() && pb.corr[e].desc == desc && e - k < 8) e++;
+        while (e < pb.corrf.size() && pb.corrf[e].desc == desc && e - k < 8) e++;
         const LevelDesc &d = pb.descs[desc];
         FusedItem it{FUSED_CORR, (int)k, (int)(e - k), 3 * desc + 2, nfeat[desc], -1};
         v.push_back({d.level + 3, FUSED_CORR, desc, (int)k, it});
@@ -452,6 +453,17 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
                          ((d.nv + corr_tv(pref) - 1) / corr_tv(pref));
             }
             for (int k = 0; k < best_n; k++) pb.corr.push_back({di, (best << 28) | k});
+            // the fused launch stages at most 17x25 cells per warp: 8x16 or
+            // 16x8 tiles, the preferred one if it is one of them
+            int fb = -1, fb_n = 0;
+            for (int sh = 0; sh < CORR_NSHAPE; sh++) {
+                if (!corr_shape_fused(sh)) continue;
+                const int n = ((d.nu + corr_tu(sh) - 1) / corr_tu(sh)) *
+                              ((d.nv + corr_tv(sh) - 1) / corr_tv(sh));
+                if (fb < 0 || n < fb_n || sh == pref) { fb = sh; fb_n = n; }
+                if (sh == pref) break;
+            }
+            for (int k = 0; k < fb_n; k++) pb.corrf.push_back({di, (fb << 28) | k});
         }
     }
     if (o.nms) {
@@ -493,6 +505,7 @@ void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
     L.hist = take(pb.hist.size() * sizeof(Job));
     L.feat = take(pb.feat.size() * sizeof(Job));
     L.corr = take(pb.corr.size() * sizeof(Job));
+    L.corrf = take(pb.corrf.size() * sizeof(Job));
     L.items = take(pb.items.size() * sizeof(FusedItem));
     L.total = off;
     info.nitems = (int)pb.items.size();
@@ -558,6 +571,7 @@ int upload_plan(hog_ctx *ctx, const PlanBuilder &pb, const PlanInfo &info, char 
     std::memcpy(h + L.hist, pb.hist.data(), pb.hist.size() * sizeof(Job));
     std::memcpy(h + L.feat, pb.feat.data(), pb.feat.size() * sizeof(Job));
     std::memcpy(h + L.corr, pb.corr.data(), pb.corr.size() * sizeof(Job));
+    std::memcpy(h + L.corrf, pb.corrf.data(), pb.corrf.size() * sizeof(Job));
     std::memcpy(h + L.items, pb.items.data(), pb.items.size() * sizeof(FusedItem));
     CUDA_TRY(ctx, cudaMemcpyAsync(d_dst ? d_dst : ctx->d_plan, h, L.total, cudaMemcpyHostToDevice,
                                   stream));
@@ -699,7 +713,7 @@ int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStr
     a.items = reinterpret_cast<const FusedItem *>(d + L.items);
     a.nitems = info.nitems;
     a.descs = reinterpret_cast<const LevelDesc *>(d + L.descs);
-    a.jobs = reinterpret_cast<const Job *>(d + L.corr);
+    a.jobs = reinterpret_cast<const Job *>(d + L.corrf);
     a.wchunks = ctx->d_w;
     a.nf_real = ctx->nf;
     a.threshold = ctx->p.threshold;

@@ -38,6 +38,8 @@ constexpr int FEAT_TX = 32, FEAT_TY = 8;         // cells per CTA (256 threads)
 #endif
 constexpr int CORR_NSHAPE = 3;
 __host__ __device__ constexpr bool corr_shape_ok(int s) { return HOG_CORR_MINB < 4 || s != 1; }
+// shapes the persistent fused launch runs (its staging buffers hold 17x25 cells)
+__host__ __device__ constexpr bool corr_shape_fused(int s) { return s != 1; }
 __host__ __device__ constexpr int corr_tu(int s) { return s == 0 ? 8 : (s == 1 ? 4 : 16); }
 __host__ __device__ constexpr int corr_tv(int s) { return s == 0 ? 16 : (s == 1 ? 32 : 8); }
 constexpr int CORR_WARPS = 4;                    // warps (independent tiles) per CTA

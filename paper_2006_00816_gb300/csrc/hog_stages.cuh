@@ -361,7 +361,7 @@ __device__ __forceinline__ void ffma2(float2 &acc, float w0, float w1, float x0,
         : "f"(w0), "f"(w1), "f"(x0), "f"(x1));
 }
 
-template <int NF>
+template <int NF, int BUF4 = CORR_BUF4>
 __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ descs, Job jb,
                                               const float *__restrict__ wchunks, int nf_real,
                                               float threshold, float4 *buf0) {
@@ -411,9 +411,9 @@ __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ desc
     stage(0, buf0);
 #pragma unroll 1
     for (int h = 0; h < 2 * NCHUNK; h++) {
-        float4 *cur = buf0 + (h & 1) * CORR_BUF4;
+        float4 *cur = buf0 + (h & 1) * BUF4;
         if (h + 1 < 2 * NCHUNK) {
-            stage(h + 1, buf0 + ((h + 1) & 1) * CORR_BUF4);
+            stage(h + 1, buf0 + ((h + 1) & 1) * BUF4);
             cp_async_wait_group<1>();
         } else {
             cp_async_wait_group<0>();

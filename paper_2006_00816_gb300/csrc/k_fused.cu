@@ -30,7 +30,11 @@ namespace hogk {
 namespace {
 constexpr int FUSED_NT = 256;
 constexpr int FUSED_CORR_WARPS = FUSED_NT / 32;   // 8 warp tiles per correlation item
-constexpr size_t FUSED_SMEM_CORR = sizeof(float4) * CORR_BUF4 * 2 * FUSED_CORR_WARPS;
+// 8x16 and 16x8 tiles only (17x25 = 425 cells): 110.6 KB of staging, so two
+// CTAs fit on an SM
+constexpr int FUSED_BUF4 = 432;
+static_assert((8 + WIN - 1) * (16 + WIN - 1) <= FUSED_BUF4, "fused staging holds an 8x16 tile region");
+constexpr size_t FUSED_SMEM_CORR = sizeof(float4) * FUSED_BUF4 * 2 * FUSED_CORR_WARPS;
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t FUSED_SMEM = cmax(cmax(FUSED_SMEM_CORR, hist_cfg::SMEM), feat_cfg::SMEM);
 constexpr long long FUSED_SPIN_LIMIT = 1ll << 24;
@@ -42,8 +46,11 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 }
 }  // namespace
 
+// two CTAs per SM (128 registers) up to 5 filters; 8 filters need more registers
+constexpr int fused_minb(int nf) { return nf <= 5 ? 2 : 1; }
+
 template <int NF>
-__global__ void __launch_bounds__(FUSED_NT, HOG_CORR_MINB >= 4 ? 2 : 1) fused_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(FUSED_NT, fused_minb(NF)) fused_kernel(FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item, s_ok;
     const int t = threadIdx.x;
@@ -86,8 +93,9 @@ __global__ void __launch_bounds__(FUSED_NT, HOG_CORR_MINB >= 4 ? 2 : 1) fused_ke
         case FUSED_CORR: {
             const int w = t >> 5;
             if (w < item.b)
-                corr_warp_job<NF>(a.descs, a.jobs[item.a + w], a.wchunks, a.nf_real, a.threshold,
-                                  reinterpret_cast<float4 *>(smem) + (size_t)w * 2 * CORR_BUF4);
+                corr_warp_job<NF, FUSED_BUF4>(a.descs, a.jobs[item.a + w], a.wchunks, a.nf_real,
+                                              a.threshold,
+                                              reinterpret_cast<float4 *>(smem) + (size_t)w * 2 * FUSED_BUF4);
             break;
         }
         default:
