@@ -262,6 +262,76 @@ def run_serving(hog, synth, W, seconds, warm, mode, lanes=4, max_batch=16, camer
     }
 
 
+def level_cells(hog, w, h):
+    """(cells, windows, pixels) per pyramid level of a w x h frame."""
+    return [(cx * cy, max(cx - 9, 0) * max(cy - 9, 0), lw * lh)
+            for lw, lh, cx, cy, _ in hog.level_geometry(w, h)]
+
+
+def corr_roofline(hog, stats, mode, engine, nfr, steps, peaks):
+    """Roofline of the correlation (the path's FLOPs: 6,200 per window and
+    filter) from the CUDA-event stage times of the profiled pass: against
+    the measured dense bf16 peak (fp16 has the same nominal rate) for the
+    tensor-core engine, against the derived FP32 FMA peak for the CUDA
+    cores.  A launch here is one batch's correlation stage (tensor cores:
+    GEMM + row-shift reduction)."""
+    key = "corr" if mode == 0 else "fused"
+    ms, launches, units = stats[key]
+    flops = units * CORR_FLOP_PER_UNIT
+    achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else None
+    batches = max(launches // (2 if engine == 1 and mode == 0 else 1), 1)
+    if engine == 1 and mode == 0:
+        lv = level_cells(hog, W0, H0)
+        tiles = sum((c + 127) // 128 for c, _, _ in lv) * nfr * steps
+        n = (10 * NF + 15) // 16 * 16
+        executed = tiles * 3 * 20 * 2 * 128 * n * 16 / (ms / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops", 1901.0)
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "corr_tc_kernel<5> + corr_tc_reduce_kernel<5> (tcgen05, fp16 hi/lo x3)",
+                "flop_per_launch": flops / batches, "avg_launch_ms": ms / batches,
+                "executed_tensor_tflops": executed,
+                "executed_over_algorithmic": executed / achieved if achieved else None,
+                "vs_fp32_cuda_core_peak": achieved / FP32_PEAK_TFLOPS if achieved else None,
+                "flop_note": "algorithmic correlation FLOPs (6,200 per window x filter); the "
+                             "tensor pipe executes 3 fp16 passes over all cells (N padded to 64)",
+                "peak_note": "measured dense bf16 TFLOP/s (MEASURED_PEAKS.json, burst); fp16 "
+                             "dense has the same nominal rate"}
+    return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS if achieved else None, "traffic": None,
+            "kernel": "fused_kernel<5> (pyramid..correlation)" if mode == 1 else "corr_kernel<5>",
+            "flop_per_launch": flops / batches, "avg_launch_ms": ms / batches,
+            "flop_note": "correlation FLOPs only (6,200 per window x filter)",
+            "peak_note": "derived FP32 FMA peak (152 SM x 128 lanes x 2 x 2.07 GHz)"}
+
+
+def stage_table(hog, stats, nfr, steps, engine, peaks):
+    """Per stage: CUDA-event ms per step and algorithmic HBM bytes (inputs
+    read once, outputs written once) as GB/s and a fraction of the measured
+    copy bandwidth."""
+    lv = level_cells(hog, W0, H0)
+    cells = sum(c for c, _, _ in lv)
+    wins = sum(wn for _, wn, _ in lv)
+    px = [p for _, _, p in lv]
+    b = {"pyramid": sum(px[l - 1] + px[l] for l in range(1, len(px))),
+         "hist": sum(px) + cells * 18 * 4,
+         "feat": cells * 18 * 4 + cells * 128 + (cells * 128 if engine == 1 else 0),
+         "corr": (cells * 128 + cells * 10 * NF * 4 * 2 + wins * 8) if engine == 1
+                 else cells * 128 + wins * 8,
+         "nms": wins * 8 + 447 * 56}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {}
+    for k, (ms, launches, units) in stats.items():
+        if launches == 0 or k == "fused":
+            continue
+        t = ms / steps / 1e3
+        gbs = b.get(k, 0) * nfr / t / 1e9 if t > 0 else None
+        out[k] = {"ms_per_step": ms / steps, "launches_per_step": launches / steps,
+                  "algorithmic_bytes_per_frame": b.get(k), "gbs": gbs,
+                  "hbm_frac": gbs / hbm if gbs else None}
+    return out
+
+
 def cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -389,6 +459,7 @@ def main():
     # ---- autotune on the first batch (tile-shape policy, fused vs per-stage)
     tune_path = os.path.join("/tmp", "hog_gb300_tune_%d.json" % os.getpid())
     mode, corr_policy = det.autotune(frames[:args.batch], cache_path=tune_path)
+    engine = det.corr_engine()
     try:
         tune = json.load(open(tune_path))
         os.remove(tune_path)
@@ -440,18 +511,14 @@ def main():
     run_steps(args.steps)
     stats = det.stage_stats(reset=True)
     det.set_profiling(False)
-    key = "fused" if mode == 1 else "corr"
-    k_ms, k_launches, k_units = stats[key]
-    k_flops = k_units * CORR_FLOP_PER_UNIT
-    achieved = k_flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None,
-                "traffic": None,
-                "kernel": "fused_kernel<5> (pyramid..correlation)" if mode == 1 else "corr_kernel<5>",
-                "flop_per_launch": k_flops / max(k_launches, 1),
-                "avg_launch_ms": k_ms / max(k_launches, 1),
-                "flop_note": "correlation FLOPs only (6,200 per window x filter)",
-                "peak_note": "derived FP32 FMA peak (152 SM x 128 lanes x 2 x 2.07 GHz)"}
+    engine = det.corr_engine()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    roofline = corr_roofline(hog, stats, mode, engine, nfr, args.steps, peaks)
+    stages = stage_table(hog, stats, nfr, args.steps, engine, peaks)
     stage_ms = {k: v[0] / args.steps for k, v in stats.items() if v[1] > 0}
     nchunks = (nfr + args.batch - 1) // args.batch
     gpu_launches = int(sum(v[1] for v in stats.values())) + nchunks * args.steps   # + pack
@@ -491,11 +558,6 @@ def main():
 
     # ---- HBM view: algorithmic bytes (frame in, boxes out) per step
     hbm_bytes = h2d + d2h
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
 
     # ---- mixed-resolution batches and the adjoint
@@ -537,6 +599,7 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs 307 MB per step exceed the 129 MB L2; no flush"},
             "batched": {"frames_per_s": fps, "mode": "fused" if mode == 1 else "per-stage",
+                        "corr_engine": "tensor cores (tcgen05)" if engine == 1 else "FP32 CUDA cores",
                         "graphs": True, "corr_tile_policy": corr_policy,
                         "other_mode_frames_per_s": other_fps,
                         "step_p50_ms": statistics.median(chunk_ms),
@@ -555,6 +618,7 @@ def main():
             "hbm": {"algorithmic_gbs": hbm_bytes / (step_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
                     "frac": hbm_bytes / (step_ms / 1e3) / 1e9 / hbm_peak},
             "stage_ms_per_step": stage_ms,
+            "stages": stages,
             "gpu_launches": gpu_launches,
             "cpu_baseline": cpu,
             "clocks": clocks,

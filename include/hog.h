@@ -180,6 +180,22 @@ int hog_detect_batched(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, 
  * fused launch (default), 0 = one launch per stage (both as graphs). */
 int hog_set_batched_mode(hog_ctx *ctx, int32_t mode);
 
+/* Correlation engine.  0: FP32 CUDA cores, one warp per 128-window tile.
+ * 1 (default when its buffers can be allocated at hog_create): tcgen05
+ * tensor cores -- for each filter row a,
+ * G[a][p] = sum over 10 cell shifts and 32 channels of feat[p + b] W[a][b]
+ * is a GEMM over the level's cells (M = 128 cells per MMA, K = 320, N = 10
+ * rows x F filters), with features and weights split into fp16 hi + lo parts
+ * (three MMAs per step, FP32 accumulation in tensor memory); a reduction then
+ * sums score(u, v) = sum_a G[a][(u + a) cx + v].  Scores agree with engine 0
+ * to about 1e-6 (not bit for bit).  With engine 1 the persistent fused
+ * launch covers pyramid to features and the same GEMM follows it, so both
+ * batched modes stay bit-identical to hog_detect.  Engine 1 holds 128 bytes
+ * per feature cell plus 40 F bytes per cell per batch slot; switching drops
+ * cached plans.  HOG_EINVAL for other values. */
+int hog_set_corr_engine(hog_ctx *ctx, int32_t engine);
+int hog_get_corr_engine(const hog_ctx *ctx, int32_t *engine);
+
 /* Suppression launch shape.  c = 1: one CTA per frame; c = 2, 4, 8 or 16:
  * each frame's suppression on a thread-block cluster of c CTAs (positions
  * split across the CTAs' shared memory, neighbour states read through
@@ -196,9 +212,10 @@ int hog_nms_cluster_size(hog_ctx *ctx, int32_t n_frames, int32_t w, int32_t h, i
 /* Autotuner (no counterpart in the paper, which picks block sizes by hand,
  * Section 5.1 block-size table).  On the given sample batch (device frames)
  * it times the correlation stage under each warp-tile shape policy (least
- * padding, or prefer 8x16, 4x32 or 16x8 tiles) with CUDA events, then the
- * batched call in fused and per-stage mode, and keeps the fastest of each in
- * the context.  If cache_path names a JSON file written for the same device,
+ * padding, or prefer 8x16, 4x32 or 16x8 tiles) of the CUDA-core engine and
+ * under the tensor-core engine (hog_set_corr_engine) with CUDA events, then
+ * the batched call in fused and per-stage mode, and keeps the fastest of
+ * each in the context.  If cache_path names a JSON file written for the same device,
  * SM count, filter count and frame sizes, its choice is loaded instead of
  * measured; otherwise the measurement is written there.  cache_path may be
  * NULL.  Synchronises the stream. */

@@ -94,7 +94,7 @@ int compute_geometry(const hog_params &p, int W, int H, Geometry &g) {
 namespace {
 struct PlanLayout {
     size_t items = 0;
-    size_t descs = 0, frames = 0, hist = 0, feat = 0, corr = 0, corrf = 0, total = 0;
+    size_t descs = 0, frames = 0, hist = 0, feat = 0, corr = 0, corrf = 0, tc = 0, tcr = 0, total = 0;
     std::vector<size_t> pyr;
     std::vector<int> npyr;
 };
@@ -102,7 +102,7 @@ struct PlanLayout {
 // Sizes and per-stage work of a laid-out plan (what a launch needs).
 struct PlanInfo {
     PlanLayout L;
-    int nhist = 0, nfeat = 0, ncorr = 0, nframes = 0, max_npos = 0;
+    int nhist = 0, nfeat = 0, ncorr = 0, nframes = 0, max_npos = 0, ntc = 0, ntcr = 0;
     int nitems = 0, nctr = 0;       // persistent fused launch: work items, counters
     int64_t px = 0, cells = 0, wins = 0;
 };
@@ -160,6 +160,14 @@ struct hog_ctx {
     int batched_mode = MODE_FUSED;  // chosen by the autotuner
     int corr_policy = 0;            // 0: least padding; 1 + s: prefer warp-tile shape s
     int nms_cluster = 0;            // 0: automatic; 1: one CTA per frame; 2..16: cluster size
+    // correlation engine: 0 FP32 CUDA cores (k_corr.cu), 1 tensor cores (k_corr_tc.cu)
+    int corr_engine = 0;
+    std::vector<float> w_host;      // the filters as given, [F][10][10][31]
+    float *d_wuser = nullptr;       // device copy of w_host
+    uint16_t *d_wtc = nullptr;      // tensor-core B planes (hi, lo)
+    uint16_t *d_fh = nullptr;       // per slot: fp16 feature planes hi, lo [cells][32]
+    float *d_gm = nullptr;          // per slot: row-shift matrices [10 F][cells] per level
+    size_t cells_slot = 0, fh_slot = 0, gm_slot = 0;
     int plan_cache_max = 8;         // cached batch plans (a server raises it)
     cudaStream_t cap_stream = nullptr;
     // training arena (hog_backward), grown on demand
@@ -229,6 +237,28 @@ int upload_filters(hog_ctx *ctx, const float *filters, int n) {
     CUDA_TRY(ctx, cudaMemcpy(ctx->d_w, wc.data(), wc.size() * sizeof(float), cudaMemcpyHostToDevice));
     ctx->nf = n;
     ctx->nfk = nfk;
+    ctx->w_host.assign(filters, filters + (size_t)n * WIN * WIN * NFEAT);
+    return HOG_OK;
+}
+
+// Arenas and B planes of the tensor-core correlation (allocated when the
+// engine is first selected; rebuilt after a filter change).
+int prepare_tc(hog_ctx *ctx) {
+    auto F = [](void *p) { if (p) cudaFree(p); };
+    F(ctx->d_wuser); F(ctx->d_wtc); F(ctx->d_gm);
+    ctx->d_wuser = nullptr; ctx->d_wtc = nullptr; ctx->d_gm = nullptr;
+    const size_t B = (size_t)ctx->p.max_batch;
+    ctx->cells_slot = ctx->feat_slot / 32;
+    ctx->fh_slot = align_up(ctx->cells_slot * 64, 128);                  // halves
+    ctx->gm_slot = align_up(ctx->cells_slot * WIN * (size_t)ctx->nfk, 64);   // floats
+    if (!ctx->d_fh) CUDA_TRY(ctx, cudaMalloc(&ctx->d_fh, B * ctx->fh_slot * sizeof(uint16_t)));
+    CUDA_TRY(ctx, cudaMalloc(&ctx->d_gm, B * ctx->gm_slot * sizeof(float)));
+    CUDA_TRY(ctx, cudaMalloc(&ctx->d_wuser, ctx->w_host.size() * sizeof(float)));
+    CUDA_TRY(ctx, cudaMalloc(&ctx->d_wtc, corr_tc_weights_halves(ctx->nfk) * sizeof(uint16_t)));
+    CUDA_TRY(ctx, cudaMemcpy(ctx->d_wuser, ctx->w_host.data(), ctx->w_host.size() * sizeof(float),
+                             cudaMemcpyHostToDevice));
+    CUDA_TRY(ctx, launch_corr_tc_weights(ctx->d_wuser, ctx->nfk, ctx->nf, ctx->d_wtc, nullptr));
+    CUDA_TRY(ctx, cudaDeviceSynchronize());
     return HOG_OK;
 }
 
@@ -249,6 +279,7 @@ void free_ctx(hog_ctx *ctx) {
     }
     F(ctx->d_fctr);
     F(ctx->d_train);
+    F(ctx->d_wuser); F(ctx->d_wtc); F(ctx->d_fh); F(ctx->d_gm);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (Geometry *g : ctx->geoms) {
         F(g->d_nbr);
@@ -326,6 +357,7 @@ struct PlanBuilder {
     std::vector<std::vector<Job>> pyr;   // per step (target level)
     std::vector<Job> hist, feat, corr;
     std::vector<Job> corrf;              // correlation jobs of the fused launch (8x16, 16x8 tiles)
+    std::vector<Job> tc, tcr;            // tensor-core correlation: 128-cell tiles, 256-window blocks
     std::vector<FusedItem> items;        // persistent fused launch (built on demand)
     int nctr = 0;
 };
@@ -398,6 +430,10 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
     float *hist = ctx->d_hist + (size_t)slot * ctx->hist_slot;
     float *feat = ctx->d_feat + (size_t)slot * ctx->feat_slot;
     uint64_t *keys = ctx->d_keys + (size_t)slot * ctx->pos_slot;
+    const bool tc = ctx->corr_engine == 1;
+    uint16_t *fh = tc ? ctx->d_fh + (size_t)slot * ctx->fh_slot : nullptr;
+    float *gm = tc ? ctx->d_gm + (size_t)slot * ctx->gm_slot : nullptr;
+    size_t cell_off = 0;
     const int first = (int)pb.descs.size();
     for (int l = 0; l < g.nlev; l++) {
         LevelDesc d;
@@ -452,9 +488,22 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
                 best_n = ((d.nu + corr_tu(pref) - 1) / corr_tu(pref)) *
                          ((d.nv + corr_tv(pref) - 1) / corr_tv(pref));
             }
-            for (int k = 0; k < best_n; k++) pb.corr.push_back({di, (best << 28) | k});
+            if (tc) {
+                // tensor cores: the level's fp16 planes and row-shift matrix
+                const size_t nc = (size_t)d.cx * d.cy;
+                pb.descs.back().feat_hi = fh + cell_off * 32;
+                pb.descs.back().feat_lo = fh + (ctx->cells_slot + cell_off) * 32;
+                pb.descs.back().gmat = gm + cell_off * WIN * ctx->nfk;
+                const int nt = (int)((nc + 127) / 128), nr = (d.nu * d.nv + 255) / 256;
+                for (int k = 0; k < nt; k++) pb.tc.push_back({di, k});
+                for (int k = 0; k < nr; k++) pb.tcr.push_back({di, k});
+            } else {
+                for (int k = 0; k < best_n; k++) pb.corr.push_back({di, (best << 28) | k});
+            }
             // the fused launch stages at most 17x25 cells per warp: 8x16 or
-            // 16x8 tiles, the preferred one if it is one of them
+            // 16x8 tiles, the preferred one if it is one of them (with the
+            // tensor-core engine the fused launch stops after the features
+            // and the GEMM above follows it)
             int fb = -1, fb_n = 0;
             for (int sh = 0; sh < CORR_NSHAPE; sh++) {
                 if (!corr_shape_fused(sh)) continue;
@@ -463,8 +512,10 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
                 if (fb < 0 || n < fb_n || sh == pref) { fb = sh; fb_n = n; }
                 if (sh == pref) break;
             }
-            for (int k = 0; k < fb_n; k++) pb.corrf.push_back({di, (fb << 28) | k});
+            if (!tc)
+                for (int k = 0; k < fb_n; k++) pb.corrf.push_back({di, (fb << 28) | k});
         }
+        cell_off += (size_t)d.cx * d.cy;
     }
     if (o.nms) {
         FrameDesc fd;
@@ -506,6 +557,8 @@ void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
     L.feat = take(pb.feat.size() * sizeof(Job));
     L.corr = take(pb.corr.size() * sizeof(Job));
     L.corrf = take(pb.corrf.size() * sizeof(Job));
+    L.tc = take(pb.tc.size() * sizeof(Job));
+    L.tcr = take(pb.tcr.size() * sizeof(Job));
     L.items = take(pb.items.size() * sizeof(FusedItem));
     L.total = off;
     info.nitems = (int)pb.items.size();
@@ -513,6 +566,8 @@ void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
     info.nhist = (int)pb.hist.size();
     info.nfeat = (int)pb.feat.size();
     info.ncorr = (int)pb.corr.size();
+    info.ntc = (int)pb.tc.size();
+    info.ntcr = (int)pb.tcr.size();
     info.nframes = (int)pb.frames.size();
     info.max_npos = 0;
     for (const FrameDesc &f : pb.frames) info.max_npos = std::max(info.max_npos, f.npos);
@@ -572,6 +627,8 @@ int upload_plan(hog_ctx *ctx, const PlanBuilder &pb, const PlanInfo &info, char 
     std::memcpy(h + L.feat, pb.feat.data(), pb.feat.size() * sizeof(Job));
     std::memcpy(h + L.corr, pb.corr.data(), pb.corr.size() * sizeof(Job));
     std::memcpy(h + L.corrf, pb.corrf.data(), pb.corrf.size() * sizeof(Job));
+    std::memcpy(h + L.tc, pb.tc.data(), pb.tc.size() * sizeof(Job));
+    std::memcpy(h + L.tcr, pb.tcr.data(), pb.tcr.size() * sizeof(Job));
     std::memcpy(h + L.items, pb.items.data(), pb.items.size() * sizeof(FusedItem));
     CUDA_TRY(ctx, cudaMemcpyAsync(d_dst ? d_dst : ctx->d_plan, h, L.total, cudaMemcpyHostToDevice,
                                   stream));
@@ -604,8 +661,14 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
                               ctx->p.eps, ctx->p.trunc, stream));
     CUDA_TRY(ctx, mark(5));
     CUDA_TRY(ctx, mark(6));
-    CUDA_TRY(ctx, launch_corr(descs, reinterpret_cast<const Job *>(d + L.corr), info.ncorr,
-                              ctx->d_w, ctx->nfk, ctx->nf, ctx->p.threshold, stream));
+    if (info.ntc > 0 || info.ntcr > 0)
+        CUDA_TRY(ctx, launch_corr_tc(descs, reinterpret_cast<const Job *>(d + L.tc), info.ntc,
+                                     reinterpret_cast<const Job *>(d + L.tcr), info.ntcr, ctx->d_wtc,
+                                     ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
+                                     ctx->num_sms * corr_tc_ctas_per_sm(ctx->nfk), stream));
+    else
+        CUDA_TRY(ctx, launch_corr(descs, reinterpret_cast<const Job *>(d + L.corr), info.ncorr,
+                                  ctx->d_w, ctx->nfk, ctx->nf, ctx->p.threshold, stream));
     CUDA_TRY(ctx, mark(7));
     CUDA_TRY(ctx, mark(8));
     if (info.nframes > 0)
@@ -619,7 +682,8 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
         st[0].launches += npyr; st[0].units += info.px;
         st[1].launches += info.nhist > 0; st[1].units += info.nhist > 0 ? info.cells : 0;
         st[2].launches += info.nfeat > 0; st[2].units += info.nfeat > 0 ? info.cells : 0;
-        st[3].launches += info.ncorr > 0; st[3].units += info.ncorr > 0 ? info.wins : 0;
+        st[3].launches += (info.ncorr > 0) + (info.ntc > 0) + (info.ntcr > 0);
+        st[3].units += (info.ncorr > 0 || info.ntcr > 0) ? info.wins : 0;
         st[4].launches += info.nframes > 0; st[4].units += info.nframes;
     }
     return HOG_OK;
@@ -730,6 +794,11 @@ int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStr
     };
     CUDA_TRY(ctx, mark(10));
     CUDA_TRY(ctx, launch_fused(a, ctx->nfk, ctx->fused_grid, stream));
+    if (info.ntc > 0 || info.ntcr > 0)   // tensor-core correlation after the fused stages
+        CUDA_TRY(ctx, launch_corr_tc(a.descs, reinterpret_cast<const Job *>(d + L.tc), info.ntc,
+                                     reinterpret_cast<const Job *>(d + L.tcr), info.ntcr, ctx->d_wtc,
+                                     ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
+                                     ctx->num_sms * corr_tc_ctas_per_sm(ctx->nfk), stream));
     CUDA_TRY(ctx, mark(11));
     CUDA_TRY(ctx, mark(8));
     if (info.nframes > 0)
@@ -739,7 +808,8 @@ int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStr
     if (ctx->prof) {
         ctx->prof_pending = true;
         ctx->prof_mask = (1u << 4) | (1u << 5);
-        ctx->stats[5].launches += info.nitems > 0; ctx->stats[5].units += info.wins;
+        ctx->stats[5].launches += (info.nitems > 0) + (info.ntc > 0) + (info.ntcr > 0);
+        ctx->stats[5].units += info.wins;
         ctx->stats[4].launches += info.nframes > 0; ctx->stats[4].units += info.nframes;
     }
     return HOG_OK;
@@ -1000,6 +1070,14 @@ int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters
             return HOG_ENOMEM;
         }
     }
+    // tensor-core correlation by default; the CUDA-core engine if its
+    // buffers cannot be had
+    if (prepare_tc(ctx) == HOG_OK) {
+        ctx->corr_engine = 1;
+    } else {
+        cudaGetLastError();
+        ctx->err.clear();
+    }
     *out = ctx;
     return HOG_OK;
 }
@@ -1007,7 +1085,13 @@ int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters
 int hog_set_filters(hog_ctx *ctx, const float *filters_host, int32_t n_filters) {
     if (!ctx) return HOG_EINVAL;
     cudaDeviceSynchronize();
-    return upload_filters(ctx, filters_host, n_filters);
+    const int nfk0 = ctx->nfk;
+    int rc = upload_filters(ctx, filters_host, n_filters);
+    if (rc == HOG_OK && ctx->corr_engine == 1) {
+        if (ctx->nfk != nfk0) clear_plans(ctx);   // row-shift matrices change size
+        rc = prepare_tc(ctx);
+    }
+    return rc;
 }
 
 void hog_destroy(hog_ctx *ctx) {
@@ -1153,6 +1237,24 @@ int hog_detect_batched(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, 
                          (cudaStream_t)stream_, ctx->batched_mode, true);
 }
 
+int hog_set_corr_engine(hog_ctx *ctx, int32_t engine) {
+    if (!ctx || (engine != 0 && engine != 1)) return HOG_EINVAL;
+    if (engine == ctx->corr_engine) return HOG_OK;
+    clear_plans(ctx);   // plans hold the engine's jobs and buffers
+    if (engine == 1) {
+        const int rc = prepare_tc(ctx);
+        if (rc) return rc;
+    }
+    ctx->corr_engine = engine;
+    return HOG_OK;
+}
+
+int hog_get_corr_engine(const hog_ctx *ctx, int32_t *engine) {
+    if (!ctx || !engine) return HOG_EINVAL;
+    *engine = ctx->corr_engine;
+    return HOG_OK;
+}
+
 int hog_set_nms_cluster(hog_ctx *ctx, int32_t c) {
     if (!ctx || !(c == 0 || c == 1 || c == 2 || c == 4 || c == 8 || c == 16)) return HOG_EINVAL;
     if (c != ctx->nms_cluster) {
@@ -1263,13 +1365,18 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
             const std::string txt(buf);
             const std::string kq = "\"key\": \"" + key + "\"";
             if (txt.find(kq) != std::string::npos) {
-                int mode = -1, pol = -1;
+                int mode = -1, pol = -1, eng = 0;
                 const size_t a = txt.find("\"batched_mode\": ");
                 const size_t b = txt.find("\"corr_policy\": ");
+                const size_t c = txt.find("\"corr_engine\": ");
                 if (a != std::string::npos) mode = std::atoi(txt.c_str() + a + 16);
                 if (b != std::string::npos) pol = std::atoi(txt.c_str() + b + 15);
-                if ((mode == MODE_STAGED || mode == MODE_FUSED) && pol >= 0 && pol <= CORR_NSHAPE) {
+                if (c != std::string::npos) eng = std::atoi(txt.c_str() + c + 15);
+                if ((mode == MODE_STAGED || mode == MODE_FUSED) && pol >= 0 && pol <= CORR_NSHAPE &&
+                    (eng == 0 || eng == 1)) {
                     if (pol != ctx->corr_policy) { ctx->corr_policy = pol; clear_plans(ctx); }
+                    const int rc = hog_set_corr_engine(ctx, eng);
+                    if (rc) return rc;
                     ctx->batched_mode = mode;
                     return HOG_OK;
                 }
@@ -1299,9 +1406,11 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
         *ms /= reps;
         return HOG_OK;
     };
-    // 1. correlation tile-shape policy: time the correlation stage (events)
+    // 1. correlation tile-shape policy of the CUDA-core engine, then the
+    //    tensor-core engine: time the correlation stage (events)
     const bool was_prof = ctx->prof;
-    int rc = hog_set_profiling(ctx, 1);
+    int rc = hog_set_corr_engine(ctx, 0);
+    if (!rc) rc = hog_set_profiling(ctx, 1);
     double best_corr = 1e30;
     int best_pol = 0;
     double pol_ms[CORR_NSHAPE + 1];
@@ -1321,10 +1430,25 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
         pol_ms[pol] = st[3].ms / 5.0;   // 2 warm + 3 timed calls
         if (st[3].ms < best_corr) { best_corr = st[3].ms; best_pol = pol; }
     }
-    hog_set_profiling(ctx, was_prof ? 1 : 0);
-    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
     ctx->corr_policy = best_pol;
     clear_plans(ctx);
+    double tc_ms = -1.0;
+    if (rc == HOG_OK && hog_set_corr_engine(ctx, 1) == HOG_OK) {
+        float ms = 0.0f;
+        hog_stage_stat st[HOG_NSTAGES];
+        rc = timed(MODE_STAGED, false, 1, &ms);
+        hog_stage_stats(ctx, st, HOG_NSTAGES, 1);
+        if (!rc) rc = timed(MODE_STAGED, false, 3, &ms);
+        hog_stage_stats(ctx, st, HOG_NSTAGES, 1);
+        if (!rc) {
+            tc_ms = st[3].ms / 5.0;
+            if (st[3].ms >= best_corr) rc = hog_set_corr_engine(ctx, 0);
+        }
+    } else {
+        ctx->err.clear();   // no tensor-core buffers: the CUDA-core engine stays
+    }
+    hog_set_profiling(ctx, was_prof ? 1 : 0);
+    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
     // 2. batched execution mode (both as graphs)
     float ms_staged = 0.0f, ms_fused = 0.0f;
     rc = timed(MODE_STAGED, true, 5, &ms_staged);
@@ -1338,6 +1462,8 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
         if (f) {
             std::fprintf(f, "{\n  \"key\": \"%s\",\n  \"batched_mode\": %d,\n  \"corr_policy\": %d,\n",
                          key.c_str(), ctx->batched_mode, ctx->corr_policy);
+            std::fprintf(f, "  \"corr_engine\": %d,\n  \"corr_ms_tensor\": %.4f,\n", ctx->corr_engine,
+                         tc_ms);
             std::fprintf(f, "  \"ms_per_batch\": {\"staged\": %.4f, \"fused\": %.4f},\n",
                          ms_staged, ms_fused);
             std::fprintf(f, "  \"corr_ms_by_policy\": [");

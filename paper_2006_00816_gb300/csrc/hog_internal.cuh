@@ -103,6 +103,10 @@ struct LevelDesc {
     float *feat_user;       // optional [cy][cx][31] copy (hog_features)
     float *scores_user;     // optional [F][nu][nv] (hog_scores)
     uint64_t *keys;         // [nu][nv] suppression keys of this level
+    // tensor-core correlation (when enabled): features as fp16 hi + lo parts,
+    // [cy*cx][32] each, and the row-shift matrix G [10*F][cy*cx] (fp32)
+    uint16_t *feat_hi, *feat_lo;
+    float *gmat;
 };
 
 // Per-frame suppression work.
@@ -191,6 +195,20 @@ cudaError_t launch_window_adjoint(const float *pyr, size_t pyr_stride, const flo
 cudaError_t launch_fpyr_adjoint(float *dP, size_t pyr_stride, const TrainLevels &lv, int q,
                                 const int4 *best, const float *margin, int n, cudaStream_t s);
 cudaError_t launch_filter_chunks(const float *wuser, float *wch, cudaStream_t s);
+
+// Tensor-core correlation (k_corr_tc.cu): GEMM N = 10 filter rows x F
+// filters padded to a multiple of 16.
+__host__ __device__ constexpr int tc_n(int nf) { return (10 * nf + 15) / 16 * 16; }
+// fp16 halves of the two (hi, lo) B planes for an nf_kernel-filter build
+size_t corr_tc_weights_halves(int nf_kernel);
+cudaError_t launch_corr_tc_weights(const float *w_user, int nf_kernel, int nf_real, uint16_t *wb,
+                                   cudaStream_t stream);
+// GEMM over `njobs` 128-cell tiles (Job = level descriptor, tile), then the
+// row-shift reduction, threshold and keys over `nrjobs` 256-window blocks
+cudaError_t launch_corr_tc(const LevelDesc *descs, const Job *jobs, int njobs, const Job *rjobs,
+                           int nrjobs, const uint16_t *wb, int nf_kernel, int nf_real,
+                           float threshold, int *flags, int grid, cudaStream_t stream);
+int corr_tc_ctas_per_sm(int nf_kernel);
 
 // ---- asynchronous detection for the serving runtime (hog_api.cu) ---------
 int detect_enqueue(hog_ctx *ctx, const hog_frame *frames, int nb, cudaStream_t stream, int mode,

@@ -9,6 +9,8 @@
 // stand-alone kernels read data of earlier launches and may use __ldg.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "hog_internal.cuh"
 
 namespace hogk {
@@ -314,6 +316,26 @@ __device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float ep
             float *u = d.feat_user + cell * NFEAT;
 #pragma unroll
             for (int o = 0; o < NFEAT; o++) u[o] = f[o];
+        }
+        if (d.feat_hi) {
+            // fp16 split for the tensor-core correlation: hi = f rounded to
+            // fp16, lo = (f - hi) rounded to fp16; |f - hi - lo| <= 2^-22 |f|
+            uint32_t hw[16], lw[16];
+#pragma unroll
+            for (int o = 0; o < 16; o++) {
+                const __half h0 = __float2half_rn(f[2 * o]), h1 = __float2half_rn(f[2 * o + 1]);
+                const __half l0 = __float2half_rn(f[2 * o] - __half2float(h0));
+                const __half l1 = __float2half_rn(f[2 * o + 1] - __half2float(h1));
+                hw[o] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+                lw[o] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+            }
+            uint4 *ph = reinterpret_cast<uint4 *>(d.feat_hi + cell * 32);
+            uint4 *pl = reinterpret_cast<uint4 *>(d.feat_lo + cell * 32);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                ph[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                pl[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+            }
         }
     }
     __syncthreads();   // shared memory may be reused by the caller's next tile

@@ -95,6 +95,8 @@ _SIGS = {
     "hog_detect_batched": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
     "hog_set_batched_mode": (C.c_int, [_vp, _i32]),
     "hog_set_nms_cluster": (C.c_int, [_vp, _i32]),
+    "hog_set_corr_engine": (C.c_int, [_vp, _i32]),
+    "hog_get_corr_engine": (C.c_int, [_vp, _P(_i32)]),
     "hog_nms_cluster_size": (C.c_int, [_vp, _i32, _i32, _i32, _P(_i32)]),
     "hog_autotune": (C.c_int, [_vp, _P(Frame), _i32, C.c_char_p, _vp]),
     "hog_get_tuning": (C.c_int, [_vp, _P(_i32), _P(_i32)]),
@@ -252,6 +254,15 @@ class Detector:
     def set_batched_mode(self, mode):
         """1: persistent fused launch, 0: one launch per stage."""
         self._check(_lib.hog_set_batched_mode(self._h, int(mode)))
+
+    def set_corr_engine(self, engine):
+        """Correlation: 0 FP32 CUDA cores, 1 tcgen05 tensor cores (fp16 hi/lo split)."""
+        self._check(_lib.hog_set_corr_engine(self._h, int(engine)))
+
+    def corr_engine(self):
+        e = _i32(0)
+        self._check(_lib.hog_get_corr_engine(self._h, C.byref(e)))
+        return e.value
 
     def set_nms_cluster(self, c):
         """Suppression launch: 1 one CTA per frame, 2/4/8/16 cluster size,

@@ -65,13 +65,14 @@ def test_autotune_keeps_results_and_caches(H, synth, tmp_path):
     W = synth.filters(5)
     det = H.Detector(W, max_w=1280, max_h=1024, max_batch=8)
     frames = _mixed(synth, 8)
-    ref, rc = det.detect(frames)
     path = str(tmp_path / "tune.json")
     mode, pol = det.autotune(frames, cache_path=path)
     assert mode in (0, 1) and 0 <= pol <= 3
     rec = json.load(open(path))
     assert rec["batched_mode"] == mode and rec["corr_policy"] == pol
     assert len(rec["corr_ms_by_policy"]) == 4
+    # the per-frame call under the chosen correlation engine
+    ref, rc = det.detect(frames)
     got, gc = det.detect(frames, batched=True)
     assert gc.tolist() == rc.tolist()
     assert np.array_equal(got, ref)       # tile shapes change speed, not arithmetic
