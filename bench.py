@@ -39,6 +39,13 @@ WORKLOAD = "eyeblink stream 640x480 uint8, 1000 frames, 5 filters 10x10x31 FP32,
 CORR_FLOP_PER_UNIT = 2 * 10 * 10 * 31          # one window x one filter
 # FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.070 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the tensor-core
+# correlation stage for one 250-frame 640x480 batch, from one ncu capture of
+# corr_tc_kernel<5> and corr_tc_reduce_kernel<5> (--set full, 250-frame
+# batch); valid while the kernel source is the one captured (first 16 hex
+# digits of its SHA-256)
+CORR_TC_TRAFFIC_250 = (479.834624e6 + 692.63872e6) + (581.026816e6 + 18.4384e6)
+CORR_TC_SOURCE_SHA = "f1a8fb2a8f9b8246"
 PAPER_CONTEXT = {"ms_per_frame": 0.333, "frames_per_s": 3003,
                  "hardware": "NVIDIA Titan X (Pascal), 16 frames/launch, incl. transfers"}
 
@@ -58,6 +65,9 @@ def parse():
     ap.add_argument("--serve-warmup", type=float, default=1.0)
     ap.add_argument("--mixed-frames", type=int, default=256)
     ap.add_argument("--backward-reps", type=int, default=20)
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner record to load (or write): a profiled run then uses the "
+                         "choice measured without the profiler")
     return ap.parse_args()
 
 
@@ -286,8 +296,15 @@ def corr_roofline(hog, stats, mode, engine, nfr, steps, peaks):
         n = (10 * NF + 15) // 16 * 16
         executed = tiles * 3 * 20 * 2 * 128 * n * 16 / (ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops", 1901.0)
+        import hashlib
+        src = os.path.join(ROOT, "paper_2006_00816_gb300", "csrc", "k_corr_tc.cu")
+        same = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == CORR_TC_SOURCE_SHA
+        frames_per_launch = nfr * steps / batches
+        traffic = CORR_TC_TRAFFIC_250 * frames_per_launch / 250 if same else None
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "traffic_note": "ncu dram read+write of GEMM + reduce for a 250-frame batch, "
+                                "scaled to this launch's frames",
                 "kernel": "corr_tc_kernel<5> + corr_tc_reduce_kernel<5> (tcgen05, fp16 hi/lo x3)",
                 "flop_per_launch": flops / batches, "avg_launch_ms": ms / batches,
                 "executed_tensor_tflops": executed,
@@ -457,12 +474,13 @@ def main():
         torch.cuda.synchronize(dev)
 
     # ---- autotune on the first batch (tile-shape policy, fused vs per-stage)
-    tune_path = os.path.join("/tmp", "hog_gb300_tune_%d.json" % os.getpid())
+    tune_path = args.tune_cache or os.path.join("/tmp", "hog_gb300_tune_%d.json" % os.getpid())
     mode, corr_policy = det.autotune(frames[:args.batch], cache_path=tune_path)
     engine = det.corr_engine()
     try:
         tune = json.load(open(tune_path))
-        os.remove(tune_path)
+        if not args.tune_cache:
+            os.remove(tune_path)
     except (OSError, ValueError):
         tune = {}
 
