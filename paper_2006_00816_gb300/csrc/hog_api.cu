@@ -455,7 +455,8 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
             d.sw = prev.w; d.sh = prev.h; d.spitch = prev.pitch;
         }
         d.hist = hist + g.hist_off[l];
-        d.feat = feat + g.feat_off[l];
+        // the FP32 feature layout feeds the CUDA-core correlation only
+        d.feat = tc ? nullptr : feat + g.feat_off[l];
         d.feat_user = o.feat_user ? o.feat_user + g.ufeat_off[l] : nullptr;
         d.scores_user = o.scores_user ? o.scores_user + o.score_off[l] : nullptr;
         d.keys = keys + g.pos_off[l];

@@ -306,11 +306,13 @@ __device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float ep
 
         const size_t plane = (size_t)d.cy * d.cx * CHUNK;
         const size_t cell = (size_t)i * d.cx + j;
+        if (d.feat) {   // FP32 chunked layout (CUDA-core correlation)
 #pragma unroll
-        for (int ch = 0; ch < NCHUNK; ch++) {
-            float4 *dst = reinterpret_cast<float4 *>(d.feat + ch * plane + cell * CHUNK);
-            dst[0] = make_float4(f[8 * ch + 0], f[8 * ch + 1], f[8 * ch + 2], f[8 * ch + 3]);
-            dst[1] = make_float4(f[8 * ch + 4], f[8 * ch + 5], f[8 * ch + 6], f[8 * ch + 7]);
+            for (int ch = 0; ch < NCHUNK; ch++) {
+                float4 *dst = reinterpret_cast<float4 *>(d.feat + ch * plane + cell * CHUNK);
+                dst[0] = make_float4(f[8 * ch + 0], f[8 * ch + 1], f[8 * ch + 2], f[8 * ch + 3]);
+                dst[1] = make_float4(f[8 * ch + 4], f[8 * ch + 5], f[8 * ch + 6], f[8 * ch + 7]);
+            }
         }
         if (d.feat_user) {
             float *u = d.feat_user + cell * NFEAT;
