@@ -40,12 +40,11 @@ CORR_FLOP_PER_UNIT = 2 * 10 * 10 * 31          # one window x one filter
 # FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.070 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the tensor-core
-# correlation stage for one 250-frame 640x480 batch, from one ncu capture of
-# corr_tc_kernel<5> and corr_tc_reduce_kernel<5> (--set full, 250-frame
-# batch); valid while the kernel source is the one captured (first 16 hex
-# digits of its SHA-256)
-CORR_TC_TRAFFIC_250 = (479.834624e6 + 692.63872e6) + (581.026816e6 + 18.4384e6)
-CORR_TC_SOURCE_SHA = "f1a8fb2a8f9b8246"
+# correlation stage for one 250-frame 640x480 batch, per engine, from one ncu
+# capture (--set full, 250-frame batch); valid while k_corr_tc.cu is the
+# source captured (first 16 hex digits of its SHA-256); None: not captured
+CORR_TC_TRAFFIC_250 = {1: None, 2: None}
+CORR_TC_SOURCE_SHA = None
 PAPER_CONTEXT = {"ms_per_frame": 0.333, "frames_per_s": 3003,
                  "hardware": "NVIDIA Titan X (Pascal), 16 frames/launch, incl. transfers"}
 
@@ -289,8 +288,9 @@ def corr_roofline(hog, stats, mode, engine, nfr, steps, peaks):
     ms, launches, units = stats[key]
     flops = units * CORR_FLOP_PER_UNIT
     achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else None
-    batches = max(launches // (2 if engine == 1 and mode == 0 else 1), 1)
-    if engine == 1 and mode == 0:
+    per_batch = 2 if (engine == 2 and mode == 0) else 1
+    batches = max(launches // per_batch, 1)
+    if engine in (1, 2) and mode == 0:
         lv = level_cells(hog, W0, H0)
         tiles = sum((c + 127) // 128 for c, _, _ in lv) * nfr * steps
         n = (10 * NF + 15) // 16 * 16
@@ -300,12 +300,17 @@ def corr_roofline(hog, stats, mode, engine, nfr, steps, peaks):
         src = os.path.join(ROOT, "paper_2006_00816_gb300", "csrc", "k_corr_tc.cu")
         same = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == CORR_TC_SOURCE_SHA
         frames_per_launch = nfr * steps / batches
-        traffic = CORR_TC_TRAFFIC_250 * frames_per_launch / 250 if same else None
+        t250 = CORR_TC_TRAFFIC_250.get(engine)
+        traffic = t250 * frames_per_launch / 250 if (same and t250) else None
+        kernel = ("corr_tcf_kernel<5> (tcgen05 GEMM + on-chip row-shift reduction, fp16 hi/lo x3)"
+                  if engine == 1 else
+                  "corr_tc_kernel<5> + corr_tc_reduce_kernel<5> (tcgen05, fp16 hi/lo x3, G in HBM)")
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "traffic_note": "ncu dram read+write of GEMM + reduce for a 250-frame batch, "
-                                "scaled to this launch's frames",
-                "kernel": "corr_tc_kernel<5> + corr_tc_reduce_kernel<5> (tcgen05, fp16 hi/lo x3)",
+                "traffic_note": "ncu dram read+write of the correlation stage for a 250-frame "
+                                "batch, scaled to this launch's frames (null: no capture of "
+                                "this source)",
+                "kernel": kernel,
                 "flop_per_launch": flops / batches, "avg_launch_ms": ms / batches,
                 "executed_tensor_tflops": executed,
                 "executed_over_algorithmic": executed / achieved if achieved else None,
@@ -332,9 +337,10 @@ def stage_table(hog, stats, nfr, steps, engine, peaks):
     px = [p for _, _, p in lv]
     b = {"pyramid": sum(px[l - 1] + px[l] for l in range(1, len(px))),
          "hist": sum(px) + cells * 18 * 4,
-         "feat": cells * 18 * 4 + cells * 128 + (cells * 128 if engine == 1 else 0),
-         "corr": (cells * 128 + cells * 10 * NF * 4 * 2 + wins * 8) if engine == 1
-                 else cells * 128 + wins * 8,
+         # features: histograms in; FP32 layout (CUDA cores) or fp16 hi+lo planes out
+         "feat": cells * 18 * 4 + cells * 128,
+         # correlation: features in, keys out (+ G written and read: engine 2)
+         "corr": cells * 128 + wins * 8 + (cells * 10 * NF * 4 * 2 if engine == 2 else 0),
          "nms": wins * 8 + 447 * 56}
     hbm = peaks.get("hbm_gbs", 6800.0)
     out = {}
@@ -617,7 +623,8 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs 307 MB per step exceed the 129 MB L2; no flush"},
             "batched": {"frames_per_s": fps, "mode": "fused" if mode == 1 else "per-stage",
-                        "corr_engine": "tensor cores (tcgen05)" if engine == 1 else "FP32 CUDA cores",
+                        "corr_engine": {0: "FP32 CUDA cores", 1: "tensor cores (tcgen05), fused reduction",
+                                        2: "tensor cores (tcgen05), two-pass"}[engine],
                         "graphs": True, "corr_tile_policy": corr_policy,
                         "other_mode_frames_per_s": other_fps,
                         "step_p50_ms": statistics.median(chunk_ms),

@@ -181,18 +181,22 @@ int hog_detect_batched(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, 
 int hog_set_batched_mode(hog_ctx *ctx, int32_t mode);
 
 /* Correlation engine.  0: FP32 CUDA cores, one warp per 128-window tile.
- * 1 (default when its buffers can be allocated at hog_create): tcgen05
+ * 1 (default when its buffers can be allocated at hog_create) and 2: tcgen05
  * tensor cores -- for each filter row a,
  * G[a][p] = sum over 10 cell shifts and 32 channels of feat[p + b] W[a][b]
  * is a GEMM over the level's cells (M = 128 cells per MMA, K = 320, N = 10
  * rows x F filters), with features and weights split into fp16 hi + lo parts
- * (three MMAs per step, FP32 accumulation in tensor memory); a reduction then
- * sums score(u, v) = sum_a G[a][(u + a) cx + v].  Scores agree with engine 0
- * to about 1e-6 (not bit for bit).  With engine 1 the persistent fused
- * launch covers pyramid to features and the same GEMM follows it, so both
- * batched modes stay bit-identical to hog_detect.  Engine 1 holds 128 bytes
- * per feature cell plus 40 F bytes per cell per batch slot; switching drops
- * cached plans.  HOG_EINVAL for other values. */
+ * (three MMAs per step, FP32 accumulation in tensor memory), and
+ * score(u, v) = sum_a G[a][(u + a) cx + v].  Engine 1 sums G on chip, in a
+ * ring of partial scores in shared memory, while the next tile's MMAs run
+ * (one persistent CTA per SM over bands of window rows); engine 2 writes G
+ * to device memory and sums it in a second kernel.  Engines 1 and 2 give
+ * bit-identical scores; they agree with engine 0 to about 1e-6 (not bit for
+ * bit).  With a tensor engine the persistent fused launch covers pyramid to
+ * features and the same correlation kernel follows it, so both batched
+ * modes stay bit-identical to hog_detect.  Engines 1 and 2 hold 128 bytes
+ * per feature cell per batch slot, engine 2 another 40 F bytes; switching
+ * drops cached plans.  HOG_EINVAL for other values. */
 int hog_set_corr_engine(hog_ctx *ctx, int32_t engine);
 int hog_get_corr_engine(const hog_ctx *ctx, int32_t *engine);
 

@@ -95,6 +95,7 @@ namespace {
 struct PlanLayout {
     size_t items = 0;
     size_t descs = 0, frames = 0, hist = 0, feat = 0, corr = 0, corrf = 0, tc = 0, tcr = 0, total = 0;
+    size_t bands = 0, cta_first = 0;
     std::vector<size_t> pyr;
     std::vector<int> npyr;
 };
@@ -103,6 +104,7 @@ struct PlanLayout {
 struct PlanInfo {
     PlanLayout L;
     int nhist = 0, nfeat = 0, ncorr = 0, nframes = 0, max_npos = 0, ntc = 0, ntcr = 0;
+    int tcf_grid = 0;               // fused tensor-core correlation: CTAs (0: not used)
     int nitems = 0, nctr = 0;       // persistent fused launch: work items, counters
     int64_t px = 0, cells = 0, wins = 0;
 };
@@ -160,7 +162,8 @@ struct hog_ctx {
     int batched_mode = MODE_FUSED;  // chosen by the autotuner
     int corr_policy = 0;            // 0: least padding; 1 + s: prefer warp-tile shape s
     int nms_cluster = 0;            // 0: automatic; 1: one CTA per frame; 2..16: cluster size
-    // correlation engine: 0 FP32 CUDA cores (k_corr.cu), 1 tensor cores (k_corr_tc.cu)
+    // correlation engine: 0 FP32 CUDA cores (k_corr.cu); tensor cores
+    // (k_corr_tc.cu): 1 GEMM and reduction fused, 2 two passes through G
     int corr_engine = 0;
     std::vector<float> w_host;      // the filters as given, [F][10][10][31]
     float *d_wuser = nullptr;       // device copy of w_host
@@ -243,7 +246,7 @@ int upload_filters(hog_ctx *ctx, const float *filters, int n) {
 
 // Arenas and B planes of the tensor-core correlation (allocated when the
 // engine is first selected; rebuilt after a filter change).
-int prepare_tc(hog_ctx *ctx) {
+int prepare_tc(hog_ctx *ctx, bool need_g) {
     auto F = [](void *p) { if (p) cudaFree(p); };
     F(ctx->d_wuser); F(ctx->d_wtc); F(ctx->d_gm);
     ctx->d_wuser = nullptr; ctx->d_wtc = nullptr; ctx->d_gm = nullptr;
@@ -252,7 +255,7 @@ int prepare_tc(hog_ctx *ctx) {
     ctx->fh_slot = align_up(ctx->cells_slot * 64, 128);                  // halves
     ctx->gm_slot = align_up(ctx->cells_slot * WIN * (size_t)ctx->nfk, 64);   // floats
     if (!ctx->d_fh) CUDA_TRY(ctx, cudaMalloc(&ctx->d_fh, B * ctx->fh_slot * sizeof(uint16_t)));
-    CUDA_TRY(ctx, cudaMalloc(&ctx->d_gm, B * ctx->gm_slot * sizeof(float)));
+    if (need_g) CUDA_TRY(ctx, cudaMalloc(&ctx->d_gm, B * ctx->gm_slot * sizeof(float)));
     CUDA_TRY(ctx, cudaMalloc(&ctx->d_wuser, ctx->w_host.size() * sizeof(float)));
     CUDA_TRY(ctx, cudaMalloc(&ctx->d_wtc, corr_tc_weights_halves(ctx->nfk) * sizeof(uint16_t)));
     CUDA_TRY(ctx, cudaMemcpy(ctx->d_wuser, ctx->w_host.data(), ctx->w_host.size() * sizeof(float),
@@ -358,6 +361,9 @@ struct PlanBuilder {
     std::vector<Job> hist, feat, corr;
     std::vector<Job> corrf;              // correlation jobs of the fused launch (8x16, 16x8 tiles)
     std::vector<Job> tc, tcr;            // tensor-core correlation: 128-cell tiles, 256-window blocks
+    std::vector<int> tcf_levels;         // fused tensor-core correlation: level descriptors to band
+    std::vector<TcBand> bands;           // ... their bands, in per-CTA order
+    std::vector<int32_t> cta_first;      // ... CTA k runs bands [cta_first[k], cta_first[k+1])
     std::vector<FusedItem> items;        // persistent fused launch (built on demand)
     int nctr = 0;
 };
@@ -430,9 +436,9 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
     float *hist = ctx->d_hist + (size_t)slot * ctx->hist_slot;
     float *feat = ctx->d_feat + (size_t)slot * ctx->feat_slot;
     uint64_t *keys = ctx->d_keys + (size_t)slot * ctx->pos_slot;
-    const bool tc = ctx->corr_engine == 1;
+    const bool tc = ctx->corr_engine >= 1;
     uint16_t *fh = tc ? ctx->d_fh + (size_t)slot * ctx->fh_slot : nullptr;
-    float *gm = tc ? ctx->d_gm + (size_t)slot * ctx->gm_slot : nullptr;
+    float *gm = ctx->corr_engine == 2 ? ctx->d_gm + (size_t)slot * ctx->gm_slot : nullptr;
     size_t cell_off = 0;
     const int first = (int)pb.descs.size();
     for (int l = 0; l < g.nlev; l++) {
@@ -494,10 +500,14 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
                 const size_t nc = (size_t)d.cx * d.cy;
                 pb.descs.back().feat_hi = fh + cell_off * 32;
                 pb.descs.back().feat_lo = fh + (ctx->cells_slot + cell_off) * 32;
-                pb.descs.back().gmat = gm + cell_off * WIN * ctx->nfk;
-                const int nt = (int)((nc + 127) / 128), nr = (d.nu * d.nv + 255) / 256;
-                for (int k = 0; k < nt; k++) pb.tc.push_back({di, k});
-                for (int k = 0; k < nr; k++) pb.tcr.push_back({di, k});
+                if (ctx->corr_engine == 2) {
+                    pb.descs.back().gmat = gm + cell_off * WIN * ctx->nfk;
+                    const int nt = (int)((nc + 127) / 128), nr = (d.nu * d.nv + 255) / 256;
+                    for (int k = 0; k < nt; k++) pb.tc.push_back({di, k});
+                    for (int k = 0; k < nr; k++) pb.tcr.push_back({di, k});
+                } else {
+                    pb.tcf_levels.push_back(di);
+                }
             } else {
                 for (int k = 0; k < best_n; k++) pb.corr.push_back({di, (best << 28) | k});
             }
@@ -542,6 +552,89 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
 
 
 
+// Bands of the fused tensor-core correlation and their assignment to CTAs
+// (one CTA per SM).  A band's cost is its number of 128-cell tiles; each
+// extra band of a level re-reads 9 cell rows.  The band height is chosen
+// to minimise the estimated makespan max(largest band, total / CTAs) (a
+// large batch keeps whole levels, a single frame splits its big levels),
+// then bands go to CTAs longest first, each to the least loaded CTA.
+void build_tc_bands(PlanBuilder &pb, int num_sms) {
+    pb.bands.clear();
+    pb.cta_first.clear();
+    if (pb.tcf_levels.empty()) return;
+    struct Strip { int desc, nu, c0, nvs, P; };
+    std::vector<Strip> strips;
+    for (int di : pb.tcf_levels) {
+        const LevelDesc &d = pb.descs[di];
+        const int S = (d.nv + (TCF_PMAX - WIN)) / (TCF_PMAX - WIN + 1);   // ceil(nv / (PMAX - 9))
+        int c0 = 0;
+        for (int k = 0; k < S; k++) {
+            const int nvs = d.nv / S + (k < d.nv % S ? 1 : 0);
+            strips.push_back({di, d.nu, c0, nvs, S == 1 ? d.cx : nvs + WIN - 1});
+            c0 += nvs;
+        }
+    }
+    // window rows per band for a tile budget M (at least one row)
+    auto rows_for = [](const Strip &st, long M) {
+        const long h = M * 128 / st.P - (WIN - 1);
+        return (int)std::max(1L, std::min((long)st.nu, h));
+    };
+    const long cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 1L << 30};
+    constexpr int NC = (int)(sizeof cand / sizeof cand[0]);
+    long span[NC], total[NC], best_span = -1;
+    for (int k = 0; k < NC; k++) {
+        long tot = 0, maxt = 0;
+        for (const Strip &st : strips) {
+            const int h0 = rows_for(st, cand[k]);
+            const int nb = (st.nu + h0 - 1) / h0;
+            const int h = (st.nu + nb - 1) / nb;
+            const long t = tcf_tiles(0, h, st.P);
+            tot += (long)nb * t;
+            maxt = std::max(maxt, t);
+        }
+        span[k] = std::max(maxt, (tot + num_sms - 1) / num_sms);
+        total[k] = tot;
+        if (best_span < 0 || span[k] < best_span) best_span = span[k];
+    }
+    // among budgets within ~15 % of the best makespan, the least total work
+    // (re-read rows cost HBM traffic and energy for little latency)
+    long best_M = cand[NC - 1], best_tot = -1;
+    for (int k = 0; k < NC; k++)
+        if (span[k] * 20 <= best_span * 23 + 20 && (best_tot < 0 || total[k] < best_tot)) {
+            best_tot = total[k];
+            best_M = cand[k];
+        }
+    std::vector<TcBand> all;
+    std::vector<long> cost;
+    for (const Strip &st : strips) {
+        const int h0 = rows_for(st, best_M);
+        const int nb = (st.nu + h0 - 1) / h0;
+        for (int k = 0; k < nb; k++) {
+            const int u0 = (int)((long)st.nu * k / nb), u1 = (int)((long)st.nu * (k + 1) / nb);
+            all.push_back({st.desc, u0, u1, st.c0, st.P, st.nvs});
+            cost.push_back(tcf_tiles(u0, u1, st.P));
+        }
+    }
+    std::vector<int> order(all.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    const int grid = (int)std::min<size_t>(all.size(), (size_t)num_sms);
+    std::vector<long> load(grid, 0);
+    std::vector<std::vector<int>> per(grid);
+    for (int i : order) {
+        int c = 0;
+        for (int k = 1; k < grid; k++)
+            if (load[k] < load[c]) c = k;
+        load[c] += cost[i];
+        per[c].push_back(i);
+    }
+    pb.cta_first.push_back(0);
+    for (int c = 0; c < grid; c++) {
+        for (int i : per[c]) pb.bands.push_back(all[i]);
+        pb.cta_first.push_back((int32_t)pb.bands.size());
+    }
+}
+
 void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
     PlanLayout &L = info.L;
     size_t off = 0;
@@ -560,6 +653,8 @@ void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
     L.corrf = take(pb.corrf.size() * sizeof(Job));
     L.tc = take(pb.tc.size() * sizeof(Job));
     L.tcr = take(pb.tcr.size() * sizeof(Job));
+    L.bands = take(pb.bands.size() * sizeof(TcBand));
+    L.cta_first = take(pb.cta_first.size() * sizeof(int32_t));
     L.items = take(pb.items.size() * sizeof(FusedItem));
     L.total = off;
     info.nitems = (int)pb.items.size();
@@ -569,6 +664,7 @@ void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
     info.ncorr = (int)pb.corr.size();
     info.ntc = (int)pb.tc.size();
     info.ntcr = (int)pb.tcr.size();
+    info.tcf_grid = pb.cta_first.empty() ? 0 : (int)pb.cta_first.size() - 1;
     info.nframes = (int)pb.frames.size();
     info.max_npos = 0;
     for (const FrameDesc &f : pb.frames) info.max_npos = std::max(info.max_npos, f.npos);
@@ -630,6 +726,8 @@ int upload_plan(hog_ctx *ctx, const PlanBuilder &pb, const PlanInfo &info, char 
     std::memcpy(h + L.corrf, pb.corrf.data(), pb.corrf.size() * sizeof(Job));
     std::memcpy(h + L.tc, pb.tc.data(), pb.tc.size() * sizeof(Job));
     std::memcpy(h + L.tcr, pb.tcr.data(), pb.tcr.size() * sizeof(Job));
+    std::memcpy(h + L.bands, pb.bands.data(), pb.bands.size() * sizeof(TcBand));
+    std::memcpy(h + L.cta_first, pb.cta_first.data(), pb.cta_first.size() * sizeof(int32_t));
     std::memcpy(h + L.items, pb.items.data(), pb.items.size() * sizeof(FusedItem));
     CUDA_TRY(ctx, cudaMemcpyAsync(d_dst ? d_dst : ctx->d_plan, h, L.total, cudaMemcpyHostToDevice,
                                   stream));
@@ -662,7 +760,12 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
                               ctx->p.eps, ctx->p.trunc, stream));
     CUDA_TRY(ctx, mark(5));
     CUDA_TRY(ctx, mark(6));
-    if (info.ntc > 0 || info.ntcr > 0)
+    if (info.tcf_grid > 0)
+        CUDA_TRY(ctx, launch_corr_tcf(descs, reinterpret_cast<const TcBand *>(d + L.bands),
+                                      reinterpret_cast<const int32_t *>(d + L.cta_first), info.tcf_grid,
+                                      ctx->d_wtc, ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
+                                      stream));
+    else if (info.ntc > 0 || info.ntcr > 0)
         CUDA_TRY(ctx, launch_corr_tc(descs, reinterpret_cast<const Job *>(d + L.tc), info.ntc,
                                      reinterpret_cast<const Job *>(d + L.tcr), info.ntcr, ctx->d_wtc,
                                      ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
@@ -683,15 +786,16 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
         st[0].launches += npyr; st[0].units += info.px;
         st[1].launches += info.nhist > 0; st[1].units += info.nhist > 0 ? info.cells : 0;
         st[2].launches += info.nfeat > 0; st[2].units += info.nfeat > 0 ? info.cells : 0;
-        st[3].launches += (info.ncorr > 0) + (info.ntc > 0) + (info.ntcr > 0);
-        st[3].units += (info.ncorr > 0 || info.ntcr > 0) ? info.wins : 0;
+        st[3].launches += (info.ncorr > 0) + (info.ntc > 0) + (info.ntcr > 0) + (info.tcf_grid > 0);
+        st[3].units += (info.ncorr > 0 || info.ntcr > 0 || info.tcf_grid > 0) ? info.wins : 0;
         st[4].launches += info.nframes > 0; st[4].units += info.nframes;
     }
     return HOG_OK;
 }
 
 // Build, upload and launch a one-off plan (inspection entry points).
-int run_plan(hog_ctx *ctx, const PlanBuilder &pb, cudaStream_t stream) {
+int run_plan(hog_ctx *ctx, PlanBuilder &pb, cudaStream_t stream) {
+    build_tc_bands(pb, ctx->num_sms);
     PlanInfo info;
     layout_plan(pb, ctx->nf, info);
     int rc = upload_plan(ctx, pb, info, nullptr, stream);
@@ -734,6 +838,7 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
         add_frame(ctx, pb, *g, f, i, frame_base + i, o);
     }
     build_fused_items(pb);
+    build_tc_bands(pb, ctx->num_sms);
     PlanInfo info;
     layout_plan(pb, ctx->nf, info);
     // least recently used entry (or a free one)
@@ -795,7 +900,12 @@ int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStr
     };
     CUDA_TRY(ctx, mark(10));
     CUDA_TRY(ctx, launch_fused(a, ctx->nfk, ctx->fused_grid, stream));
-    if (info.ntc > 0 || info.ntcr > 0)   // tensor-core correlation after the fused stages
+    if (info.tcf_grid > 0)   // tensor-core correlation after the fused stages
+        CUDA_TRY(ctx, launch_corr_tcf(a.descs, reinterpret_cast<const TcBand *>(d + L.bands),
+                                      reinterpret_cast<const int32_t *>(d + L.cta_first), info.tcf_grid,
+                                      ctx->d_wtc, ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
+                                      stream));
+    else if (info.ntc > 0 || info.ntcr > 0)
         CUDA_TRY(ctx, launch_corr_tc(a.descs, reinterpret_cast<const Job *>(d + L.tc), info.ntc,
                                      reinterpret_cast<const Job *>(d + L.tcr), info.ntcr, ctx->d_wtc,
                                      ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
@@ -809,7 +919,7 @@ int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStr
     if (ctx->prof) {
         ctx->prof_pending = true;
         ctx->prof_mask = (1u << 4) | (1u << 5);
-        ctx->stats[5].launches += (info.nitems > 0) + (info.ntc > 0) + (info.ntcr > 0);
+        ctx->stats[5].launches += (info.nitems > 0) + (info.ntc > 0) + (info.ntcr > 0) + (info.tcf_grid > 0);
         ctx->stats[5].units += info.wins;
         ctx->stats[4].launches += info.nframes > 0; ctx->stats[4].units += info.nframes;
     }
@@ -1073,7 +1183,7 @@ int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters
     }
     // tensor-core correlation by default; the CUDA-core engine if its
     // buffers cannot be had
-    if (prepare_tc(ctx) == HOG_OK) {
+    if (prepare_tc(ctx, false) == HOG_OK) {
         ctx->corr_engine = 1;
     } else {
         cudaGetLastError();
@@ -1088,9 +1198,9 @@ int hog_set_filters(hog_ctx *ctx, const float *filters_host, int32_t n_filters) 
     cudaDeviceSynchronize();
     const int nfk0 = ctx->nfk;
     int rc = upload_filters(ctx, filters_host, n_filters);
-    if (rc == HOG_OK && ctx->corr_engine == 1) {
+    if (rc == HOG_OK && ctx->corr_engine >= 1) {
         if (ctx->nfk != nfk0) clear_plans(ctx);   // row-shift matrices change size
-        rc = prepare_tc(ctx);
+        rc = prepare_tc(ctx, ctx->corr_engine == 2);
     }
     return rc;
 }
@@ -1239,11 +1349,11 @@ int hog_detect_batched(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, 
 }
 
 int hog_set_corr_engine(hog_ctx *ctx, int32_t engine) {
-    if (!ctx || (engine != 0 && engine != 1)) return HOG_EINVAL;
+    if (!ctx || engine < 0 || engine > 2) return HOG_EINVAL;
     if (engine == ctx->corr_engine) return HOG_OK;
     clear_plans(ctx);   // plans hold the engine's jobs and buffers
-    if (engine == 1) {
-        const int rc = prepare_tc(ctx);
+    if (engine >= 1) {
+        const int rc = prepare_tc(ctx, engine == 2);
         if (rc) return rc;
     }
     ctx->corr_engine = engine;
@@ -1374,7 +1484,7 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
                 if (b != std::string::npos) pol = std::atoi(txt.c_str() + b + 15);
                 if (c != std::string::npos) eng = std::atoi(txt.c_str() + c + 15);
                 if ((mode == MODE_STAGED || mode == MODE_FUSED) && pol >= 0 && pol <= CORR_NSHAPE &&
-                    (eng == 0 || eng == 1)) {
+                    eng >= 0 && eng <= 2) {
                     if (pol != ctx->corr_policy) { ctx->corr_policy = pol; clear_plans(ctx); }
                     const int rc = hog_set_corr_engine(ctx, eng);
                     if (rc) return rc;
@@ -1433,21 +1543,25 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
     }
     ctx->corr_policy = best_pol;
     clear_plans(ctx);
-    double tc_ms = -1.0;
-    if (rc == HOG_OK && hog_set_corr_engine(ctx, 1) == HOG_OK) {
+    // tensor-core engines: 2 (two passes through G), then 1 (fused)
+    double tc_ms = -1.0, tc2_ms = -1.0;
+    int best_engine = 0;
+    for (int eng = 2; eng >= 1 && rc == HOG_OK; eng--) {
+        if (hog_set_corr_engine(ctx, eng) != HOG_OK) {
+            ctx->err.clear();   // no tensor-core buffers: the CUDA-core engine stays
+            continue;
+        }
         float ms = 0.0f;
         hog_stage_stat st[HOG_NSTAGES];
         rc = timed(MODE_STAGED, false, 1, &ms);
         hog_stage_stats(ctx, st, HOG_NSTAGES, 1);
         if (!rc) rc = timed(MODE_STAGED, false, 3, &ms);
         hog_stage_stats(ctx, st, HOG_NSTAGES, 1);
-        if (!rc) {
-            tc_ms = st[3].ms / 5.0;
-            if (st[3].ms >= best_corr) rc = hog_set_corr_engine(ctx, 0);
-        }
-    } else {
-        ctx->err.clear();   // no tensor-core buffers: the CUDA-core engine stays
+        if (rc) break;
+        (eng == 1 ? tc_ms : tc2_ms) = st[3].ms / 5.0;
+        if (st[3].ms < best_corr) { best_corr = st[3].ms; best_engine = eng; }
     }
+    if (rc == HOG_OK && ctx->corr_engine != best_engine) rc = hog_set_corr_engine(ctx, best_engine);
     hog_set_profiling(ctx, was_prof ? 1 : 0);
     if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
     // 2. batched execution mode (both as graphs)
@@ -1465,6 +1579,7 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
                          key.c_str(), ctx->batched_mode, ctx->corr_policy);
             std::fprintf(f, "  \"corr_engine\": %d,\n  \"corr_ms_tensor\": %.4f,\n", ctx->corr_engine,
                          tc_ms);
+            std::fprintf(f, "  \"corr_ms_tensor_two_pass\": %.4f,\n", tc2_ms);
             std::fprintf(f, "  \"ms_per_batch\": {\"staged\": %.4f, \"fused\": %.4f},\n",
                          ms_staged, ms_fused);
             std::fprintf(f, "  \"corr_ms_by_policy\": [");

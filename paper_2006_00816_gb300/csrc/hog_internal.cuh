@@ -104,7 +104,8 @@ struct LevelDesc {
     float *scores_user;     // optional [F][nu][nv] (hog_scores)
     uint64_t *keys;         // [nu][nv] suppression keys of this level
     // tensor-core correlation (when enabled): features as fp16 hi + lo parts,
-    // [cy*cx][32] each, and the row-shift matrix G [10*F][cy*cx] (fp32)
+    // each [4 channel groups][cy*cx][8], and (two-pass form only) the
+    // row-shift matrix G [10*F][cy*cx] (fp32)
     uint16_t *feat_hi, *feat_lo;
     float *gmat;
 };
@@ -209,6 +210,23 @@ cudaError_t launch_corr_tc(const LevelDesc *descs, const Job *jobs, int njobs, c
                            int nrjobs, const uint16_t *wb, int nf_kernel, int nf_real,
                            float threshold, int *flags, int grid, cudaStream_t stream);
 int corr_tc_ctas_per_sm(int nf_kernel);
+
+// Fused tensor-core correlation (GEMM and row-shift reduction in one
+// kernel).  A band is a block of window rows [u0, u1) and window columns
+// [c0, c0 + nvs) of one level; it reads cell rows [u0, u1 + 9) and cell
+// columns [c0, c0 + P), P = nvs + 9 <= TCF_PMAX (P = cx: the full width).
+constexpr int TCF_PMAX = 168;
+struct TcBand {
+    int32_t desc, u0, u1, c0, P, nvs;
+};
+__host__ __device__ constexpr int tcf_ring_rows(int P) { return (128 + P - 1) / P + WIN; }
+__host__ __device__ constexpr int tcf_tiles(int u0, int u1, int P) {
+    return ((u1 + WIN - 1 - u0) * P + 127) / 128;
+}
+// Bands in per-CTA order: CTA k runs bands[cta_first[k] .. cta_first[k+1]).
+cudaError_t launch_corr_tcf(const LevelDesc *descs, const TcBand *bands, const int32_t *cta_first,
+                            int grid, const uint16_t *wb, int nf_kernel, int nf_real,
+                            float threshold, int *flags, cudaStream_t stream);
 
 // ---- asynchronous detection for the serving runtime (hog_api.cu) ---------
 int detect_enqueue(hog_ctx *ctx, const hog_frame *frames, int nb, cudaStream_t stream, int mode,

@@ -331,12 +331,15 @@ __device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float ep
                 hw[o] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
                 lw[o] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
             }
-            uint4 *ph = reinterpret_cast<uint4 *>(d.feat_hi + cell * 32);
-            uint4 *pl = reinterpret_cast<uint4 *>(d.feat_lo + cell * 32);
+            // group-major planes [4 channel groups][cy*cx cells][8 channels]:
+            // a run of cells of one group is contiguous (bulk-copy friendly)
+            const size_t nc = (size_t)d.cy * d.cx;
+            uint4 *ph = reinterpret_cast<uint4 *>(d.feat_hi) + cell;
+            uint4 *pl = reinterpret_cast<uint4 *>(d.feat_lo) + cell;
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                ph[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
-                pl[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                ph[q * nc] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                pl[q * nc] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
             }
         }
     }

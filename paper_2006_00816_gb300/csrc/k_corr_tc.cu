@@ -103,6 +103,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -163,7 +175,8 @@ __global__ void __launch_bounds__(TC_NT) corr_tc_kernel(const LevelDesc *__restr
             const int g = rem / TC_ROWS, r = rem - g * TC_ROWS;
             const int cell = q0 + r;
             const bool ok = cell < ncells;
-            const uint16_t *src = (plane ? d.feat_lo : d.feat_hi) + (size_t)(ok ? cell : 0) * 32 + g * 8;
+            const uint16_t *src =
+                (plane ? d.feat_lo : d.feat_hi) + ((size_t)g * ncells + (ok ? cell : 0)) * 8;
             cp_async16_zfill(As + ((size_t)(plane * 4 + g) * TC_ROWS + r) * 16, src, ok);
         }
         cp_async_wait_all();
@@ -280,6 +293,375 @@ __global__ void corr_tc_weights_kernel(const float *__restrict__ w, int nf_real,
     const __half lo = __float2half_rn(x - __half2float(hi));
     wb[idx] = __half_as_ushort(hi);
     wb[PLANE + idx] = __half_as_ushort(lo);
+}
+
+// ===========================================================================
+// Fused form: GEMM and row-shift reduction in one kernel, G never leaves
+// the SM.  A CTA owns bands of window rows (whole levels in large batches)
+// and walks each band's cells in row-major order in 128-cell tiles.  For a
+// tile's cell (r, v) and filter row a, G[a F + f] is the a-th term of
+// window (r - a, v); a ring of partial scores in shared memory, one row per
+// window row in flight, collects the terms:
+//   a = 0: ring = 0 + G[f]          (window row r opens)
+//   a > 0: ring += G[a F + f]
+//   a = 9: the window is complete -> scores, threshold, key.
+// Within one tile the ten steps are separated by barriers: cells of one
+// column in consecutive rows add into the same window at consecutive steps.
+// Cell rows are visited in increasing order, so every window sums its ten
+// terms in the order a = 0..9 whatever the banding -- the same sum, bit for
+// bit, as the two-pass reduce kernel.
+//
+// Warp roles (192 threads, one CTA per SM): warps 0-3 read the accumulator
+// (TMEM lane quarters) and run the ring; warp 4 issues the MMAs; warp 5
+// stages A tiles with bulk copies (cp.async.bulk, mbarrier complete_tx) into
+// a 3-stage ring.  Two TMEM accumulators let the MMAs of tile k+1 run while
+// the epilogue reads tile k.  Every wait is bounded; on expiry the CTA
+// stops, drains its copies and MMAs, frees TMEM and sets flags[2].
+namespace {
+constexpr int TF_EPI = 128;                 // epilogue threads (warps 0-3)
+constexpr int TF_NT = 192;                  // + MMA warp + producer warp
+constexpr int TF_STAGES = 3;
+constexpr size_t TF_A_STAGE = 2 * TC_A_PLANE;   // hi + lo planes of one tile
+// ring entries per filter: max over P <= TCF_PMAX of tcf_ring_rows(P) * (P - 9)
+constexpr int tf_ring_max() {
+    int m = 0;
+    for (int P = WIN; P <= TCF_PMAX; P++) {
+        const int e = tcf_ring_rows(P) * (P - WIN + 1);
+        m = e > m ? e : m;
+    }
+    return m;
+}
+constexpr int TF_RING = tf_ring_max();
+// TMEM columns per accumulator: a power of two >= N (accumulator 1 starts there)
+__host__ __device__ constexpr int tf_acc(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : 128); }
+__host__ __device__ constexpr int tf_alloc(int cols) {
+    return cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : 256));
+}
+__host__ __device__ constexpr size_t tf_smem(int nf) {
+    return 2 * tc_b_plane(nf) + TF_STAGES * TF_A_STAGE + sizeof(float) * (size_t)nf * TF_RING;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+// Bounded wait on the phase of parity `parity`; false if it gave up or
+// another role of the CTA already did.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int *abort_flag) {
+    long long spins = 0;
+    while (!mbar_try(mbar, parity)) {
+        if (*abort_flag || ++spins >= TC_SPIN) return false;
+        if (spins > 64) __nanosleep(32);
+    }
+    return true;
+}
+__device__ __forceinline__ void epi_sync() {   // the four epilogue warps
+    asm volatile("bar.sync 1, %0;" ::"n"(TF_EPI) : "memory");
+}
+__device__ __forceinline__ bool epi_all(bool ok) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\t"
+                 "setp.ne.u32 p, %1, 0;\n\t"
+                 "bar.red.and.pred q, 1, %2, p;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)ok), "n"(TF_EPI) : "memory");
+    return r != 0;
+}
+
+// Cells [q, q + n) of a band's local row-major order that lie in one
+// contiguous run of the level's cell planes: returns the run's length and
+// its first cell index in the level.
+__device__ __forceinline__ int band_run(const TcBand &b, int cx, int q, int n, int *gcell) {
+    if (b.P == cx) {   // full width: rows are contiguous in the level
+        *gcell = b.u0 * cx + q;
+        return n;
+    }
+    const int r = q / b.P, cl = q - r * b.P;
+    *gcell = (b.u0 + r) * cx + b.c0 + cl;
+    return min(n, b.P - cl);
+}
+}  // namespace
+
+template <int NF>
+__global__ void __launch_bounds__(TF_NT, 1) corr_tcf_kernel(const LevelDesc *__restrict__ descs,
+                                                           const TcBand *__restrict__ bands,
+                                                           const int32_t *__restrict__ cta_first,
+                                                           const uint16_t *__restrict__ wb,
+                                                           int nf_real, float threshold, int *flags) {
+    constexpr int N = tc_n(NF), ACC = tf_acc(N), COLS = tf_alloc(2 * ACC);
+    constexpr size_t BP = tc_b_plane(NF);
+    extern __shared__ __align__(128) unsigned char sm[];
+    unsigned char *Bs = sm;                                  // [hi, lo][10][4][N][16 B]
+    unsigned char *As = sm + 2 * BP;                         // [stage][hi, lo][4][137][16 B]
+    float *ring = reinterpret_cast<float *>(As + TF_STAGES * TF_A_STAGE);   // [NF][TF_RING]
+    __shared__ __align__(8) uint64_t bar_full[TF_STAGES], bar_empty[TF_STAGES];
+    __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
+    __shared__ uint32_t tslot;
+    __shared__ volatile int s_abort;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+
+    for (int k = t; k < (int)(2 * BP / 16); k += TF_NT)
+        cp_async16(Bs + 16 * (size_t)k, reinterpret_cast<const unsigned char *>(wb) + 16 * (size_t)k);
+    if (t == 0) {
+        for (int i = 0; i < TF_STAGES; i++) {
+            mbar_init(smem_addr(&bar_full[i]), 1);    // producer's arrive.expect_tx
+            mbar_init(smem_addr(&bar_empty[i]), 1);   // MMA commit
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(smem_addr(&bar_tfull[i]), 1);   // MMA commit
+            mbar_init(smem_addr(&bar_tempty[i]), 4);  // one arrive per epilogue warp
+        }
+        mbar_init(smem_addr(&bar_drain), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_addr(&tslot)), "r"(COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    cp_async_wait_all();
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tbase = tslot;
+    const int first = cta_first[blockIdx.x], last = cta_first[blockIdx.x + 1];
+    int issued[TF_STAGES] = {0, 0, 0};   // producer: batches issued per stage
+
+    if (warp == 5) {
+        // ---- producer: A tiles (hi and lo planes, 137 cells) by bulk copies
+        int stage = 0, use = 0;   // use = how many tiles went through stage so far / TF_STAGES
+        bool ok = true;
+        for (int bi = first; bi < last && ok; bi++) {
+            const TcBand b = bands[bi];
+            const LevelDesc &d = descs[b.desc];
+            const int nc = d.cx * d.cy;
+            const int ncl = (b.u1 + WIN - 1 - b.u0) * b.P;   // local cells of the band
+            const int nt = tcf_tiles(b.u0, b.u1, b.P);
+            for (int tile = 0; tile < nt; tile++) {
+                // warp-uniform decision (lanes poll independently)
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait(smem_addr(&bar_empty[stage]), (uint32_t)((use & 1) ^ 1), &s_abort));
+                if (!ok) { s_abort = 1; break; }
+                const int q0 = tile * TC_M, qe = min(q0 + TC_ROWS, ncl);
+                // total bytes of this tile's runs (every lane computes the same)
+                uint32_t bytes = 0;
+                for (int q = q0; q < qe;) {
+                    int gc;
+                    const int n = band_run(b, d.cx, q, qe - q, &gc);
+                    bytes += (uint32_t)n * 16u * 8u;
+                    q += n;
+                }
+                const uint32_t fb = smem_addr(&bar_full[stage]);
+                if (lane == 0) mbar_expect_tx(fb, bytes);
+                __syncwarp();
+                const uint32_t abase = smem_addr(As + stage * TF_A_STAGE);
+                int k = 0;
+                for (int q = q0; q < qe; k++) {
+                    int gc;
+                    const int n = band_run(b, d.cx, q, qe - q, &gc);
+                    // lanes 8k .. 8k+7 copy (plane, group) = lane & 7 of run k
+                    if ((lane >> 3) == (k & 3)) {
+                        const int pg = lane & 7, plane = pg >> 2, g = pg & 3;
+                        const uint16_t *src = (plane ? d.feat_lo : d.feat_hi) + ((size_t)g * nc + gc) * 8;
+                        const uint32_t dst = abase + (uint32_t)(((plane * 4 + g) * TC_ROWS + (q - q0)) * 16);
+                        bulk_g2s(dst, src, (uint32_t)n * 16u, fb);
+                    }
+                    q += n;
+                }
+                __syncwarp();
+                issued[stage]++;
+                if (++stage == TF_STAGES) { stage = 0; use++; }
+            }
+        }
+    } else if (warp == 4) {
+        // ---- MMA issuer
+        int stage = 0, use = 0, acc = 0, ause = 0;
+        constexpr uint32_t IDESC = tc_idesc(N);
+        const uint32_t b_s = smem_addr(Bs);
+        bool ok = true;
+        for (int bi = first; bi < last && ok; bi++) {
+            const TcBand b = bands[bi];
+            const int nt = tcf_tiles(b.u0, b.u1, b.P);
+            for (int tile = 0; tile < nt; tile++) {
+                ok = mbar_wait(smem_addr(&bar_full[stage]), (uint32_t)(use & 1), &s_abort) &&
+                     mbar_wait(smem_addr(&bar_tempty[acc]), (uint32_t)((ause & 1) ^ 1), &s_abort);
+                ok = __all_sync(0xffffffffu, ok);   // warp-uniform decision
+                if (!ok) { s_abort = 1; break; }
+                fence_after();
+                if (lane == 0) {
+                    // descriptors: the start-address field (bits 0-13, address
+                    // >> 4) of a base descriptor plus compile-time offsets in
+                    // 16-byte units (shared addresses < 256 KB: no carry)
+                    const uint64_t ah0 = sdesc(smem_addr(As + stage * TF_A_STAGE), TC_ROWS * 16, 128);
+                    const uint64_t bh0 = sdesc(b_s, N * 16, 128);
+                    const uint32_t d_t = tbase + (uint32_t)(acc * ACC);
+#pragma unroll
+                    for (int s = 0; s < TC_KSTEPS; s++) {
+                        const int bsh = s >> 1, half = s & 1;
+                        const uint64_t aoff = (uint64_t)((2 * half) * TC_ROWS + bsh);
+                        const uint64_t boff = (uint64_t)((bsh * 4 + 2 * half) * N);
+                        const uint64_t ah = ah0 + aoff, al = ah0 + (TC_A_PLANE >> 4) + aoff;
+                        const uint64_t bh = bh0 + boff, bl = bh0 + (BP >> 4) + boff;
+                        mma_f16(d_t, ah, bh, IDESC, s > 0 ? 1u : 0u);
+                        mma_f16(d_t, ah, bl, IDESC, 1u);
+                        mma_f16(d_t, al, bh, IDESC, 1u);
+                    }
+                    mma_commit(smem_addr(&bar_empty[stage]));   // A stage free once read
+                    mma_commit(smem_addr(&bar_tfull[acc]));     // accumulator ready
+                }
+                __syncwarp();
+                if (++stage == TF_STAGES) { stage = 0; use++; }
+                if (++acc == 2) { acc = 0; ause++; }
+            }
+        }
+    } else {
+        // ---- epilogue: accumulator -> ring of partial scores -> keys
+        int acc = 0, ause = 0;
+        bool ok = true;
+        for (int bi = first; bi < last && ok; bi++) {
+            const TcBand b = bands[bi];
+            const LevelDesc &d = descs[b.desc];
+            const int ncl = (b.u1 + WIN - 1 - b.u0) * b.P;
+            const int nt = tcf_tiles(b.u0, b.u1, b.P);
+            const int RS = tcf_ring_rows(b.P);
+            for (int tile = 0; tile < nt; tile++) {
+                ok = epi_all(mbar_wait(smem_addr(&bar_tfull[acc]), (uint32_t)(ause & 1), &s_abort));
+                if (!ok) { s_abort = 1; break; }
+                fence_after();
+                float G[WIN * NF];
+                {
+                    constexpr int NL = (WIN * NF + 15) / 16;
+                    const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * ACC);
+#pragma unroll
+                    uint32_t r[NL][16];
+#pragma unroll
+                    for (int c = 0; c < NL; c++) tmem_ld16_nowait(ta + 16 * c, r[c]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int c = 0; c < NL; c++)
+#pragma unroll
+                        for (int j = 0; j < 16; j++)
+                            if (16 * c + j < WIN * NF) G[16 * c + j] = __uint_as_float(r[c][j]);
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&bar_tempty[acc]));
+                if (++acc == 2) { acc = 0; ause++; }
+
+                const int q = tile * TC_M + t;
+                const int r = q / b.P, cl = q - r * b.P;   // local cell row / column
+                const bool live = q < ncl && cl < b.nvs;
+                const int v = b.c0 + cl;
+                const int nwr = b.u1 - b.u0;
+                // ring slot of window row r - a is (r - a) mod RS: start at
+                // r mod RS and step down by one row of nvs entries per a
+                int idx = (r % RS) * b.nvs + cl;
+                const int wrap = RS * b.nvs;
+#pragma unroll
+                for (int a = 0; a < WIN; a++) {
+                    const int ul = r - a;   // local window row
+                    if (live && ul >= 0 && ul < nwr) {
+                        if (a == 0) {
+#pragma unroll
+                            for (int f = 0; f < NF; f++) ring[f * TF_RING + idx] = 0.0f + G[f];
+                        } else {
+#pragma unroll
+                            for (int f = 0; f < NF; f++) ring[f * TF_RING + idx] += G[a * NF + f];
+                        }
+                        if (a == WIN - 1) {
+                            const int u = b.u0 + ul;
+                            float sc[NF];
+#pragma unroll
+                            for (int f = 0; f < NF; f++) sc[f] = ring[f * TF_RING + idx] * (1.0f / 64.0f);
+                            float best = sc[0];
+                            int fb = 0;
+#pragma unroll
+                            for (int f = 1; f < NF; f++)
+                                if (f < nf_real && sc[f] > best) { best = sc[f]; fb = f; }
+                            if (d.scores_user) {
+#pragma unroll
+                                for (int f = 0; f < NF; f++)
+                                    if (f < nf_real) d.scores_user[((size_t)f * d.nu + u) * d.nv + v] = sc[f];
+                            }
+                            if (d.keys)
+                                d.keys[(size_t)u * d.nv + v] =
+                                    (d.scan && best > threshold) ? make_key(best, d.level, fb, u, v) : KEY_NONE;
+                        }
+                    }
+                    idx -= b.nvs;
+                    if (idx < 0) idx += wrap;
+                    epi_sync();
+                }
+            }
+        }
+    }
+
+    // ---- teardown: no copy or MMA may still be in flight when TMEM is
+    // freed and the CTA exits
+    __syncthreads();
+    if (warp == 5 && s_abort) {
+        for (int i = 0; i < TF_STAGES; i++) {
+            if (issued[i] == 0) continue;
+            long long spins = 0;
+            while (!mbar_try(smem_addr(&bar_full[i]), (uint32_t)((issued[i] - 1) & 1)) && ++spins < TC_SPIN)
+                __nanosleep(64);
+        }
+    }
+    if (warp == 4) {
+        if (lane == 0) mma_commit(smem_addr(&bar_drain));
+        __syncwarp();
+        long long spins = 0;
+        while (!mbar_try(smem_addr(&bar_drain), 0u) && ++spins < TC_SPIN) __nanosleep(64);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(COLS)
+                     : "memory");
+    if (t == 0 && s_abort) atomicOr(flags + 2, 1);
+}
+
+namespace {
+template <int NF>
+cudaError_t launch_tcf_t(const LevelDesc *descs, const TcBand *bands, const int32_t *cta_first, int grid,
+                         const uint16_t *wb, int nf_real, float threshold, int *flags,
+                         cudaStream_t stream) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(corr_tcf_kernel<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tf_smem(NF));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (grid > 0)
+        corr_tcf_kernel<NF><<<grid, TF_NT, tf_smem(NF), stream>>>(descs, bands, cta_first, wb, nf_real,
+                                                                  threshold, flags);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_corr_tcf(const LevelDesc *descs, const TcBand *bands, const int32_t *cta_first,
+                            int grid, const uint16_t *wb, int nf_kernel, int nf_real, float threshold,
+                            int *flags, cudaStream_t stream) {
+    switch (nf_kernel) {
+    case 1: return launch_tcf_t<1>(descs, bands, cta_first, grid, wb, nf_real, threshold, flags, stream);
+    case 5: return launch_tcf_t<5>(descs, bands, cta_first, grid, wb, nf_real, threshold, flags, stream);
+    case 8: return launch_tcf_t<8>(descs, bands, cta_first, grid, wb, nf_real, threshold, flags, stream);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 namespace {

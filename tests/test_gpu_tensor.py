@@ -1,10 +1,13 @@
-"""GPU tests of the two correlation engines (hog_set_corr_engine): the
-tcgen05 tensor-core contraction (fp16 hi/lo split, three MMAs per K step,
-row-shift reduction) and the FP32 CUDA-core kernel, each against the FP64
-oracle (scores |g-o| <= 1e-4, the bar of Section 4.1.1's linear filter);
-suppression exact on each engine's own scores; batched modes bit-identical
-to the per-frame call under each engine; ragged levels smaller than one
-128-cell tile; engine and filter-count changes."""
+"""GPU tests of the correlation engines (hog_set_corr_engine): the tcgen05
+tensor-core contraction (fp16 hi/lo split, three MMAs per K step) with the
+row-shift reduction fused on chip (engine 1) or in a second pass (engine
+2), and the FP32 CUDA-core kernel (engine 0), each against the FP64 oracle
+(scores |g-o| <= 1e-4, the bar of Section 4.1.1's linear filter); engines 1
+and 2 bit-identical; suppression exact on each engine's own scores; batched
+modes bit-identical to the per-frame call under each engine (the fused
+engine bands levels differently for one frame and for a batch); ragged
+levels smaller than one 128-cell tile; frames wider than one band strip;
+engine and filter-count changes."""
 import numpy as np
 import pytest
 
@@ -35,7 +38,8 @@ def dev(a):
 
 
 CASES = [("cfg1_320x240", 1), ("eyeblink_640x480", 5), ("eyeblink_640x480", 8),
-         ("sxga_1280x1024", 5), ("odd_81x97", 5), ("ragged_333x211", 1)]
+         ("sxga_1280x1024", 5), ("odd_81x97", 5), ("ragged_333x211", 1),
+         ("wide_2000x120", 5), ("wide_2000x120", 8)]
 
 
 def _frame(S, name):
@@ -47,6 +51,8 @@ def _frame(S, name):
         return S.camera_frame(4, 2)
     if name == "odd_81x97":
         return np.random.default_rng(77).integers(0, 256, (97, 81), dtype=np.uint8)
+    if name == "wide_2000x120":       # 250 cells wide: two band strips at level 0
+        return S.single_frame(2000, 120, config=14)
     return S.single_frame(333, 211, config=13)
 
 
@@ -58,7 +64,7 @@ def test_scores_both_engines_vs_oracle(H, S, oracle, name, nf):
     det = H.Detector(W, max_w=w, max_h=h, max_batch=2)
     ref = oracle.frame_scores(f, W)
     got = {}
-    for e in (1, 0):
+    for e in (1, 2, 0):
         det.set_corr_engine(e)
         assert det.corr_engine() == e
         got[e] = [s.cpu().numpy() for s in det.scores(dev(f))]
@@ -68,6 +74,8 @@ def test_scores_both_engines_vs_oracle(H, S, oracle, name, nf):
             assert np.abs(a - b).max() <= SCORE_ATOL, (e, np.abs(a - b).max())
     for a, b in zip(got[0], got[1]):
         assert np.abs(a - b).max() <= 1e-5
+    for a, b in zip(got[1], got[2]):
+        assert a.tobytes() == b.tobytes()      # same MMAs, same summation order
 
 
 def _kept(rows):
@@ -75,7 +83,7 @@ def _kept(rows):
                    float(np.float32(r["score"]))) for r in rows)
 
 
-@pytest.mark.parametrize("engine", [1, 0])
+@pytest.mark.parametrize("engine", [1, 2, 0])
 def test_nms_exact_on_each_engines_scores(H, S, oracle, engine):
     f = S.camera_frame(5, 1)
     W = S.filters(5)
@@ -99,7 +107,7 @@ def test_nms_exact_on_each_engines_scores(H, S, oracle, engine):
     assert _kept(dets) == _kept(srt[keep])
 
 
-@pytest.mark.parametrize("engine", [1, 0])
+@pytest.mark.parametrize("engine", [1, 2, 0])
 def test_batched_modes_identical_per_engine(H, S, engine):
     frames = [dev(f) for f in S.mixed_frames(7)] + [
         dev(np.full((90, 100), 7, np.uint8)), dev(np.full((60, 300), 9, np.uint8)),
@@ -129,8 +137,15 @@ def test_engine_switch_and_filter_change(H, S, oracle):
     s = det.scores(dev(f))
     for x, o in zip(s, oracle.frame_scores(f, W1)):
         assert np.abs(x.cpu().numpy() - o).max() <= SCORE_ATOL
+    det.set_corr_engine(2)                     # two-pass form: same scores and boxes
+    s2 = det.scores(dev(f))
+    assert all(x.cpu().numpy().tobytes() == y.cpu().numpy().tobytes() for x, y in zip(s, s2))
+    c = det.detect([dev(f)])
+    det.set_corr_engine(1)
     with pytest.raises(H.HogError):
-        det.set_corr_engine(2)
+        det.set_corr_engine(3)
+    assert det.corr_engine() == 1
+    assert c[0].tobytes() == det.detect([dev(f)])[0].tobytes()
 
 
 def test_autotune_records_engine(H, S, tmp_path):
@@ -141,9 +156,9 @@ def test_autotune_records_engine(H, S, tmp_path):
     path = str(tmp_path / "tune.json")
     det.autotune(frames, cache_path=path)
     rec = json.load(open(path))
-    assert rec["corr_engine"] in (0, 1) and rec["corr_engine"] == det.corr_engine()
-    assert rec["corr_ms_tensor"] > 0
+    assert rec["corr_engine"] in (0, 1, 2) and rec["corr_engine"] == det.corr_engine()
+    assert rec["corr_ms_tensor"] > 0 and rec["corr_ms_tensor_two_pass"] > 0
     det2 = H.Detector(S.filters(5), max_w=640, max_h=480, max_batch=8)
-    det2.set_corr_engine(1 - rec["corr_engine"])
+    det2.set_corr_engine((rec["corr_engine"] + 1) % 3)
     det2.autotune(frames, cache_path=path)     # loaded from the file, not measured
     assert det2.corr_engine() == rec["corr_engine"]
