@@ -133,7 +133,7 @@ struct hog_ctx {
     uint8_t *d_pyr = nullptr;
     float *d_hist = nullptr, *d_feat = nullptr;
     uint64_t *d_keys = nullptr;
-    uint32_t *d_nmsws = nullptr;    // suppression workspace, 13 bytes (4 words) per position
+    uint32_t *d_nmsws = nullptr;    // suppression workspace, 14 bytes (4 words) per position
     hog_det *d_dets = nullptr;
     int32_t *d_counts = nullptr;
     int *d_flags = nullptr;

@@ -118,7 +118,7 @@ struct FrameDesc {
     int32_t lev_nu[MAX_LEVELS], lev_nv[MAX_LEVELS];
     int32_t lev_pos[MAX_LEVELS + 1];
     const uint64_t *keys;             // [npos]
-    uint32_t *ws;                     // suppression workspace (global mode), 5 B per position
+    uint32_t *ws;                     // suppression workspace (global mode), 14 B per position
     const int32_t *nbr;               // [MAXN][npos] neighbour lists, slot-major
     const uint8_t *nbr_cnt;           // [npos]
     hog_det *out;                     // [out_cap]

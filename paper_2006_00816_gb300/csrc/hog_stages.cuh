@@ -11,6 +11,8 @@
 
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "hog_internal.cuh"
 
 namespace hogk {
@@ -78,14 +80,13 @@ __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
 // no sum longer than 64 terms.  256 threads own 16x16 blocks and emit the
 // 15x15 cells whose four blocks they hold.
 //
-// Orientation in exact integer arithmetic: fold (dx, dy) into the first
-// quadrant; the sector is the number of bin boundaries (10, 30, 50, 70
-// degrees) the vector lies beyond, tested as |dy| C - |dx| S > 0 with
-// C, S = round(2^20 cos, 2^20 sin).  For every 8-bit gradient this equals
-// the exact test (smallest |dy cos - dx sin| on the grid 1.3e-3 = 1340 units
-// at 2^20, against at most 255 units of rounding); products fit in int32.
-// dx == 0 (the only exact tie) goes to bin 4 (dy > 0) or 13.  Branch-free:
-// the quadrant is resolved with selects.
+// Orientation: fold (dx, dy) into the first quadrant; the sector q is the
+// number of bin boundaries (10, 30, 50, 70 degrees) the vector lies beyond,
+// tested in FP32 as |dy| > fl(|dx| tan(boundary)).  For every 8-bit
+// gradient this equals the exact test: the gap between |dy| and |dx|
+// tan(boundary) is at least 2.0e-3 on the integer grid, the rounding of the
+// product at most 4e-5.  dx == 0 (the only exact tie) goes to bin 4 (dy > 0)
+// or 13.  Branch-free: the quadrant is resolved with selects.
 namespace hist_cfg {
 constexpr int NT = HIST_BX * HIST_BY;          // 256 threads, one per block
 constexpr int PX = HIST_BX * CELL + 2;         // 130 staged columns (blocks + 1-px halo)
@@ -98,17 +99,18 @@ constexpr size_t SMEM_XB = sizeof(int) * 132;
 constexpr size_t SMEM = SMEM_PART + SMEM_SRC + SMEM_XB;             // 95,056
 }  // namespace hist_cfg
 
-__device__ __forceinline__ int orientation_bin_i(int dx, int dy) {
-    const int ax = dx < 0 ? -dx : dx;
-    const int ay = dy < 0 ? -dy : dy;
-    const int q = (ay * 1032646 - ax * 182083 > 0) + (ay * 908093 - ax * 524288 > 0) +
-                  (ay * 674012 - ax * 803256 > 0) + (ay * 358634 - ax * 985339 > 0);
-    // dx == 0 (q = 4 when dy != 0) is placed on the right half-plane for
-    // dy > 0 (bin 4) and on the left one for dy < 0 (bin 13); selects only
+__device__ __forceinline__ int orientation_bin_f(int dx, int dy) {
+    const float fx = (float)(dx < 0 ? -dx : dx);
+    const float fy = (float)(dy < 0 ? -dy : dy);
+    // tan 10, 30, 50, 70 degrees rounded to FP32
+    const int q = (fy > fx * 0.17632698f) + (fy > fx * 0.57735026f) + (fy > fx * 1.19175363f) +
+                  (fy > fx * 2.74747753f);
+    // right half-plane (dx == 0: dy > 0 is on the right): bins q or 18 - q;
+    // left: 9 - q or 9 + q
     const bool right = dx > 0 || (dx == 0 && dy > 0);
-    const int up = right ? q : 9 - q;
-    const int dn = right ? (q == 0 ? 0 : 18 - q) : 9 + q;
-    return dy >= 0 ? up : dn;
+    const int base = right ? 0 : 9;
+    const int b = (right == (dy >= 0)) ? base + q : base - q;
+    return b < 0 ? b + 18 : b;
 }
 
 // Tent weight of footprint offset t (0..15) in sixteenths: 16 - |2t - 15|.
@@ -148,17 +150,25 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         if (ci == 0) xbase[r] = (int)((intptr_t)c0 - (intptr_t)rp);
         if (a <= rp + (uintptr_t)(xb - 1)) cp_async16(srcS + r * SROWB + 16 * ci, (const void *)a);
     }
-    for (int k = t; k < 4 * NBIN * NT; k += NT) part[k] = 0.0f;
+    for (int k = t; k < NBIN * NT; k += NT) reinterpret_cast<float4 *>(part)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     cp_async_wait_all();
     __syncthreads();
 
     // one 8x8 block per thread: pixels X = 8 bj - 4 + ox, Y = 8 bi - 4 + oy.
     // Pixels outside the voting range (X < 1, X > xmax) read staged bytes
-    // that exist but vote with magnitude 0; zero gradients vote 0 as well
-    // (adding +0 leaves the non-negative partials unchanged).  Magnitude
-    // sqrt(s) of the exact integer s = dx^2 + dy^2 as s * rsqrt(s).
+    // that exist but vote with weight 0 (their column's tent weights are
+    // zeroed); zero gradients vote 0 as well (adding +0 leaves the
+    // non-negative partials unchanged).  Magnitude sqrt(s) of the exact
+    // integer s = dx^2 + dy^2 as s * rsqrt(s).
     const int by = t / HIST_BX, bx = t - by * HIST_BX;
     const int X0 = CELL * (j0 + bx) - 4, Y0 = CELL * (i0 + by) - 4;
+    float wx0v[8], wx1v[8];   // column tent weights to cell cols bj-1, bj (0: no vote)
+#pragma unroll
+    for (int ox = 0; ox < 8; ox++) {
+        const bool ok = X0 + ox >= 1 && X0 + ox <= xmax;
+        wx0v[ox] = ok ? tent16(ox + 8) : 0.0f;
+        wx1v[ox] = ok ? tent16(ox) : 0.0f;
+    }
     float *p0 = part + t;
 #pragma unroll 1
     for (int oy = 0; oy < 8; oy++) {
@@ -174,16 +184,15 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
             const int X = X0 + ox;
             const int dx = (int)mid[X + 1] - (int)mid[X - 1];
             const int dy = (int)dn[X] - (int)up[X];
-            const int b = orientation_bin_i(dx, dy);
-            const int s2 = dx * dx + dy * dy;
-            float m = (float)s2 * rsqrtf((float)max(s2, 1));
-            m = (X >= 1 && X <= xmax) ? m : 0.0f;
-            const float wx1 = tent16(ox), wx0 = tent16(ox + 8);   // to cell cols bj, bj-1
+            const int b = orientation_bin_f(dx, dy);
+            const float sf = (float)(dx * dx + dy * dy);
+            const float m = sf * rsqrtf(fmaxf(sf, 1.0f));
+            const float m0 = m * wy0, m1 = m * wy1;
             float *pb = p0 + b * NT;
-            pb[0 * NBIN * NT] = fmaf(m, wy0 * wx0, pb[0 * NBIN * NT]);   // cell (bi-1, bj-1)
-            pb[1 * NBIN * NT] = fmaf(m, wy0 * wx1, pb[1 * NBIN * NT]);   // cell (bi-1, bj)
-            pb[2 * NBIN * NT] = fmaf(m, wy1 * wx0, pb[2 * NBIN * NT]);   // cell (bi,   bj-1)
-            pb[3 * NBIN * NT] = fmaf(m, wy1 * wx1, pb[3 * NBIN * NT]);   // cell (bi,   bj)
+            pb[0 * NBIN * NT] = fmaf(m0, wx0v[ox], pb[0 * NBIN * NT]);   // cell (bi-1, bj-1)
+            pb[1 * NBIN * NT] = fmaf(m0, wx1v[ox], pb[1 * NBIN * NT]);   // cell (bi-1, bj)
+            pb[2 * NBIN * NT] = fmaf(m1, wx0v[ox], pb[2 * NBIN * NT]);   // cell (bi,   bj-1)
+            pb[3 * NBIN * NT] = fmaf(m1, wx1v[ox], pb[3 * NBIN * NT]);   // cell (bi,   bj)
         }
     }
     __syncthreads();
@@ -523,20 +532,27 @@ __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ desc
 // keep a box unless a kept, higher-ranked box overlaps it with IoU >
 // nms_iou.  The greedy result is the unique set K with "p in K iff no member
 // of K ranked above p overlaps p", reached here by rounds in which every
-// undecided candidate looks at its higher-ranked overlapping neighbours: one
-// of them kept -> suppressed; all of them suppressed -> kept; otherwise it
-// waits.  The best undecided candidate always decides, so the rounds end
-// (about ten rounds on 640x480 frames); decisions are final, so a thread may
-// read a neighbour's state while it changes within a round.
+// undecided candidate p decides or waits:
+//   - p's bit in the suppression bitmask is set (a kept neighbour marked
+//     it) -> p is suppressed;
+//   - otherwise p scans its higher-ranked overlapping neighbours from where
+//     its last scan stopped: one of them kept -> suppressed; one undecided ->
+//     p waits (a neighbour kept later marks p's bit); all suppressed or
+//     ranked below -> p is kept and marks all its neighbours' bits.
+// The best undecided candidate always decides, so the rounds end (about ten
+// rounds on 640x480 frames); decisions are final, so a thread may read a
+// neighbour's state or bit while it changes within a round.  Neighbours
+// passed over (suppressed, or not a candidate above p) stay settled, so a
+// candidate's slots are scanned about once in all.
 //
 // Overlap lists (IoU > nms_iou, FP64) come from the per-frame-size geometry
 // in slot-major order nbr[s * npos + p]: one thread per candidate, so a
-// warp's load of slot s reads consecutive entries, and eight slots are
-// loaded before they are used.  Each round walks a compacted list of the
-// still-undecided candidates, so sparse late rounds cost little.  Ranks compare the key's high word (the
-// score order) held in shared memory; equal high words fall back to the full
-// key in global memory.  Workspace: 5 bytes per window position, in shared
-// memory (SM) or in fd.ws.  NT threads.
+// warp's load of slot s reads consecutive entries.  Each round walks a
+// compacted list of the still-undecided candidates, so sparse late rounds
+// cost little.  Ranks compare the key's high word (the score order) held in
+// shared memory; equal high words fall back to the full key in global
+// memory.  Workspace (nms_ws_bytes): in shared memory (SM, candidate lists of
+// 16-bit positions) or in fd.ws (32-bit positions).  NT threads.
 constexpr uint8_t NMS_ALIVE = 1, NMS_KEPT = 2, NMS_DEAD = 0;
 constexpr uint32_t NMS_NOKEY = 0xffffffffu;   // key high word of a non-candidate
 
@@ -555,18 +571,35 @@ __device__ __forceinline__ WinBox window_box(int W0, int H0, int Wl, int Hl, int
     return b;
 }
 
-__host__ __device__ constexpr size_t nms_ws_bytes(int npos) { return (size_t)npos * 13 + 64; }
+// Workspace per frame: key high words (4 B per position), two candidate
+// lists (2 B per position each in shared memory, 4 B in global memory), the
+// suppression bitmask (1 bit), state and resume slot (1 B each).
+__host__ __device__ constexpr size_t nms_ws_bytes(int npos, bool in_smem) {
+    return (size_t)npos * (in_smem ? 10 : 14) + 4 * (size_t)((npos + 31) / 32) + 64;
+}
+// Positions a shared-memory workspace can index (16-bit list entries).
+constexpr int NMS_SMEM_MAX_NPOS = 65535;
 
 template <bool SM, int NT, bool COH>
 __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *smem, int *flags,
                                           int *sh /* NT/32 + 4 ints of shared memory */) {
+    using idx_t = typename std::conditional<SM, uint16_t, int32_t>::type;
     const int t = threadIdx.x;
     const int npos = fd.npos;
     unsigned char *base = SM ? smem : reinterpret_cast<unsigned char *>(fd.ws);
     uint32_t *khi = reinterpret_cast<uint32_t *>(base);              // key high words
-    int32_t *list[2] = {reinterpret_cast<int32_t *>(base) + npos,    // undecided candidates,
-                        reinterpret_cast<int32_t *>(base) + 2 * (size_t)npos};   // double buffer
-    volatile uint8_t *state = base + (size_t)npos * 12;
+    idx_t *list[2] = {reinterpret_cast<idx_t *>(base + 4 * (size_t)npos),   // undecided
+                      reinterpret_cast<idx_t *>(base + 4 * (size_t)npos) + npos};   // (double buffer)
+    // suppression bitmask: bit q set once a neighbour of q has been kept, so
+    // q (if ranked below it) is suppressed without scanning its neighbours
+    const int nwords = (npos + 31) / 32;
+    const size_t off_supp = (size_t)npos * (4 + 2 * sizeof(idx_t));
+    volatile uint32_t *supp = reinterpret_cast<volatile uint32_t *>(base + off_supp);
+    volatile uint8_t *state = base + off_supp + 4 * (size_t)nwords;
+    // per candidate: how many leading neighbour slots are settled for good
+    // (not a candidate, ranked below, or suppressed); later rounds resume
+    // the scan there.  Written and read by the candidate's own thread only.
+    uint8_t *resume = base + off_supp + 4 * (size_t)nwords + npos;
     const uint64_t *gkeys = fd.keys;
     const int32_t *__restrict__ nbr = fd.nbr;                        // [slot][npos]
     const uint8_t *__restrict__ nbr_cnt = fd.nbr_cnt;
@@ -585,10 +618,11 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
         int b0 = 0;
         if (lane == __ffs(m) - 1) b0 = atomicAdd(s_n + which, __popc(m));
         b0 = __shfl_sync(0xffffffffu, b0, __ffs(m) - 1);
-        if (flag) list[which][b0 + __popc(m & ((1u << lane) - 1))] = p;
+        if (flag) list[which][b0 + __popc(m & ((1u << lane) - 1))] = (idx_t)p;
     };
 
     if (t == 0) { s_n[0] = 0; s_n[1] = 0; }
+    for (int k = t; k < nwords; k += NT) supp[k] = 0u;
     __syncthreads();
     for (int p0 = 0; p0 < npos; p0 += NT) {          // whole warps iterate together
         const int p = p0 + t;
@@ -597,6 +631,7 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
             h = (uint32_t)(ld_in<COH>(gkeys + p) >> 32);
             khi[p] = h;
             state[p] = h != NMS_NOKEY ? NMS_ALIVE : NMS_DEAD;
+            resume[p] = 0;
         }
         append(h != NMS_NOKEY, p, 0);
     }
@@ -610,31 +645,54 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
         __syncthreads();
         for (int i0 = 0; i0 < n_cur; i0 += NT) {     // whole warps iterate together
             const int i = i0 + t;
-            bool undecided = false;
+            bool undecided = false, kept = false;
             int p = -1;
             if (i < n_cur) {
                 p = list[cur][i];
                 const uint32_t hp = khi[p];
                 const int n = __ldg(nbr_cnt + p);
-                bool dead = false, wait = false;
-                for (int s0 = 0; s0 < n && !dead; s0 += 8) {
-                    int q[8];
+                bool dead = (supp[p >> 5] >> (p & 31)) & 1u, wait = false;
+                // scan the unsettled slots up to the first higher-ranked
+                // neighbour that is kept (p is suppressed) or undecided (p
+                // waits; a neighbour kept later marks p in the bitmask)
+                const int r0 = resume[p];
+                int settled = r0;   // end of the settled prefix of the slots
+                for (int s0 = r0; s0 < n && !dead && !wait; s0 += 4) {
+                    int q[4];
 #pragma unroll
-                    for (int k = 0; k < 8; k++)
+                    for (int k = 0; k < 4; k++)
                         q[k] = s0 + k < n ? __ldg(nbr + (size_t)(s0 + k) * npos + p) : -1;
 #pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        if (q[k] < 0) continue;
+                    for (int k = 0; k < 4; k++) {
+                        if (q[k] < 0 || dead || wait) continue;
                         const uint32_t hq = khi[q[k]];
-                        if (hq == NMS_NOKEY || !above(q[k], p, hq, hp)) continue;
-                        const uint8_t sq = state[q[k]];
+                        uint8_t sq = NMS_DEAD;   // not above p: settled like a suppressed one
+                        if (hq != NMS_NOKEY && above(q[k], p, hq, hp)) sq = state[q[k]];
                         if (sq == NMS_KEPT) dead = true;
                         else if (sq == NMS_ALIVE) wait = true;
+                        else settled = s0 + k + 1;
                     }
                 }
-                if (dead) state[p] = NMS_DEAD;
-                else if (!wait) state[p] = NMS_KEPT;
-                else undecided = true;
+                if (dead) {
+                    state[p] = NMS_DEAD;
+                } else if (!wait) {
+                    state[p] = NMS_KEPT;
+                    kept = true;
+                } else {
+                    undecided = true;
+                    resume[p] = (uint8_t)settled;
+                }
+            }
+            // each kept candidate marks all its neighbours, the warp's lanes
+            // splitting the slots (neighbours ranked above it are decided
+            // already: it could not be kept while one was undecided)
+            for (unsigned km = __ballot_sync(0xffffffffu, kept); km; km &= km - 1) {
+                const int pk = __shfl_sync(0xffffffffu, p, __ffs(km) - 1);
+                const int nk = __ldg(nbr_cnt + pk);
+                for (int s = lane; s < nk; s += 32) {
+                    const int q = __ldg(nbr + (size_t)s * npos + pk);
+                    atomicOr(const_cast<uint32_t *>(supp) + (q >> 5), 1u << (q & 31));
+                }
             }
             append(undecided, p, cur ^ 1);
         }

@@ -26,7 +26,8 @@
 namespace hogk {
 
 namespace {
-constexpr int NMS_NT = 1024;
+constexpr int NMS_NT = 1024;         // cluster form: threads per CTA
+constexpr int NMS_BATCH_NT = 512;    // one CTA per frame: two CTAs per SM for 640x480 frames
 constexpr int NMS_SMEM_MAX = 200 * 1024;   // dynamic shared memory for keys and states
 
 __device__ __forceinline__ double box_iou(const WinBox &a, const WinBox &b) {
@@ -90,11 +91,11 @@ __global__ void __launch_bounds__(256) nms_geometry_kernel(GeomDesc g, int32_t *
 }
 
 template <bool SM>
-__global__ void __launch_bounds__(NMS_NT) nms_kernel(const FrameDesc *__restrict__ frames,
-                                                     int *flags) {
+__global__ void __launch_bounds__(NMS_BATCH_NT) nms_kernel(const FrameDesc *__restrict__ frames,
+                                                           int *flags) {
     extern __shared__ __align__(16) unsigned char nsm[];
-    __shared__ int sh[NMS_NT / 32 + 4];   // warp sums, total, two list sizes
-    nms_frame<SM, NMS_NT, false>(frames[blockIdx.x], nsm, flags, sh);
+    __shared__ int sh[NMS_BATCH_NT / 32 + 4];   // warp sums, total, two list sizes
+    nms_frame<SM, NMS_BATCH_NT, false>(frames[blockIdx.x], nsm, flags, sh);
 }
 
 __global__ void __launch_bounds__(256) pack_kernel(const hog_det *__restrict__ dets, int per_frame,
@@ -427,7 +428,9 @@ int nms_cluster_size(int nframes, int max_npos, int request) {
         const int want = g_nsm / nframes;
         c = 1;
         while (c * 2 <= want && c * 2 <= cmax) c *= 2;
-        if (nms_ws_bytes(max_npos) > (size_t)NMS_SMEM_MAX && c < 2) c = 2;
+        if ((nms_ws_bytes(max_npos, true) > (size_t)NMS_SMEM_MAX || max_npos > NMS_SMEM_MAX_NPOS) &&
+            c < 2)
+            c = 2;
     }
     while (c < cmax && nms_cluster_ws_bytes(max_npos, c) > (size_t)NMS_SMEM_MAX) c *= 2;
     if (c >= 2 && nms_cluster_ws_bytes(max_npos, c) > (size_t)NMS_SMEM_MAX) return 1;
@@ -460,11 +463,11 @@ cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *
         cfg.numAttrs = 1;
         return cudaLaunchKernelEx(&cfg, nms_cluster_kernel, frames, flags);
     }
-    const size_t ws = nms_ws_bytes(max_npos);
-    if (ws <= (size_t)NMS_SMEM_MAX)
-        nms_kernel<true><<<nframes, NMS_NT, ws, stream>>>(frames, flags);
+    const size_t ws = nms_ws_bytes(max_npos, true);
+    if (ws <= (size_t)NMS_SMEM_MAX && max_npos <= NMS_SMEM_MAX_NPOS)
+        nms_kernel<true><<<nframes, NMS_BATCH_NT, ws, stream>>>(frames, flags);
     else
-        nms_kernel<false><<<nframes, NMS_NT, 0, stream>>>(frames, flags);
+        nms_kernel<false><<<nframes, NMS_BATCH_NT, 0, stream>>>(frames, flags);
     return cudaGetLastError();
 }
 
