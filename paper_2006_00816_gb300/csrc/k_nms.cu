@@ -143,13 +143,15 @@ cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, uint8_t *cnt, i
 // [r*P, r*P + P), P = ceil(npos / C), and keeps the key high words, states
 // and candidate lists of its range in its own shared memory.  A neighbour's
 // key and state are read from the owning CTA's shared memory through the
-// cluster's distributed shared memory (mapa + ld.shared::cluster).  Each CTA
+// cluster's distributed shared memory (mapa + ld.shared::cluster), and a
+// kept candidate marks its neighbours' suppression bits in their owners'
+// shared memory with remote atomics (atom.shared::cluster.or).  Each CTA
 // only writes the states of its own positions; the rounds are the same as
 // in the one-CTA form, with a cluster barrier (release/acquire) closing each
 // round, after which every CTA reads the cluster's count of undecided
-// candidates from CTA 0.  Within a round a remote state may be read stale,
-// which can only make a candidate wait one more round: the kept set is the
-// same for every C.  This gives one frame the shared memory and L2
+// candidates from CTA 0.  Within a round a remote state or bit may be read
+// stale, which can only make a candidate wait one more round: the kept set
+// is the same for every C.  This gives one frame the shared memory and L2
 // bandwidth of C SMs (a 1280x1024 frame has about 55K positions, 715 KB of
 // state: more than one SM holds), and cuts the latency of small batches.
 namespace {
@@ -185,6 +187,9 @@ __device__ __forceinline__ uint32_t cl_ld_u8(uint32_t addr) {
     asm volatile("ld.shared::cluster.u8 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
     return v;
 }
+__device__ __forceinline__ void cl_or_u32(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
 __device__ __forceinline__ void cl_st_u32(uint32_t addr, uint32_t v) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
@@ -195,8 +200,10 @@ __device__ __forceinline__ void cl_sync() {
 }  // namespace
 
 constexpr int NMS_MAX_CLUSTER = 16;
+// per CTA: key high words, two lists (4 B each), the suppression bits, and
+// state and resume slot (1 B each) of its owned positions
 __host__ __device__ constexpr size_t nms_cluster_ws_bytes(int npos, int c) {
-    return (size_t)((npos + c - 1) / c) * 13 + 64;
+    return (size_t)((npos + c - 1) / c) * 14 + 4 * (size_t)(((npos + c - 1) / c + 31) / 32) + 64;
 }
 
 __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc *__restrict__ frames,
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
     __shared__ int sh[NMS_NT / 32 + 4];
     __shared__ int s_cnt[2][NMS_MAX_CLUSTER];     // read in CTA 0: undecided per CTA
     __shared__ int s_kept[NMS_MAX_CLUSTER];       // read in CTA 0: kept per CTA
-    __shared__ uint32_t s_rkhi[NMS_MAX_CLUSTER], s_rstate[NMS_MAX_CLUSTER];
+    __shared__ uint32_t s_rkhi[NMS_MAX_CLUSTER], s_rstate[NMS_MAX_CLUSTER], s_rsupp[NMS_MAX_CLUSTER];
     __shared__ int s_total;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int C = (int)cl_size(), rank = (int)cl_rank();
@@ -216,12 +223,23 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
     uint32_t *khi = reinterpret_cast<uint32_t *>(nsm);                       // [P]
     int32_t *list[2] = {reinterpret_cast<int32_t *>(nsm) + P,                  // local indices
                         reinterpret_cast<int32_t *>(nsm) + 2 * (size_t)P};
-    volatile uint8_t *state = nsm + (size_t)P * 12;
+    const int PW = (P + 31) / 32;
+    volatile uint32_t *supp = reinterpret_cast<volatile uint32_t *>(nsm + (size_t)P * 12);   // bits [P]
+    volatile uint8_t *state = nsm + (size_t)P * 12 + 4 * (size_t)PW;                        // [P]
+    uint8_t *resume = nsm + (size_t)P * 13 + 4 * (size_t)PW;                                 // [P]
     const uint64_t *gkeys = fd.keys;
     const int32_t *__restrict__ nbr = fd.nbr;
     const uint8_t *__restrict__ nbr_cnt = fd.nbr_cnt;
     int *s_n = sh + NMS_NT / 32 + 1;
     const float invP = P > 0 ? 1.0f / (float)P : 0.f;
+    // owner CTA of position q (float estimate, corrected)
+    auto owner = [&](int q) -> int {
+        int o = __float2int_rz((float)q * invP);
+        const int b = o * P;
+        if (b > q) o--;
+        else if (q - b >= P) o++;
+        return o;
+    };
 
     auto append = [&](bool flag, int i, int which) {
         const unsigned m = __ballot_sync(0xffffffffu, flag);
@@ -235,8 +253,10 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
     if (t < C) {
         s_rkhi[t] = cl_map(khi, t);
         s_rstate[t] = cl_map((const void *)state, t);
+        s_rsupp[t] = cl_map((const void *)supp, t);
     }
     if (t == 0) { s_n[0] = 0; s_n[1] = 0; }
+    for (int k = t; k < PW; k += NMS_NT) supp[k] = 0u;
     __syncthreads();
     for (int i0 = 0; i0 < nmine; i0 += NMS_NT) {
         const int i = i0 + t;
@@ -245,49 +265,68 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
             h = (uint32_t)(__ldg(gkeys + lo + i) >> 32);
             khi[i] = h;
             state[i] = h != NMS_NOKEY ? NMS_ALIVE : NMS_DEAD;
+            resume[i] = 0;
         }
         append(h != NMS_NOKEY, i, 0);
     }
-    cl_sync();   // every CTA's keys and states are initialised
+    cl_sync();   // every CTA's keys, states and bits are initialised
 
     int cur = 0, round = 0;
     for (; round <= npos; round++) {
         const int n_cur = s_n[cur];
         for (int i0 = 0; i0 < n_cur; i0 += NMS_NT) {
             const int i = i0 + t;
-            bool undecided = false;
-            int li = -1;
+            bool undecided = false, kept = false;
+            int li = -1, p = -1;
             if (i < n_cur) {
                 li = list[cur][i];
-                const int p = lo + li;
+                p = lo + li;
                 const uint32_t hp = khi[li];
                 const int n = __ldg(nbr_cnt + p);
-                bool dead = false, wait = false;
-                for (int s0 = 0; s0 < n && !dead; s0 += 8) {
-                    int q[8];
+                bool dead = (supp[li >> 5] >> (li & 31)) & 1u, wait = false;
+                const int r0 = resume[li];
+                int settled = r0;
+                for (int s0 = r0; s0 < n && !dead && !wait; s0 += 4) {
+                    int q[4];
 #pragma unroll
-                    for (int k = 0; k < 8; k++)
+                    for (int k = 0; k < 4; k++)
                         q[k] = s0 + k < n ? __ldg(nbr + (size_t)(s0 + k) * npos + p) : -1;
 #pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        if (q[k] < 0) continue;
-                        // owner CTA and local index of q (float estimate, corrected)
-                        int o = __float2int_rz((float)q[k] * invP);
-                        int b = o * P;
-                        if (b > q[k]) { o--; b -= P; }
-                        else if (q[k] - b >= P) { o++; b += P; }
-                        const int lq = q[k] - b;
+                    for (int k = 0; k < 4; k++) {
+                        if (q[k] < 0 || dead || wait) continue;
+                        const int o = owner(q[k]);
+                        const int lq = q[k] - o * P;
                         const uint32_t hq = cl_ld_u32(s_rkhi[o] + 4u * (uint32_t)lq);
-                        if (hq == NMS_NOKEY) continue;
-                        if (hq != hp ? !(hq < hp) : !(__ldg(gkeys + q[k]) < __ldg(gkeys + p))) continue;
-                        const uint32_t sq = cl_ld_u8(s_rstate[o] + (uint32_t)lq);
+                        uint32_t sq = NMS_DEAD;   // not above p: settled like a suppressed one
+                        if (hq != NMS_NOKEY &&
+                            (hq != hp ? hq < hp : __ldg(gkeys + q[k]) < __ldg(gkeys + p)))
+                            sq = cl_ld_u8(s_rstate[o] + (uint32_t)lq);
                         if (sq == NMS_KEPT) dead = true;
                         else if (sq == NMS_ALIVE) wait = true;
+                        else settled = s0 + k + 1;
                     }
                 }
-                if (dead) state[li] = NMS_DEAD;
-                else if (!wait) state[li] = NMS_KEPT;
-                else undecided = true;
+                if (dead) {
+                    state[li] = NMS_DEAD;
+                } else if (!wait) {
+                    state[li] = NMS_KEPT;
+                    kept = true;
+                } else {
+                    undecided = true;
+                    resume[li] = (uint8_t)settled;
+                }
+            }
+            // each kept candidate marks all its neighbours' bits in their
+            // owners' shared memory, the warp's lanes splitting the slots
+            for (unsigned km = __ballot_sync(0xffffffffu, kept); km; km &= km - 1) {
+                const int pk = __shfl_sync(0xffffffffu, p, __ffs(km) - 1);
+                const int nk = __ldg(nbr_cnt + pk);
+                for (int s = lane; s < nk; s += 32) {
+                    const int q = __ldg(nbr + (size_t)s * npos + pk);
+                    const int o = owner(q);
+                    const int lq = q - o * P;
+                    cl_or_u32(s_rsupp[o] + 4u * (uint32_t)(lq >> 5), 1u << (lq & 31));
+                }
             }
             append(undecided, li, cur ^ 1);
         }
