@@ -318,6 +318,8 @@ int get_geometry(hog_ctx *ctx, int W, int H, cudaStream_t stream, Geometry **out
         gd.iou = (double)ctx->p.nms_iou;
         for (int l = 0; l < g->nlev; l++) {
             gd.lev_w[l] = g->lw[l]; gd.lev_h[l] = g->lh[l];
+            gd.lev_rx[l] = (double)W / (double)g->lw[l];
+            gd.lev_ry[l] = (double)H / (double)g->lh[l];
             gd.lev_nu[l] = g->nu[l]; gd.lev_nv[l] = g->nv[l];
             gd.lev_pos[l] = g->pos_off[l];
         }
@@ -535,6 +537,8 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         fd.frame = frame_index;
         for (int l = 0; l < g.nlev; l++) {
             fd.lev_w[l] = g.lw[l]; fd.lev_h[l] = g.lh[l];
+            fd.lev_rx[l] = (double)g.W / (double)g.lw[l];
+            fd.lev_ry[l] = (double)g.H / (double)g.lh[l];
             fd.lev_nu[l] = g.nu[l]; fd.lev_nv[l] = g.nv[l];
             fd.lev_pos[l] = g.pos_off[l];
         }

@@ -117,6 +117,7 @@ struct FrameDesc {
     int32_t lev_w[MAX_LEVELS], lev_h[MAX_LEVELS];
     int32_t lev_nu[MAX_LEVELS], lev_nv[MAX_LEVELS];
     int32_t lev_pos[MAX_LEVELS + 1];
+    double lev_rx[MAX_LEVELS], lev_ry[MAX_LEVELS];   // W/Wl, H/Hl (FP64, host-divided)
     const uint64_t *keys;             // [npos]
     uint32_t *ws;                     // suppression workspace (global mode), 14 B per position
     const int32_t *nbr;               // [MAXN][npos] neighbour lists, slot-major
@@ -139,6 +140,7 @@ struct GeomDesc {
     int32_t lev_w[MAX_LEVELS], lev_h[MAX_LEVELS];
     int32_t lev_nu[MAX_LEVELS], lev_nv[MAX_LEVELS];
     int32_t lev_pos[MAX_LEVELS + 1];
+    double lev_rx[MAX_LEVELS], lev_ry[MAX_LEVELS];   // W/Wl, H/Hl (FP64, host-divided)
     uint32_t pair_mask[MAX_LEVELS];   // bit m set: levels (l, m) can exceed the IoU
 };
 

@@ -560,9 +560,11 @@ struct WinBox {
     double x, y, w, h;
 };
 
-__device__ __forceinline__ WinBox window_box(int W0, int H0, int Wl, int Hl, int u, int v) {
-    const double rx = __ddiv_rn((double)W0, (double)Wl);
-    const double ry = __ddiv_rn((double)H0, (double)Hl);
+// Box of window (u, v) of a level in frame pixels: (8v, 8u, 80, 80) scaled
+// by rx = W0/Wl and ry = H0/Hl.  The ratios are IEEE double quotients taken
+// once per level on the host (FP64 division is slow on this GPU); every
+// product is rounded once, as in the oracle.
+__device__ __forceinline__ WinBox window_box(double rx, double ry, int u, int v) {
     WinBox b;
     b.x = __dmul_rn((double)(CELL * v), rx);
     b.y = __dmul_rn((double)(CELL * u), ry);
@@ -645,23 +647,25 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
         __syncthreads();
         for (int i0 = 0; i0 < n_cur; i0 += NT) {     // whole warps iterate together
             const int i = i0 + t;
-            bool undecided = false, kept = false;
-            int p = -1;
+            bool undecided = false, kept = false, dead = false, wait = false;
+            int p = -1, n = 0, settled = 0;
+            uint32_t hp = 0;
             if (i < n_cur) {
                 p = list[cur][i];
-                const uint32_t hp = khi[p];
-                const int n = __ldg(nbr_cnt + p);
-                bool dead = (supp[p >> 5] >> (p & 31)) & 1u, wait = false;
+                n = __ldg(nbr_cnt + p);
+                hp = khi[p];
+                dead = (supp[p >> 5] >> (p & 31)) & 1u;
                 // scan the unsettled slots up to the first higher-ranked
                 // neighbour that is kept (p is suppressed) or undecided (p
-                // waits; a neighbour kept later marks p in the bitmask)
+                // waits; a neighbour kept later marks p in the bitmask):
+                // four slots here, the rest by the whole warp below
                 const int r0 = resume[p];
-                int settled = r0;   // end of the settled prefix of the slots
-                for (int s0 = r0; s0 < n && !dead && !wait; s0 += 4) {
+                settled = r0;   // end of the settled prefix of the slots
+                if (!dead) {
                     int q[4];
 #pragma unroll
                     for (int k = 0; k < 4; k++)
-                        q[k] = s0 + k < n ? __ldg(nbr + (size_t)(s0 + k) * npos + p) : -1;
+                        q[k] = r0 + k < n ? __ldg(nbr + (size_t)(r0 + k) * npos + p) : -1;
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         if (q[k] < 0 || dead || wait) continue;
@@ -670,9 +674,45 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
                         if (hq != NMS_NOKEY && above(q[k], p, hq, hp)) sq = state[q[k]];
                         if (sq == NMS_KEPT) dead = true;
                         else if (sq == NMS_ALIVE) wait = true;
-                        else settled = s0 + k + 1;
+                        else settled = r0 + k + 1;
                     }
                 }
+            }
+            // candidates with slots left: the warp scans them one at a time,
+            // a lane per slot, and takes the first unsettled slot in order
+            for (unsigned um = __ballot_sync(0xffffffffu, p >= 0 && !dead && !wait && settled < n); um;
+                 um &= um - 1) {
+                const int src = __ffs(um) - 1;
+                const int pp = __shfl_sync(0xffffffffu, p, src);
+                const int nn = __shfl_sync(0xffffffffu, n, src);
+                const uint32_t hpp = __shfl_sync(0xffffffffu, hp, src);
+                int res = 0, at = nn;   // 0: all settled, 1: kept neighbour, 2: undecided one
+                for (int sb = __shfl_sync(0xffffffffu, settled, src); sb < nn; sb += 32) {
+                    const int sl = sb + lane;
+                    uint32_t cls = 0;
+                    if (sl < nn) {
+                        const int q = __ldg(nbr + (size_t)sl * npos + pp);
+                        const uint32_t hq = khi[q];
+                        if (hq != NMS_NOKEY && above(q, pp, hq, hpp)) {
+                            const uint8_t sq = state[q];
+                            cls = sq == NMS_KEPT ? 1u : (sq == NMS_ALIVE ? 2u : 0u);
+                        }
+                    }
+                    const unsigned hit = __ballot_sync(0xffffffffu, cls != 0);
+                    if (hit) {
+                        const int f = __ffs(hit) - 1;
+                        res = (int)__shfl_sync(0xffffffffu, cls, f);
+                        at = sb + f;
+                        break;
+                    }
+                }
+                if (lane == src) {
+                    if (res == 1) dead = true;
+                    else if (res == 2) wait = true;
+                    settled = at;
+                }
+            }
+            if (p >= 0) {
                 if (dead) {
                     state[p] = NMS_DEAD;
                 } else if (!wait) {
@@ -733,7 +773,7 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
             const uint64_t k = ld_in<COH>(gkeys + p);
             const int l = key_level(k);
             const int u = key_u(k), v = key_v(k);
-            const WinBox b = window_box(fd.W, fd.H, fd.lev_w[l], fd.lev_h[l], u, v);
+            const WinBox b = window_box(fd.lev_rx[l], fd.lev_ry[l], u, v);
             hog_det det;
             det.frame = fd.frame;
             det.level = l;

@@ -58,24 +58,27 @@ __global__ void __launch_bounds__(256) nms_geometry_kernel(GeomDesc g, int32_t *
     const int l = level_of(g.lev_pos, g.nlev, p);
     const int idx = p - g.lev_pos[l];
     const int u = idx / g.lev_nv[l], v = idx - (idx / g.lev_nv[l]) * g.lev_nv[l];
-    const WinBox bp = window_box(g.W, g.H, g.lev_w[l], g.lev_h[l], u, v);
+    const WinBox bp = window_box(g.lev_rx[l], g.lev_ry[l], u, v);
     int n = 0;
     for (int m = 0; m < g.nlev; m++) {
         if (!((g.pair_mask[l] >> m) & 1u)) continue;
         if (g.lev_nu[m] <= 0 || g.lev_nv[m] <= 0) continue;
-        const double sx = __dmul_rn((double)CELL, __ddiv_rn((double)g.W, (double)g.lev_w[m]));
-        const double sy = __dmul_rn((double)CELL, __ddiv_rn((double)g.H, (double)g.lev_h[m]));
-        const double wm = (double)(CELL * WIN) / ((double)g.lev_w[m]) * (double)g.W;
-        const double hm = (double)(CELL * WIN) / ((double)g.lev_h[m]) * (double)g.H;
-        int vlo = (int)floor((bp.x - wm) / sx) - 1, vhi = (int)ceil((bp.x + bp.w) / sx) + 1;
-        int ulo = (int)floor((bp.y - hm) / sy) - 1, uhi = (int)ceil((bp.y + bp.h) / sy) + 1;
+        // candidate range on level m (one cell of slack on each side; the
+        // IoU test below is exact)
+        const double sx = __dmul_rn((double)CELL, g.lev_rx[m]), sy = __dmul_rn((double)CELL, g.lev_ry[m]);
+        const double wm = (double)(CELL * WIN) * g.lev_rx[m], hm = (double)(CELL * WIN) * g.lev_ry[m];
+        // reciprocals in FP32: a relative error of 1e-7 moves a bound by far
+        // less than the slack
+        const double isx = (double)(1.0f / (float)sx), isy = (double)(1.0f / (float)sy);
+        int vlo = (int)floor((bp.x - wm) * isx) - 1, vhi = (int)ceil((bp.x + bp.w) * isx) + 1;
+        int ulo = (int)floor((bp.y - hm) * isy) - 1, uhi = (int)ceil((bp.y + bp.h) * isy) + 1;
         vlo = max(vlo, 0); ulo = max(ulo, 0);
         vhi = min(vhi, g.lev_nv[m] - 1); uhi = min(uhi, g.lev_nu[m] - 1);
         for (int uu = ulo; uu <= uhi; uu++) {
             for (int vv = vlo; vv <= vhi; vv++) {
                 const int q = g.lev_pos[m] + uu * g.lev_nv[m] + vv;
                 if (q == p) continue;
-                const WinBox bq = window_box(g.W, g.H, g.lev_w[m], g.lev_h[m], uu, vv);
+                const WinBox bq = window_box(g.lev_rx[m], g.lev_ry[m], uu, vv);
                 if (box_iou(bq, bp) > g.iou) {
                     if (n < MAXN) nbr[(size_t)n * g.npos + p] = q;   // slot-major
                     n++;
@@ -392,7 +395,7 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
             const uint64_t k = __ldg(gkeys + lo + i);
             const int l = key_level(k);
             const int u = key_u(k), v = key_v(k);
-            const WinBox b = window_box(fd.W, fd.H, fd.lev_w[l], fd.lev_h[l], u, v);
+            const WinBox b = window_box(fd.lev_rx[l], fd.lev_ry[l], u, v);
             hog_det det;
             det.frame = fd.frame;
             det.level = l;
