@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--serve-warmup", type=float, default=1.0)
     ap.add_argument("--mixed-frames", type=int, default=256)
     ap.add_argument("--backward-reps", type=int, default=20)
+    ap.add_argument("--resolution-reps", type=int, default=5)
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner record to load (or write): a profiled run then uses the "
                          "choice measured without the profiler")
@@ -414,6 +415,63 @@ def run_mixed(hog, synth, W, n, reps, dev, barrier):
             "megapixels_per_s": px / batched_s / 1e6}
 
 
+# The paper's scalability study (Section 6.6, Table 10): HOG face-detection
+# time per frame on a Titan X, 16 frames per launch, largest scale skipped.
+PAPER_TABLE10_MS = {"640x480": 0.333, "1280x960": 0.734, "2560x1920": 1.436}
+
+
+def run_resolution(hog, synth, W, reps, dev, barrier, frames_640=None):
+    """Resolution scaling (the paper's Table 10 sizes): for 640x480,
+    1280x960 and 2560x1920 eyeblink frames (10, 14 and 18 levels), the
+    batched call (autotuned, graphs) in frames/s and ms per frame, and the
+    per-frame call's p50/p99 latency.  Large frames repeat a few distinct
+    seeded frames (generation on the host is slow at 2560x1920)."""
+    import torch
+    out = {}
+    plan = [((640, 480), 256, 256), ((1280, 960), 64, 16), ((2560, 1920), 16, 4)]
+    for (w, h), n, uniq in plan:
+        if (w, h) == (640, 480) and frames_640 is not None:
+            frames = frames_640[:n]
+        else:
+            base = [torch.from_numpy(synth.eyeblink_frame(i, w, h, config=6)).to(dev)
+                    for i in range(uniq)]
+            frames = [base[i % uniq] for i in range(n)]
+        det = hog.Detector(W, max_w=w, max_h=h, max_batch=n)
+        mode, _ = det.autotune(frames)
+        out_np, _keep = hog.pinned_dets(n * (16384 if w > 1280 else 4096))
+        for _ in range(3):
+            det.detect(frames, out=out_np, batched=True)
+        barrier()
+        t0 = time.perf_counter()
+        kept = 0
+        for _ in range(reps):
+            _, c = det.detect(frames, out=out_np, batched=True)
+            kept += int(c.sum())
+        barrier()
+        batched_s = (time.perf_counter() - t0) / reps
+        det.close()
+        plain = hog.Detector(W, max_w=w, max_h=h, max_batch=1)
+        for f in frames[:4]:
+            plain.detect([f], out=out_np)
+        barrier()
+        lat = []
+        for f in frames[:min(n, 32)]:
+            t1 = time.perf_counter()
+            plain.detect([f], out=out_np)
+            lat.append((time.perf_counter() - t1) * 1e3)
+        plain.close()
+        key = "%dx%d" % (w, h)
+        out[key] = {"levels": len(hog.level_geometry(w, h)), "batch": n,
+                    "batched_frames_per_s": n / batched_s,
+                    "batched_ms_per_frame": batched_s * 1e3 / n,
+                    "plain_p50_ms": statistics.median(lat),
+                    "plain_p99_ms": float(np.percentile(lat, 99)),
+                    "kept_per_frame": kept / (reps * n),
+                    "mode": "fused" if mode == 1 else "per-stage",
+                    "paper_ms_per_frame": PAPER_TABLE10_MS[key]}
+    return out
+
+
 def run_backward(hog, synth, reps, dev, barrier):
     """Adjoint: hinge loss on the best window of one filter over 64 seeded
     128x128 crops; time per hog_backward call (loss, dW and dI)."""
@@ -589,6 +647,8 @@ def main():
         if args.mixed_frames > 0 else None
     backward = run_backward(hog, synth, args.backward_reps, dev, barrier) \
         if args.backward_reps > 0 else None
+    resolution = run_resolution(hog, synth, W, args.resolution_reps, dev, barrier, frames) \
+        if args.resolution_reps > 0 else None
 
     # ---- serving: continuous batching over 8 camera streams (rank 0 of a
     # replica job serves its own GPU like every other rank)
@@ -636,6 +696,7 @@ def main():
                       "stage_ms_per_frame": plain_stages},
             "mixed_batch": mixed,
             "backward": backward,
+            "resolution_scaling": resolution,
             "serving": serving,
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
