@@ -74,6 +74,12 @@ def lib():
             "hgo_box": (None, [i, i, i, i, i, i, P(Det)]),
             "hgo_nms": (i, [P(Det), i, d, i32p]),
             "hgo_pyramid_u8": (i, [u8p, i, i, i, i, u8p, sz]),
+            "hgo_downscale_direct_u8": (None, [u8p, i, i, i, i, u8p, i, i, i]),
+            "hgo_pyramid_u8_ex": (i, [u8p, i, i, i, i, i, i, u8p, sz]),
+            "hgo_frame_features_ex": (i, [u8p, i, i, i, i, i, i, d, d, i, dp, sz]),
+            "hgo_frame_scores_ex": (i, [u8p, i, i, i, i, i, i, d, d, dp, i, dp, sz]),
+            "hgo_frame_candidates_ex": (i, [u8p, i, i, i, i, i, i, d, d, d, dp, i, P(Det), i]),
+            "hgo_detect_ex": (i, [u8p, i, i, i, i, i, i, d, d, d, d, dp, i, P(Det), i, i32p]),
             "hgo_pyramid_f64": (i, [dp, i, i, i, dp, sz]),
             "hgo_frame_features": (i, [u8p, i, i, i, i, d, d, i, dp, sz]),
             "hgo_frame_scores": (i, [u8p, i, i, i, i, d, d, dp, i, dp, sz]),
@@ -155,14 +161,27 @@ def correlate(feat, filt):
     return out
 
 
-def pyramid_u8(frame, min_size=80):
-    """List of uint8 levels of the exact-integer pyramid."""
+def downscale_direct_u8(img, s, dw, dh):
+    """Direct-to-size downscale of a level-0 image to (dw, dh) with the ratio
+    (6/5)^s (Section 6.6, future work); s = 1 is the 5/6 step."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    h, w = img.shape
+    out = np.zeros((dh, dw), np.uint8)
+    lib().hgo_downscale_direct_u8(_p(img, C.c_uint8), w, h, w, int(s), _p(out, C.c_uint8),
+                                  dw, dh, dw)
+    return out
+
+
+def pyramid_u8(frame, min_size=80, skip_levels=0, direct=False):
+    """List of uint8 levels of the exact-integer pyramid.  direct=True with
+    skip_levels = s >= 2: level s straight from level 0, levels 1..s-1 zero."""
     frame = np.ascontiguousarray(frame, dtype=np.uint8)
     h, w = frame.shape
     sizes = level_sizes(w, h, min_size)
     cap = sum(a * b for a, b in sizes)
     buf = np.zeros(max(cap, 1), np.uint8)
-    lib().hgo_pyramid_u8(_p(frame, C.c_uint8), w, h, w, min_size, _p(buf, C.c_uint8), cap)
+    lib().hgo_pyramid_u8_ex(_p(frame, C.c_uint8), w, h, w, min_size, int(skip_levels),
+                            int(bool(direct)), _p(buf, C.c_uint8), cap)
     out, off = [], 0
     for lw, lh in sizes:
         out.append(buf[off:off + lw * lh].reshape(lh, lw))
@@ -184,15 +203,17 @@ def pyramid_f64(img, min_size=80):
     return out
 
 
-def frame_features(frame, min_size=80, eps=EPS, tau=TAU, float_mode=False):
+def frame_features(frame, min_size=80, eps=EPS, tau=TAU, float_mode=False, skip_levels=0,
+                   direct=False):
     """List of per-level feature maps [cy][cx][31] (float64)."""
     frame = np.ascontiguousarray(frame, dtype=np.uint8)
     h, w = frame.shape
     sizes = level_sizes(w, h, min_size)
     cap = sum((a // CELL) * (b // CELL) for a, b in sizes) * NFEAT
     buf = np.zeros(max(cap, 1), np.float64)
-    lib().hgo_frame_features(_p(frame, C.c_uint8), w, h, w, min_size, eps, tau,
-                             int(bool(float_mode)), _p(buf, C.c_double), cap)
+    lib().hgo_frame_features_ex(_p(frame, C.c_uint8), w, h, w, min_size, int(skip_levels),
+                                int(bool(direct)), eps, tau, int(bool(float_mode)),
+                                _p(buf, C.c_double), cap)
     out, off = [], 0
     for lw, lh in sizes:
         n = (lh // CELL) * (lw // CELL) * NFEAT
@@ -201,7 +222,7 @@ def frame_features(frame, min_size=80, eps=EPS, tau=TAU, float_mode=False):
     return out
 
 
-def frame_scores(frame, filt, min_size=80, eps=EPS, tau=TAU):
+def frame_scores(frame, filt, min_size=80, eps=EPS, tau=TAU, skip_levels=0, direct=False):
     """List of per-level score maps [F][cy-9][cx-9] (float64)."""
     frame = np.ascontiguousarray(frame, dtype=np.uint8)
     filt = np.ascontiguousarray(filt, dtype=np.float64)
@@ -211,8 +232,9 @@ def frame_scores(frame, filt, min_size=80, eps=EPS, tau=TAU):
     dims = [((b // CELL) - WIN + 1, (a // CELL) - WIN + 1) for a, b in sizes]
     cap = sum(nf * nu * nv for nu, nv in dims)
     buf = np.zeros(max(cap, 1), np.float64)
-    lib().hgo_frame_scores(_p(frame, C.c_uint8), w, h, w, min_size, eps, tau,
-                           _p(filt, C.c_double), nf, _p(buf, C.c_double), cap)
+    lib().hgo_frame_scores_ex(_p(frame, C.c_uint8), w, h, w, min_size, int(skip_levels),
+                              int(bool(direct)), eps, tau, _p(filt, C.c_double), nf,
+                              _p(buf, C.c_double), cap)
     out, off = [], 0
     for nu, nv in dims:
         out.append(buf[off:off + nf * nu * nv].reshape(nf, nu, nv))
@@ -221,7 +243,7 @@ def frame_scores(frame, filt, min_size=80, eps=EPS, tau=TAU):
 
 
 def frame_candidates(frame, filt, min_size=80, skip_levels=0, eps=EPS, tau=TAU,
-                     threshold=0.0):
+                     threshold=0.0, direct=False):
     frame = np.ascontiguousarray(frame, dtype=np.uint8)
     filt = np.ascontiguousarray(filt, dtype=np.float64)
     h, w = frame.shape
@@ -229,9 +251,9 @@ def frame_candidates(frame, filt, min_size=80, skip_levels=0, eps=EPS, tau=TAU,
     cap = sum(nf * max(b // CELL - WIN + 1, 0) * max(a // CELL - WIN + 1, 0)
               for a, b in level_sizes(w, h, min_size))
     out = np.zeros(max(cap, 1), DET_DTYPE)
-    n = lib().hgo_frame_candidates(_p(frame, C.c_uint8), w, h, w, min_size, skip_levels,
-                                   eps, tau, threshold, _p(filt, C.c_double), nf,
-                                   _p(out, Det), cap)
+    n = lib().hgo_frame_candidates_ex(_p(frame, C.c_uint8), w, h, w, min_size, skip_levels,
+                                      int(bool(direct)), eps, tau, threshold,
+                                      _p(filt, C.c_double), nf, _p(out, Det), cap)
     return out[:n].copy()
 
 
@@ -257,7 +279,7 @@ def iou(a, b):
 
 
 def detect(frame, filt, min_size=80, skip_levels=0, eps=EPS, tau=TAU, threshold=0.0,
-           nms_iou=0.5):
+           nms_iou=0.5, direct=False):
     """Kept detections of one frame in rank order, and the candidate count."""
     frame = np.ascontiguousarray(frame, dtype=np.uint8)
     filt = np.ascontiguousarray(filt, dtype=np.float64)
@@ -267,9 +289,9 @@ def detect(frame, filt, min_size=80, skip_levels=0, eps=EPS, tau=TAU, threshold=
               for a, b in level_sizes(w, h, min_size))
     out = np.zeros(max(cap, 1), DET_DTYPE)
     ncand = C.c_int32(0)
-    k = lib().hgo_detect(_p(frame, C.c_uint8), w, h, w, min_size, skip_levels, eps, tau,
-                         threshold, nms_iou, _p(filt, C.c_double), nf, _p(out, Det), cap,
-                         C.byref(ncand))
+    k = lib().hgo_detect_ex(_p(frame, C.c_uint8), w, h, w, min_size, skip_levels,
+                            int(bool(direct)), eps, tau, threshold, nms_iou,
+                            _p(filt, C.c_double), nf, _p(out, Det), cap, C.byref(ncand))
     return out[:k].copy(), ncand.value
 
 

@@ -40,6 +40,11 @@
  *   R8 boxes (8v, 8u, 80, 80) in level pixels mapped to the frame by W0/Wl,
  *      H0/Hl; greedy NMS over all levels and filters of a frame in order
  *      (score desc, level, filter, u, v); suppress when IoU > nms_iou.
+ *   R12 direct-to-size (Section 6.6, future work), with skip_levels = s >= 2:
+ *      level s is resampled from level 0 in one step with the ratio (6/5)^s
+ *      under the R2 rule generalised (weights in units of 1/(2*5^s)); the
+ *      levels between are not computed; the later levels follow in 5/6
+ *      steps.  For s = 1 the one step is the 5/6 step itself.
  * Built with -ffp-contract=off so that results are identical on x86-64 and
  * aarch64 hosts.
  */
@@ -316,6 +321,66 @@ int hgo_nms(hgo_det *cands, int n, double iou_thr, int32_t *keep)
 /* Whole-frame helpers used by the tests.                                    */
 
 /* uint8 pyramid of all kept levels, concatenated tightly ([h_l][w_l] each). */
+/* Direct-to-size first downscale (Section 6.6, future work: scale the
+ * frame straight to the largest level that is needed, then continue in 5/6
+ * steps).  Level s is resampled from level 0 in one step with the ratio
+ * (6/5)^s per axis, pixel-centre aligned: source coordinate
+ *   (x + 1/2) (6/5)^s - 1/2 = ((2x + 1) 6^s - 5^s) / (2 * 5^s),
+ * bilinear with exact weights in units of 1 / (2 * 5^s), rounded half up to
+ * uint8.  For s = 1 this is the 5/6 step itself.  The output is the
+ * (w_s, h_s) of the level-size rule, which never exceeds (5/6)^s of the
+ * frame, so the right and lower neighbours always exist.  s <= 8.          */
+void hgo_downscale_direct_u8(const uint8_t *src, int w, int h, int sstride, int s,
+                             uint8_t *dst, int dw, int dh, int dstride)
+{
+    int64_t p6 = 1, p5 = 1;
+    for (int k = 0; k < s; k++) { p6 *= 6; p5 *= 5; }
+    const int64_t D = 2 * p5;           /* weight denominator per axis */
+    (void)w; (void)h;
+    for (int y = 0; y < dh; y++) {
+        int64_t Y = (2 * (int64_t)y + 1) * p6 - p5;
+        int64_t y0 = Y / D, fy = Y % D;
+        for (int x = 0; x < dw; x++) {
+            int64_t X = (2 * (int64_t)x + 1) * p6 - p5;
+            int64_t x0 = X / D, fx = X % D;
+            int64_t p00 = src[y0 * sstride + x0];
+            int64_t p10 = src[y0 * sstride + x0 + 1];
+            int64_t p01 = src[(y0 + 1) * sstride + x0];
+            int64_t p11 = src[(y0 + 1) * sstride + x0 + 1];
+            int64_t acc = (D - fx) * (D - fy) * p00 + fx * (D - fy) * p10
+                        + (D - fx) * fy * p01 + fx * fy * p11;
+            dst[(size_t)y * dstride + x] = (uint8_t)((acc + D * D / 2) / (D * D));
+        }
+    }
+}
+
+/* Pyramid with the first `skip_levels` levels skipped for detection.  With
+ * direct != 0 and skip_levels = s >= 2, level s comes from level 0 by
+ * hgo_downscale_direct_u8 and levels 1 .. s-1 are not computed (left 0);
+ * the levels after s follow in 5/6 steps as usual.                          */
+int hgo_pyramid_u8_ex(const uint8_t *frame, int w, int h, int stride, int min_size,
+                      int skip_levels, int direct, uint8_t *out, size_t cap)
+{
+    int ws[64], hs[64];
+    int L = hgo_level_sizes(w, h, min_size, ws, hs, 64);
+    if (L > 64) return -1;
+    size_t need = 0, offs[64];
+    for (int l = 0; l < L; l++) { offs[l] = need; need += (size_t)ws[l] * hs[l]; }
+    if (need > cap) return -2;
+    if (direct && skip_levels > 8) return -3;
+    if (L == 0) return 0;
+    memset(out, 0, need);
+    for (int y = 0; y < h; y++) memcpy(out + (size_t)y * w, frame + (size_t)y * stride, (size_t)w);
+    for (int l = 1; l < L; l++) {
+        if (direct && skip_levels >= 2 && l < skip_levels) continue;
+        if (direct && skip_levels >= 2 && l == skip_levels)
+            hgo_downscale_direct_u8(out, ws[0], hs[0], ws[0], l, out + offs[l], ws[l], hs[l], ws[l]);
+        else
+            hgo_downscale_u8(out + offs[l - 1], ws[l - 1], hs[l - 1], ws[l - 1], out + offs[l], ws[l]);
+    }
+    return L;
+}
+
 int hgo_pyramid_u8(const uint8_t *frame, int w, int h, int stride, int min_size,
                    uint8_t *out, size_t cap)
 {
@@ -356,9 +421,23 @@ int hgo_pyramid_f64(const double *img, int w, int h, int min_size, double *out, 
 
 /* Features of every level, concatenated ([cy_l][cx_l][31] each).  The
  * pyramid is uint8 (float_mode 0) or real-valued (float_mode 1).           */
+int hgo_frame_features_ex(const uint8_t *frame, int w, int h, int stride, int min_size,
+                          int skip_levels, int direct, double eps, double tau, int float_mode,
+                          double *feat, size_t cap);
+
 int hgo_frame_features(const uint8_t *frame, int w, int h, int stride, int min_size,
                        double eps, double tau, int float_mode,
                        double *feat, size_t cap)
+{
+    return hgo_frame_features_ex(frame, w, h, stride, min_size, 0, 0, eps, tau, float_mode,
+                                 feat, cap);
+}
+
+/* Features of every level; with direct pyramids (hgo_pyramid_u8_ex) the
+ * levels that are not computed get zero features.                         */
+int hgo_frame_features_ex(const uint8_t *frame, int w, int h, int stride, int min_size,
+                          int skip_levels, int direct, double eps, double tau, int float_mode,
+                          double *feat, size_t cap)
 {
     int ws[64], hs[64];
     int L = hgo_level_sizes(w, h, min_size, ws, hs, 64);
@@ -378,13 +457,19 @@ int hgo_frame_features(const uint8_t *frame, int w, int h, int stride, int min_s
         free(img);
     } else {
         uint8_t *p8 = (uint8_t *)malloc(npx + 1);
-        hgo_pyramid_u8(frame, w, h, stride, min_size, p8, npx);
+        hgo_pyramid_u8_ex(frame, w, h, stride, min_size, skip_levels, direct, p8, npx);
         for (size_t i = 0; i < npx; i++) pyr[i] = p8[i];
         free(p8);
     }
     size_t poff = 0, foff = 0;
     for (int l = 0; l < L; l++) {
         int cx = ws[l] / CELL, cy = hs[l] / CELL;
+        if (!float_mode && direct && skip_levels >= 2 && l >= 1 && l < skip_levels) {
+            memset(feat + foff, 0, sizeof(double) * (size_t)cx * cy * NFEAT);
+            poff += (size_t)ws[l] * hs[l];
+            foff += (size_t)cx * cy * NFEAT;
+            continue;
+        }
         double *hist = (double *)malloc(sizeof(double) * ((size_t)cx * cy * NBIN + 1));
         hgo_cell_hist(pyr + poff, ws[l], hs[l], hist);
         hgo_features(hist, cx, cy, eps, tau, feat + foff);
@@ -397,9 +482,21 @@ int hgo_frame_features(const uint8_t *frame, int w, int h, int stride, int min_s
 }
 
 /* Scores of every level, concatenated ([nf][cy_l-9][cx_l-9] each).         */
+int hgo_frame_scores_ex(const uint8_t *frame, int w, int h, int stride, int min_size,
+                        int skip_levels, int direct, double eps, double tau,
+                        const double *filt, int nf, double *scores, size_t cap);
+
 int hgo_frame_scores(const uint8_t *frame, int w, int h, int stride, int min_size,
                      double eps, double tau, const double *filt, int nf,
                      double *scores, size_t cap)
+{
+    return hgo_frame_scores_ex(frame, w, h, stride, min_size, 0, 0, eps, tau, filt, nf,
+                               scores, cap);
+}
+
+int hgo_frame_scores_ex(const uint8_t *frame, int w, int h, int stride, int min_size,
+                        int skip_levels, int direct, double eps, double tau,
+                        const double *filt, int nf, double *scores, size_t cap)
 {
     int ws[64], hs[64];
     int L = hgo_level_sizes(w, h, min_size, ws, hs, 64);
@@ -412,7 +509,8 @@ int hgo_frame_scores(const uint8_t *frame, int w, int h, int stride, int min_siz
     }
     if (nwin > cap) return -2;
     double *feat = (double *)malloc(sizeof(double) * (ncell * NFEAT + 1));
-    hgo_frame_features(frame, w, h, stride, min_size, eps, tau, 0, feat, ncell * NFEAT);
+    hgo_frame_features_ex(frame, w, h, stride, min_size, skip_levels, direct, eps, tau, 0, feat,
+                          ncell * NFEAT);
     size_t foff = 0, soff = 0;
     for (int l = 0; l < L; l++) {
         int cx = ws[l] / CELL, cy = hs[l] / CELL;
@@ -427,9 +525,22 @@ int hgo_frame_scores(const uint8_t *frame, int w, int h, int stride, int min_siz
 /* Candidates of one frame: every (level >= skip_levels, filter, u, v) whose
  * score is strictly higher than the threshold, with its frame box.  Returns
  * the candidate count (may exceed cap; only cap are written) or < 0.        */
+int hgo_frame_candidates_ex(const uint8_t *frame, int w, int h, int stride, int min_size,
+                            int skip_levels, int direct, double eps, double tau,
+                            double threshold, const double *filt, int nf, hgo_det *out, int cap);
+
 int hgo_frame_candidates(const uint8_t *frame, int w, int h, int stride, int min_size,
                          int skip_levels, double eps, double tau, double threshold,
                          const double *filt, int nf, hgo_det *out, int cap)
+{
+    return hgo_frame_candidates_ex(frame, w, h, stride, min_size, skip_levels, 0, eps, tau,
+                                   threshold, filt, nf, out, cap);
+}
+
+/* As hgo_frame_candidates, the pyramid direct-to-size when direct != 0.    */
+int hgo_frame_candidates_ex(const uint8_t *frame, int w, int h, int stride, int min_size,
+                            int skip_levels, int direct, double eps, double tau,
+                            double threshold, const double *filt, int nf, hgo_det *out, int cap)
 {
     int ws[64], hs[64];
     int L = hgo_level_sizes(w, h, min_size, ws, hs, 64);
@@ -438,7 +549,8 @@ int hgo_frame_candidates(const uint8_t *frame, int w, int h, int stride, int min
     for (int l = 0; l < L; l++)
         nwin += (size_t)nf * (hs[l] / CELL - WIN + 1) * (ws[l] / CELL - WIN + 1);
     double *scores = (double *)malloc(sizeof(double) * (nwin + 1));
-    hgo_frame_scores(frame, w, h, stride, min_size, eps, tau, filt, nf, scores, nwin);
+    hgo_frame_scores_ex(frame, w, h, stride, min_size, skip_levels, direct, eps, tau, filt, nf,
+                        scores, nwin);
     int n = 0;
     size_t soff = 0;
     for (int l = 0; l < L; l++) {
@@ -465,10 +577,24 @@ int hgo_frame_candidates(const uint8_t *frame, int w, int h, int stride, int min
 
 /* Full detection of one frame: candidates then greedy NMS.  Writes the kept
  * detections in rank order; returns the kept count (or < 0).               */
+int hgo_detect_ex(const uint8_t *frame, int w, int h, int stride, int min_size,
+                  int skip_levels, int direct, double eps, double tau, double threshold,
+                  double nms_iou, const double *filt, int nf, hgo_det *out, int cap,
+                  int32_t *n_candidates);
+
 int hgo_detect(const uint8_t *frame, int w, int h, int stride, int min_size,
                int skip_levels, double eps, double tau, double threshold,
                double nms_iou, const double *filt, int nf, hgo_det *out, int cap,
                int32_t *n_candidates)
+{
+    return hgo_detect_ex(frame, w, h, stride, min_size, skip_levels, 0, eps, tau, threshold,
+                         nms_iou, filt, nf, out, cap, n_candidates);
+}
+
+int hgo_detect_ex(const uint8_t *frame, int w, int h, int stride, int min_size,
+                  int skip_levels, int direct, double eps, double tau, double threshold,
+                  double nms_iou, const double *filt, int nf, hgo_det *out, int cap,
+                  int32_t *n_candidates)
 {
     int ws[64], hs[64];
     int L = hgo_level_sizes(w, h, min_size, ws, hs, 64);
@@ -477,8 +603,8 @@ int hgo_detect(const uint8_t *frame, int w, int h, int stride, int min_size,
     for (int l = 0; l < L; l++)
         nwin += (size_t)nf * (hs[l] / CELL - WIN + 1) * (ws[l] / CELL - WIN + 1);
     hgo_det *c = (hgo_det *)malloc(sizeof(hgo_det) * (nwin + 1));
-    int n = hgo_frame_candidates(frame, w, h, stride, min_size, skip_levels, eps, tau,
-                                 threshold, filt, nf, c, (int)nwin);
+    int n = hgo_frame_candidates_ex(frame, w, h, stride, min_size, skip_levels, direct, eps, tau,
+                                    threshold, filt, nf, c, (int)nwin);
     if (n_candidates) *n_candidates = n;
     int32_t *keep = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
     hgo_nms(c, n, nms_iou, keep);
