@@ -472,6 +472,36 @@ def run_resolution(hog, synth, W, reps, dev, barrier, frames_640=None):
     return out
 
 
+def run_skip(hog, W, reps, barrier, frames):
+    """Skipping the largest scales (Section 5.1: a face of >= 20 % of the
+    frame needs no level-0 scan; the paper's GPU figures skip it) and the
+    direct-to-size pyramid (Section 6.6): batched 640x480 frames/s for
+    skip_levels 0, 1 and 2, and 2 with level 2 resampled straight from the
+    frame."""
+    out = {}
+    n = len(frames)
+    out_np, _keep = hog.pinned_dets(n * 4096)
+    for name, kw in (("full", {}), ("skip1", {"skip_levels": 1}), ("skip2", {"skip_levels": 2}),
+                     ("skip2_direct", {"skip_levels": 2, "direct_first": 1})):
+        det = hog.Detector(W, max_w=W0, max_h=H0, max_batch=n, **kw)
+        det.autotune(frames)
+        for _ in range(3):
+            det.detect(frames, out=out_np, batched=True)
+        barrier()
+        t0 = time.perf_counter()
+        kept = 0
+        for _ in range(reps):
+            _, c = det.detect(frames, out=out_np, batched=True)
+            kept += int(c.sum())
+        barrier()
+        dt = (time.perf_counter() - t0) / reps
+        det.close()
+        out[name] = {"frames_per_s": n / dt, "ms_per_frame": dt * 1e3 / n,
+                     "kept_per_frame": kept / (reps * n)}
+    out["workload"] = "%d frames of the 640x480 eyeblink stream, 5 filters, batched" % n
+    return out
+
+
 def run_backward(hog, synth, reps, dev, barrier):
     """Adjoint: hinge loss on the best window of one filter over 64 seeded
     128x128 crops; time per hog_backward call (loss, dW and dI)."""
@@ -649,6 +679,8 @@ def main():
         if args.backward_reps > 0 else None
     resolution = run_resolution(hog, synth, W, args.resolution_reps, dev, barrier, frames) \
         if args.resolution_reps > 0 else None
+    skip = run_skip(hog, W, args.resolution_reps, barrier, frames[:256]) \
+        if args.resolution_reps > 0 else None
 
     # ---- serving: continuous batching over 8 camera streams (rank 0 of a
     # replica job serves its own GPU like every other rank)
@@ -697,6 +729,7 @@ def main():
             "mixed_batch": mixed,
             "backward": backward,
             "resolution_scaling": resolution,
+            "skip_largest_scales": skip,
             "serving": serving,
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

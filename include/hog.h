@@ -69,7 +69,11 @@ typedef struct {
     int32_t scale_num;          /* 5  (each level is 5/6 of the previous)     */
     int32_t scale_den;          /* 6                                          */
     int32_t min_size;           /* 80: keep a level while min(w,h) >= this    */
-    int32_t skip_levels;        /* 0: levels < skip_levels are not scanned    */
+    int32_t skip_levels;        /* 0: levels < skip_levels are not scanned     *
+                                 * (Section 5.1: a face of >= 20 % of the      *
+                                 * frame needs no scan of the largest scale);  *
+                                 * detection computes no histograms or         *
+                                 * features for them either                    */
     float   eps;                /* 1e-4: added to block energies              */
     float   trunc;              /* 0.2: truncation of normalised bins         */
     float   threshold;          /* 0: detection iff score > threshold         */
@@ -78,6 +82,13 @@ typedef struct {
     int32_t max_batch;          /* frames per internal batch                  */
     int32_t max_dets_per_frame; /* device capacity of kept boxes per frame    */
     int32_t float_pyramid;      /* 0: uint8 pyramid (detection)               */
+    int32_t direct_first;       /* 0; 1 with skip_levels = s >= 2: level s is  *
+                                 * resampled straight from the frame with the *
+                                 * ratio (6/5)^s (Section 6.6, future work:   *
+                                 * direct-to-size downscale), levels 1..s-1   *
+                                 * are not computed (hog_pyramid/_features/   *
+                                 * _scores return zeros there), later levels  *
+                                 * follow in 5/6 steps.  s <= 8 with 1.       */
 } hog_params;
 
 /* One frame: 8-bit grayscale, row pitch in bytes (>= w).  For the device
@@ -243,7 +254,8 @@ int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog
  * nothing is allocated: the scratch (pyramid, histograms, internal features,
  * launch tables) is a 4 MiB file-scope device array that every GPU loading
  * libhog keeps until exit.  Only *p's min_size, eps and trunc are used (the
- * fixed fields are still checked).  frame (device) must be at most 640 x 480,
+ * fixed fields are still checked; direct_first must be 0: this entry point
+ * computes the plain 5/6 pyramid).  frame (device) must be at most 640 x 480,
  * else HOG_EINVAL with a message in err.  feat_out (device), levels (host)
  * and the capacities behave as in hog_features.  err (host, may be NULL)
  * receives a message on failure.  All calls on a device share the array:

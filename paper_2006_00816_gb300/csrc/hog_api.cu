@@ -216,6 +216,8 @@ int check_params(const hog_params *p, std::string &why) {
     if (p->max_batch < 1 || p->max_batch > 4096) { why = "max_batch out of range"; return HOG_EINVAL; }
     if (p->max_dets_per_frame < 1) { why = "max_dets_per_frame < 1"; return HOG_EINVAL; }
     if (p->float_pyramid != 0) { why = "float_pyramid is only used by hog_backward"; return HOG_EINVAL; }
+    if (p->direct_first != 0 && p->direct_first != 1) { why = "direct_first must be 0 or 1"; return HOG_EINVAL; }
+    if (p->direct_first && p->skip_levels > 8) { why = "direct_first needs skip_levels <= 8"; return HOG_EINVAL; }
     return HOG_OK;
 }
 
@@ -356,6 +358,12 @@ int get_geometry(hog_ctx *ctx, int W, int H, cudaStream_t stream, Geometry **out
 
 // ---- plans ---------------------------------------------------------------
 
+// Direct-to-size pyramids (hog_params.direct_first, skip_levels = s >= 2):
+// level s is resampled straight from the frame, levels 1..s-1 do not exist.
+bool level_absent(const hog_params &p, int l) {
+    return p.direct_first && p.skip_levels >= 2 && l >= 1 && l < p.skip_levels;
+}
+
 struct PlanBuilder {
     std::vector<LevelDesc> descs;
     std::vector<FrameDesc> frames;
@@ -388,7 +396,8 @@ void build_fused_items(PlanBuilder &pb) {
         for (const Job &j : seg) {
             const LevelDesc &d = pb.descs[j.desc];
             FusedItem it{FUSED_PYR, j.desc, j.tile, -1, 0, 3 * j.desc + 0};
-            if (d.level >= 2) { it.wait = 3 * (j.desc - 1) + 0; it.target = npyr[j.desc - 1]; }
+            // a 5/6 step waits for the previous level; a direct level reads the frame
+            if (d.level >= 2 && d.dpow < 2) { it.wait = 3 * (j.desc - 1) + 0; it.target = npyr[j.desc - 1]; }
             v.push_back({d.level, FUSED_PYR, j.desc, j.tile, it});
         }
     for (const Job &j : pb.hist) {
@@ -451,6 +460,7 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         d.frame = frame_index; d.level = l;
         d.scan = l >= ctx->p.skip_levels ? 1 : 0;
         d.pos_off = g.pos_off[l];
+        const bool absent = level_absent(ctx->p, l);
         if (l == 0) {
             d.img = f.data;
             d.pitch = f.pitch;
@@ -458,9 +468,12 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
             d.dst = pyr + g.pyr_off[l];
             d.img = d.dst;
             d.pitch = g.pitch[l];
-            const LevelDesc &prev = pb.descs[first + l - 1];
+            // a direct-to-size level reads the frame, a 5/6 step the previous level
+            const bool direct = ctx->p.direct_first && ctx->p.skip_levels >= 2 && l == ctx->p.skip_levels;
+            const LevelDesc &prev = pb.descs[direct ? first : first + l - 1];
             d.src = prev.img;
             d.sw = prev.w; d.sh = prev.h; d.spitch = prev.pitch;
+            d.dpow = direct ? l : 0;
         }
         d.hist = hist + g.hist_off[l];
         // the FP32 feature layout feeds the CUDA-core correlation only
@@ -470,18 +483,22 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         d.keys = keys + g.pos_off[l];
         pb.descs.push_back(d);
         const int di = first + l;
-        if (l >= 1) {
+        if (l >= 1 && !absent) {
             if ((int)pb.pyr.size() < l + 1) pb.pyr.resize(l + 1);
             const int nt = ((d.w + PYR_TX - 1) / PYR_TX) * ((d.h + PYR_TY - 1) / PYR_TY);
             for (int k = 0; k < nt; k++) pb.pyr[l].push_back({di, k});
         }
-        if (o.feat) {
+        // histograms and features: for scanned levels, and for every level
+        // whose features or scores the caller asked for (not for levels a
+        // direct-to-size pyramid leaves out)
+        const bool want = d.scan || o.feat_user || o.scores_user;
+        if (o.feat && want && !absent) {
             const int nh = ((d.cx + HIST_TX - 1) / HIST_TX) * ((d.cy + HIST_TY - 1) / HIST_TY);
             for (int k = 0; k < nh; k++) pb.hist.push_back({di, k});
             const int nfj = ((d.cx + FEAT_TX - 1) / FEAT_TX) * ((d.cy + FEAT_TY - 1) / FEAT_TY);
             for (int k = 0; k < nfj; k++) pb.feat.push_back({di, k});
         }
-        if (o.corr && d.nu > 0 && d.nv > 0 && (d.scan || o.scores_user)) {
+        if (o.corr && d.nu > 0 && d.nv > 0 && (d.scan || o.scores_user) && !absent) {
             // warp-tile shape: the one that pads this level's window grid
             // least, or the autotuner's preferred shape
             int best = 0, best_slots = 0, best_n = 0;
@@ -535,6 +552,7 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         std::memset(&fd, 0, sizeof fd);
         fd.W = g.W; fd.H = g.H; fd.nlev = g.nlev; fd.npos = g.npos;
         fd.frame = frame_index;
+        fd.scan_from = g.pos_off[std::min(std::max(ctx->p.skip_levels, 0), g.nlev)];
         for (int l = 0; l < g.nlev; l++) {
             fd.lev_w[l] = g.lw[l]; fd.lev_h[l] = g.lh[l];
             fd.lev_rx[l] = (double)g.W / (double)g.lw[l];
@@ -1108,6 +1126,7 @@ void hog_default_params(hog_params *p) {
     p->max_batch = 64;
     p->max_dets_per_frame = 16384;
     p->float_pyramid = 0;
+    p->direct_first = 0;
 }
 
 int hog_level_geometry(const hog_params *p, int32_t w, int32_t h, hog_level *levels, int32_t cap,
@@ -1265,8 +1284,11 @@ int hog_pyramid(hog_ctx *ctx, const hog_frame *frame, uint8_t *out, size_t cap_b
     if (rc) return rc;
     for (int l = 0; l < g.nlev; l++) {
         const LevelDesc &d = pb.descs[l];
-        CUDA_TRY(ctx, cudaMemcpy2DAsync(out + levels[l].offset, (size_t)d.w, d.img, (size_t)d.pitch,
-                                        (size_t)d.w, (size_t)d.h, cudaMemcpyDeviceToDevice, stream));
+        if (level_absent(ctx->p, l))
+            CUDA_TRY(ctx, cudaMemsetAsync(out + levels[l].offset, 0, (size_t)d.w * d.h, stream));
+        else
+            CUDA_TRY(ctx, cudaMemcpy2DAsync(out + levels[l].offset, (size_t)d.w, d.img, (size_t)d.pitch,
+                                            (size_t)d.w, (size_t)d.h, cudaMemcpyDeviceToDevice, stream));
     }
     return HOG_OK;
 }
@@ -1293,6 +1315,10 @@ int hog_features(hog_ctx *ctx, const hog_frame *frame, float *feat_out, size_t c
     o.corr = false; o.nms = false;
     o.feat_user = feat_out;
     add_frame(ctx, pb, g, *frame, 0, 0, o);
+    for (int l = 0; l < g.nlev; l++)
+        if (level_absent(ctx->p, l))
+            CUDA_TRY(ctx, cudaMemsetAsync(feat_out + g.ufeat_off[l], 0,
+                                          sizeof(float) * (size_t)g.cx[l] * g.cy[l] * NFEAT, stream));
     return run_plan(ctx, pb, stream);
 }
 
@@ -1323,6 +1349,10 @@ int hog_scores(hog_ctx *ctx, const hog_frame *frame, float *scores_out, size_t c
     o.scores_user = scores_out;
     o.score_off = soff;
     add_frame(ctx, pb, g, *frame, 0, 0, o);
+    for (int l = 0; l < g.nlev; l++)
+        if (level_absent(ctx->p, l))
+            CUDA_TRY(ctx, cudaMemsetAsync(scores_out + soff[l], 0,
+                                          sizeof(float) * (size_t)ctx->nf * g.nu[l] * g.nv[l], stream));
     return run_plan(ctx, pb, stream);
 }
 

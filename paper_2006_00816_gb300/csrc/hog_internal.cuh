@@ -97,6 +97,8 @@ struct LevelDesc {
     int32_t cx, cy, nu, nv; // cells, windows
     int32_t frame, level;   // batch-relative frame index, level index
     int32_t scan;           // 1: this level takes part in detection
+    int32_t dpow;           // pyramid job: 0 = 5/6 step from src; s >= 2 = direct
+                            // from the frame (src) with the ratio (6/5)^s
     int32_t pos_off;        // first window position of this level in the frame
     float *hist;            // [cy][cx][18]
     float *feat;            // [4][cy][cx][8] internal layout
@@ -114,6 +116,7 @@ struct LevelDesc {
 struct FrameDesc {
     int32_t W, H, nlev, npos;
     int32_t frame;                    // batch-relative frame index
+    int32_t scan_from;                // first position of a scanned level (earlier ones: no key)
     int32_t lev_w[MAX_LEVELS], lev_h[MAX_LEVELS];
     int32_t lev_nu[MAX_LEVELS], lev_nv[MAX_LEVELS];
     int32_t lev_pos[MAX_LEVELS + 1];

@@ -28,6 +28,41 @@ __device__ __forceinline__ T ld_in(const T *p) {
 // Output pixel (x, y) of level l+1 samples level l at ((12x+1)/10,
 // (12y+1)/10) with exact weights in tenths, rounded half up (integer-exact).
 // 256 threads: 4 output pixels each, tile PYR_TX x PYR_TY.
+// Direct-to-size level (Section 6.6, future work): level s straight from
+// the frame with the ratio (6/5)^s, source coordinate ((2x+1) 6^s - 5^s) /
+// (2 5^s), weights in units of 1/(2 5^s), rounded half up; 64-bit integer
+// arithmetic, exact.  s = d.dpow (2..8).
+template <bool COH>
+__device__ __noinline__ void pyramid_direct_tile(const LevelDesc &d, int x, int y) {
+    long long p6 = 1, p5 = 1;
+    for (int k = 0; k < d.dpow; k++) { p6 *= 6; p5 *= 5; }
+    const long long D = 2 * p5;
+    const long long Y = (2 * (long long)y + 1) * p6 - p5;
+    const long long y0 = Y / D, fy = Y - D * y0;
+    const uint8_t *r0 = d.src + (size_t)y0 * d.spitch;
+    const uint8_t *r1 = r0 + d.spitch;
+    uint32_t packed = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int xx = x + k;
+        if (xx < d.w) {
+            const long long X = (2 * (long long)xx + 1) * p6 - p5;
+            const long long x0 = X / D, fx = X - D * x0;
+            const long long p00 = ld_in<COH>(r0 + x0), p10 = ld_in<COH>(r0 + x0 + 1);
+            const long long p01 = ld_in<COH>(r1 + x0), p11 = ld_in<COH>(r1 + x0 + 1);
+            const long long acc = (D - fx) * (D - fy) * p00 + fx * (D - fy) * p10 +
+                                  (D - fx) * fy * p01 + fx * fy * p11;
+            packed |= (uint32_t)((acc + D * D / 2) / (D * D)) << (8 * k);
+        }
+    }
+    uint8_t *out = d.dst + (size_t)y * d.pitch + x;
+    if (x + 3 < d.w) {
+        *reinterpret_cast<uint32_t *>(out) = packed;
+    } else {
+        for (int k = 0; k < 4 && x + k < d.w; k++) out[k] = (uint8_t)(packed >> (8 * k));
+    }
+}
+
 template <bool COH>
 __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
     const int ntx = (d.w + PYR_TX - 1) / PYR_TX;
@@ -35,6 +70,10 @@ __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
     const int x = tx * PYR_TX + (threadIdx.x & 31) * 4;
     const int y = ty * PYR_TY + (threadIdx.x >> 5);
     if (y >= d.h || x >= d.w) return;
+    if (d.dpow >= 2) {
+        pyramid_direct_tile<COH>(d, x, y);
+        return;
+    }
     const int Y = 12 * y + 1;
     const int y0 = Y / 10, fy = Y - 10 * (Y / 10);
     const uint8_t *r0 = d.src + (size_t)y0 * d.spitch;
@@ -630,7 +669,8 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
         const int p = p0 + t;
         uint32_t h = NMS_NOKEY;
         if (p < npos) {
-            h = (uint32_t)(ld_in<COH>(gkeys + p) >> 32);
+            // positions of levels that are not scanned carry no key
+            if (p >= fd.scan_from) h = (uint32_t)(ld_in<COH>(gkeys + p) >> 32);
             khi[p] = h;
             state[p] = h != NMS_NOKEY ? NMS_ALIVE : NMS_DEAD;
             resume[p] = 0;

@@ -78,7 +78,8 @@ extern "C" int hog_features_static(const hog_params *p, const hog_frame *frame, 
     if (!p || !frame || !n_levels)
         return put_error(err, err_cap, HOG_EINVAL, "hog_features_static: NULL argument");
     if (p->cell != CELL || p->win_cells_w != WIN || p->win_cells_h != WIN || p->scale_num != 5 ||
-        p->scale_den != 6 || p->min_size < CELL * WIN || !(p->eps > 0.0f) || !(p->trunc > 0.0f))
+        p->scale_den != 6 || p->min_size < CELL * WIN || !(p->eps > 0.0f) || !(p->trunc > 0.0f) ||
+        p->direct_first != 0)
         return put_error(err, err_cap, HOG_EINVAL, "hog_features_static: invalid parameters");
     if (frame->w < 0 || frame->h < 0 || frame->w > STATIC_MAX_W || frame->h > STATIC_MAX_H) {
         char buf[160];

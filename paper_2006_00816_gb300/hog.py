@@ -31,7 +31,8 @@ class Params(C.Structure):
                 ("skip_levels", C.c_int32), ("eps", C.c_float), ("trunc", C.c_float),
                 ("threshold", C.c_float), ("nms_iou", C.c_float), ("max_w", C.c_int32),
                 ("max_h", C.c_int32), ("max_batch", C.c_int32),
-                ("max_dets_per_frame", C.c_int32), ("float_pyramid", C.c_int32)]
+                ("max_dets_per_frame", C.c_int32), ("float_pyramid", C.c_int32),
+                ("direct_first", C.c_int32)]
 
 
 class Frame(C.Structure):
