@@ -80,6 +80,9 @@ def lib():
             "hgo_frame_scores_ex": (i, [u8p, i, i, i, i, i, i, d, d, dp, i, dp, sz]),
             "hgo_frame_candidates_ex": (i, [u8p, i, i, i, i, i, i, d, d, d, dp, i, P(Det), i]),
             "hgo_detect_ex": (i, [u8p, i, i, i, i, i, i, d, d, d, d, dp, i, P(Det), i, i32p]),
+            "hgo_in_roi": (i, [i, i, i, i, i, i, i, dp]),
+            "hgo_detect_roi": (i, [u8p, i, i, i, i, i, i, d, d, d, d, dp, i, dp, P(Det), i,
+                                   i32p]),
             "hgo_pyramid_f64": (i, [dp, i, i, i, dp, sz]),
             "hgo_frame_features": (i, [u8p, i, i, i, i, d, d, i, dp, sz]),
             "hgo_frame_scores": (i, [u8p, i, i, i, i, d, d, dp, i, dp, sz]),
@@ -292,6 +295,34 @@ def detect(frame, filt, min_size=80, skip_levels=0, eps=EPS, tau=TAU, threshold=
     k = lib().hgo_detect_ex(_p(frame, C.c_uint8), w, h, w, min_size, skip_levels,
                             int(bool(direct)), eps, tau, threshold, nms_iou,
                             _p(filt, C.c_double), nf, _p(out, Det), cap, C.byref(ncand))
+    return out[:k].copy(), ncand.value
+
+
+def in_roi(W0, H0, Wl, Hl, level, u, v, roi):
+    """Whether window (u, v) of a level is scanned under roi = (x0, y0, x1,
+    y1, lmin, lmax): level in range and the window's frame-pixel centre in
+    the half-open box (Section 6.6, future work)."""
+    r = np.ascontiguousarray(roi, dtype=np.float64)
+    return bool(lib().hgo_in_roi(W0, H0, Wl, Hl, level, u, v, _p(r, C.c_double)))
+
+
+def detect_roi(frame, filt, roi, min_size=80, skip_levels=0, eps=EPS, tau=TAU, threshold=0.0,
+               nms_iou=0.5, direct=False):
+    """Kept detections of one frame restricted to roi = (x0, y0, x1, y1,
+    lmin, lmax), in rank order, and the restricted candidate count."""
+    frame = np.ascontiguousarray(frame, dtype=np.uint8)
+    filt = np.ascontiguousarray(filt, dtype=np.float64)
+    r = np.ascontiguousarray(roi, dtype=np.float64)
+    h, w = frame.shape
+    nf = filt.shape[0]
+    cap = sum(nf * max(b // CELL - WIN + 1, 0) * max(a // CELL - WIN + 1, 0)
+              for a, b in level_sizes(w, h, min_size))
+    out = np.zeros(max(cap, 1), DET_DTYPE)
+    ncand = C.c_int32(0)
+    k = lib().hgo_detect_roi(_p(frame, C.c_uint8), w, h, w, min_size, skip_levels,
+                             int(bool(direct)), eps, tau, threshold, nms_iou,
+                             _p(filt, C.c_double), nf, _p(r, C.c_double), _p(out, Det), cap,
+                             C.byref(ncand))
     return out[:k].copy(), ncand.value
 
 

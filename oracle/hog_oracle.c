@@ -45,6 +45,11 @@
  *      under the R2 rule generalised (weights in units of 1/(2*5^s)); the
  *      levels between are not computed; the later levels follow in 5/6
  *      steps.  For s = 1 the one step is the 5/6 step itself.
+ *   R13 region of interest (Section 6.6, future work: scan only scales and
+ *      locations near the previous frame's face): a window is scanned iff
+ *      its level is in [lmin, lmax] and its centre, mapped to the frame in
+ *      FP64 as (8v + 40) * (W0/Wl), (8u + 40) * (H0/Hl), is in [x0, x1) x
+ *      [y0, y1) (hgo_in_roi).
  * Built with -ffp-contract=off so that results are identical on x86-64 and
  * aarch64 hosts.
  */
@@ -573,6 +578,53 @@ int hgo_frame_candidates_ex(const uint8_t *frame, int w, int h, int stride, int 
     }
     free(scores);
     return n;
+}
+
+/* Region of interest (Section 6.6, future work: near the previous frame's
+ * face only some scales and locations need a scan).  Window (u, v) of level
+ * l is scanned iff lmin <= l <= lmax and its centre, (8v + 40, 8u + 40) in
+ * level pixels mapped to the frame as fl((8v + 40) * fl(W0 / Wl)) and
+ * fl((8u + 40) * fl(H0 / Hl)), lies in [x0, x1) x [y0, y1).               */
+int hgo_in_roi(int W0, int H0, int Wl, int Hl, int l, int u, int v,
+               const double *roi /* x0, y0, x1, y1, lmin, lmax */)
+{
+    if (l < (int)roi[4] || l > (int)roi[5]) return 0;
+    double rx = (double)W0 / (double)Wl, ry = (double)H0 / (double)Hl;
+    double cx = (double)(CELL * v + CELL * WIN / 2) * rx;
+    double cy = (double)(CELL * u + CELL * WIN / 2) * ry;
+    return cx >= roi[0] && cx < roi[2] && cy >= roi[1] && cy < roi[3];
+}
+
+/* Detection restricted to a region of interest: the candidates of
+ * hgo_frame_candidates_ex whose window passes hgo_in_roi, then greedy NMS.
+ * Returns the kept count; *n_candidates gets the restricted count.        */
+int hgo_detect_roi(const uint8_t *frame, int w, int h, int stride, int min_size,
+                   int skip_levels, int direct, double eps, double tau, double threshold,
+                   double nms_iou, const double *filt, int nf, const double *roi,
+                   hgo_det *out, int cap, int32_t *n_candidates)
+{
+    int ws[64], hs[64];
+    int L = hgo_level_sizes(w, h, min_size, ws, hs, 64);
+    if (L > 64) return -1;
+    size_t nwin = 0;
+    for (int l = 0; l < L; l++)
+        nwin += (size_t)nf * (hs[l] / CELL - WIN + 1) * (ws[l] / CELL - WIN + 1);
+    hgo_det *c = (hgo_det *)malloc(sizeof(hgo_det) * (nwin + 1));
+    int n = hgo_frame_candidates_ex(frame, w, h, stride, min_size, skip_levels, direct, eps, tau,
+                                    threshold, filt, nf, c, (int)nwin);
+    int m = 0;
+    for (int i = 0; i < n; i++)
+        if (hgo_in_roi(w, h, ws[c[i].level], hs[c[i].level], c[i].level, c[i].u, c[i].v, roi))
+            c[m++] = c[i];
+    if (n_candidates) *n_candidates = m;
+    int32_t *keep = (int32_t *)malloc(sizeof(int32_t) * ((size_t)m + 1));
+    hgo_nms(c, m, nms_iou, keep);
+    int k = 0;
+    for (int i = 0; i < m; i++)
+        if (keep[i]) { if (k < cap) out[k] = c[i]; k++; }
+    free(keep);
+    free(c);
+    return k;
 }
 
 /* Full detection of one frame: candidates then greedy NMS.  Writes the kept
