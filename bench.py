@@ -502,6 +502,63 @@ def run_skip(hog, W, reps, barrier, frames):
     return out
 
 
+def run_tracking(hog, W, frames, reps, barrier, n_seq=200):
+    """Temporal region of interest (Section 6.6, future work: near the
+    previous frame's face only some scales and locations need a scan): each
+    frame is scanned only around the previous frame's best detection (box
+    grown by half its size on each side, levels within one of its level;
+    hog_roi_around + hog_detect_roi).  Per-frame latency of the tracked
+    sequence against full-frame calls, and batched frames/s of the stream
+    with each frame's region taken from the previous frame's full result."""
+    n = len(frames)
+    out_np, _keep = hog.pinned_dets(n * 2048)
+    det = hog.Detector(W, max_w=W0, max_h=H0, max_batch=250)
+    # regions from a full pass: frame k uses frame k-1's best box
+    full, counts = det.detect(frames, out=out_np, batched=True)
+    full = full.copy()
+    rois, off, prev = [], 0, None
+    for i in range(n):
+        c = int(counts[i])
+        rois.append(hog.roi_around(prev, W0, H0) if prev is not None
+                    else hog.Roi(-1e9, -1e9, 1e9, 1e9, 0, 99))
+        if c > 0:
+            seg = full[off:off + c]
+            prev = seg[int(np.argmax(seg["score"]))]
+        off += c
+    for _ in range(3):
+        det.detect_roi(frames, rois, out=out_np)
+    barrier()
+    t0 = time.perf_counter()
+    kept = 0
+    for _ in range(reps):
+        _, c = det.detect_roi(frames, rois, out=out_np)
+        kept += int(c.sum())
+    barrier()
+    batched_s = (time.perf_counter() - t0) / reps
+    det.close()
+    # sequential tracking, one frame per call (each region from the call before)
+    one = hog.Detector(W, max_w=W0, max_h=H0, max_batch=1)
+    for f in frames[:5]:
+        one.detect([f], out=out_np)
+    barrier()
+    lat, prev = [], None
+    for f in frames[:n_seq]:
+        t1 = time.perf_counter()
+        if prev is None:
+            d, c = one.detect([f], out=out_np)
+        else:
+            d, c = one.detect_roi([f], [hog.roi_around(prev, W0, H0)], out=out_np)
+        lat.append((time.perf_counter() - t1) * 1e3)
+        prev = d[int(np.argmax(d["score"]))].copy() if int(c[0]) > 0 else None
+    one.close()
+    return {"workload": "%d frames of the 640x480 eyeblink stream, region = previous frame's "
+                        "best box grown by 0.5 of its size per side, levels +-1" % n,
+            "batched_frames_per_s": n / batched_s, "batched_ms_per_frame": batched_s * 1e3 / n,
+            "kept_per_frame": kept / (reps * n),
+            "tracked_p50_ms": statistics.median(lat[1:]),
+            "tracked_p99_ms": float(np.percentile(lat[1:], 99)), "tracked_frames": n_seq}
+
+
 def run_backward(hog, synth, reps, dev, barrier):
     """Adjoint: hinge loss on the best window of one filter over 64 seeded
     128x128 crops; time per hog_backward call (loss, dW and dI)."""
@@ -681,6 +738,8 @@ def main():
         if args.resolution_reps > 0 else None
     skip = run_skip(hog, W, args.resolution_reps, barrier, frames[:256]) \
         if args.resolution_reps > 0 else None
+    tracking = run_tracking(hog, W, frames, args.resolution_reps, barrier) \
+        if args.resolution_reps > 0 else None
 
     # ---- serving: continuous batching over 8 camera streams (rank 0 of a
     # replica job serves its own GPU like every other rank)
@@ -730,6 +789,7 @@ def main():
             "backward": backward,
             "resolution_scaling": resolution,
             "skip_largest_scales": skip,
+            "temporal_roi": tracking,
             "serving": serving,
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -240,6 +240,33 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
 /* Current tuning: batched mode (0/1) and correlation shape policy (0..3). */
 int hog_get_tuning(const hog_ctx *ctx, int32_t *batched_mode, int32_t *corr_policy);
 
+/* Region of interest of one frame (Section 6.6, future work: near the
+ * previous frame's face, scan only some scales and locations).  Window (u, v)
+ * of level l is scanned iff lmin <= l <= lmax (and l >= skip_levels) and its
+ * centre, (8v + 40, 8u + 40) in level pixels mapped to the frame in FP64 as
+ * (8v + 40) * (W/Wl) and (8u + 40) * (H/Hl), lies in [x0, x1) x [y0, y1). */
+typedef struct {
+    double x0, y0, x1, y1;
+    int32_t lmin, lmax;
+} hog_roi;
+
+/* hog_detect restricted to one region of interest per frame (rois[i] for
+ * frames[i], host array): the kept boxes are greedy NMS over the scanned
+ * windows' candidates only.  Pyramid levels above the last scanned one, and
+ * histograms and features of cells no scanned window reads, are not
+ * computed.  A region covering every window gives hog_detect's result bit
+ * for bit.  Arguments, outputs and errors as hog_detect; HOG_EINVAL if rois
+ * is NULL or a box is not finite.  Synchronises the stream. */
+int hog_detect_roi(hog_ctx *ctx, const hog_frame *frames, const hog_roi *rois, int32_t n_frames,
+                   hog_det *dets, int32_t det_cap, int32_t *counts, void *stream);
+
+/* Region of interest around a previous detection (host only): the box of
+ * *prev grown by margin times its width and height on each side, clipped
+ * to the W x H frame, and the levels prev->level - dlev .. prev->level +
+ * dlev.  HOG_EINVAL for NULL pointers, a negative margin or dlev. */
+int hog_roi_around(const hog_det *prev, int32_t W, int32_t H, double margin, int32_t dlev,
+                   hog_roi *out);
+
 /* Same result as hog_detect, from frames in HOST memory: the frames are
  * copied to the device inside the call (pinned staging) and processed like
  * hog_detect_batched. */

@@ -371,7 +371,8 @@ struct PlanBuilder {
     std::vector<Job> hist, feat, corr;
     std::vector<Job> corrf;              // correlation jobs of the fused launch (8x16, 16x8 tiles)
     std::vector<Job> tc, tcr;            // tensor-core correlation: 128-cell tiles, 256-window blocks
-    std::vector<int> tcf_levels;         // fused tensor-core correlation: level descriptors to band
+    struct TcRect { int desc, u0, u1, v0, v1; };
+    std::vector<TcRect> tcf_rects;       // fused tensor-core correlation: window rectangles to band
     std::vector<TcBand> bands;           // ... their bands, in per-CTA order
     std::vector<int32_t> cta_first;      // ... CTA k runs bands [cta_first[k], cta_first[k+1])
     std::vector<FusedItem> items;        // persistent fused launch (built on demand)
@@ -439,7 +440,42 @@ struct FrameOpts {
     float *scores_user = nullptr;   // [F][nu][nv] per level
     const size_t *score_off = nullptr;
     bool corr = true, nms = true, feat = true;
+    const hog_roi *roi = nullptr;   // detection restricted to a region of interest
 };
+
+// Window rectangles [u0, u1) x [v0, v1) per level that a region of interest
+// scans (empty where none): level in [max(lmin, skip_levels), lmax], window
+// centre fl((8v + 40) fl(W/Wl)), fl((8u + 40) fl(H/Hl)) in [x0, x1) x
+// [y0, y1) -- the centre grows with v and u, so the scanned windows of a
+// level are a rectangle.
+void roi_rects(const hog_params &p, const Geometry &g, const hog_roi &r, int *u0, int *u1, int *v0,
+               int *v1) {
+    for (int l = 0; l < g.nlev; l++) {
+        u0[l] = u1[l] = v0[l] = v1[l] = 0;
+        if (l < r.lmin || l > r.lmax || l < p.skip_levels || g.nu[l] <= 0 || g.nv[l] <= 0) continue;
+        const double rx = (double)g.W / (double)g.lw[l], ry = (double)g.H / (double)g.lh[l];
+        int a = 0, b = 0;
+        while (a < g.nv[l] && (double)(CELL * a + CELL * WIN / 2) * rx < r.x0) a++;
+        b = a;
+        while (b < g.nv[l] && (double)(CELL * b + CELL * WIN / 2) * rx < r.x1) b++;
+        int c = 0, e = 0;
+        while (c < g.nu[l] && (double)(CELL * c + CELL * WIN / 2) * ry < r.y0) c++;
+        e = c;
+        while (e < g.nu[l] && (double)(CELL * e + CELL * WIN / 2) * ry < r.y1) e++;
+        if (a < b && c < e) { v0[l] = a; v1[l] = b; u0[l] = c; u1[l] = e; }
+    }
+}
+
+// Tiles of a tw x th cell tiling of a cx-wide level that meet the cell
+// rectangle [r0, r1) x [c0, c1).
+template <typename F>
+void tiles_meeting(int cx, int cy, int tw, int th, int r0, int r1, int c0, int c1, F emit) {
+    const int ntx = (cx + tw - 1) / tw;
+    r0 = std::max(r0, 0); c0 = std::max(c0, 0); r1 = std::min(r1, cy); c1 = std::min(c1, cx);
+    if (r0 >= r1 || c0 >= c1) return;
+    for (int ty = r0 / th; ty <= (r1 - 1) / th; ty++)
+        for (int tx = c0 / tw; tx <= (c1 - 1) / tw; tx++) emit(ty * ntx + tx);
+}
 
 void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame &f, int slot,
                int frame_index, const FrameOpts &o) {
@@ -452,6 +488,16 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
     float *gm = ctx->corr_engine == 2 ? ctx->d_gm + (size_t)slot * ctx->gm_slot : nullptr;
     size_t cell_off = 0;
     const int first = (int)pb.descs.size();
+    // region of interest: scanned window rectangles, and the last level any
+    // of them needs (no pyramid, histograms or features above it)
+    int ru0[MAX_LEVELS], ru1[MAX_LEVELS], rv0[MAX_LEVELS], rv1[MAX_LEVELS];
+    int lneed = g.nlev - 1;
+    if (o.roi) {
+        roi_rects(ctx->p, g, *o.roi, ru0, ru1, rv0, rv1);
+        lneed = -1;
+        for (int l = 0; l < g.nlev; l++)
+            if (ru0[l] < ru1[l]) lneed = l;
+    }
     for (int l = 0; l < g.nlev; l++) {
         LevelDesc d;
         std::memset(&d, 0, sizeof d);
@@ -459,8 +505,9 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         d.cx = g.cx[l]; d.cy = g.cy[l]; d.nu = g.nu[l]; d.nv = g.nv[l];
         d.frame = frame_index; d.level = l;
         d.scan = l >= ctx->p.skip_levels ? 1 : 0;
+        if (o.roi) d.scan = ru0[l] < ru1[l] ? 1 : 0;
         d.pos_off = g.pos_off[l];
-        const bool absent = level_absent(ctx->p, l);
+        const bool absent = level_absent(ctx->p, l) || l > lneed;
         if (l == 0) {
             d.img = f.data;
             d.pitch = f.pitch;
@@ -492,7 +539,14 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         // whose features or scores the caller asked for (not for levels a
         // direct-to-size pyramid leaves out)
         const bool want = d.scan || o.feat_user || o.scores_user;
-        if (o.feat && want && !absent) {
+        if (o.feat && want && !absent && o.roi) {
+            // only the cells the scanned windows read: features of cell rows
+            // [u0, u1 + 9) x cols [v0, v1 + 9), histograms one cell wider
+            tiles_meeting(d.cx, d.cy, HIST_TX, HIST_TY, ru0[l] - 1, ru1[l] + WIN, rv0[l] - 1,
+                          rv1[l] + WIN, [&](int k) { pb.hist.push_back({di, k}); });
+            tiles_meeting(d.cx, d.cy, FEAT_TX, FEAT_TY, ru0[l], ru1[l] + WIN - 1, rv0[l],
+                          rv1[l] + WIN - 1, [&](int k) { pb.feat.push_back({di, k}); });
+        } else if (o.feat && want && !absent) {
             const int nh = ((d.cx + HIST_TX - 1) / HIST_TX) * ((d.cy + HIST_TY - 1) / HIST_TY);
             for (int k = 0; k < nh; k++) pb.hist.push_back({di, k});
             const int nfj = ((d.cx + FEAT_TX - 1) / FEAT_TX) * ((d.cy + FEAT_TY - 1) / FEAT_TY);
@@ -524,8 +578,10 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
                     const int nt = (int)((nc + 127) / 128), nr = (d.nu * d.nv + 255) / 256;
                     for (int k = 0; k < nt; k++) pb.tc.push_back({di, k});
                     for (int k = 0; k < nr; k++) pb.tcr.push_back({di, k});
+                } else if (o.roi) {
+                    pb.tcf_rects.push_back({di, ru0[l], ru1[l], rv0[l], rv1[l]});
                 } else {
-                    pb.tcf_levels.push_back(di);
+                    pb.tcf_rects.push_back({di, 0, d.nu, 0, d.nv});
                 }
             } else {
                 for (int k = 0; k < best_n; k++) pb.corr.push_back({di, (best << 28) | k});
@@ -553,6 +609,13 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         fd.W = g.W; fd.H = g.H; fd.nlev = g.nlev; fd.npos = g.npos;
         fd.frame = frame_index;
         fd.scan_from = g.pos_off[std::min(std::max(ctx->p.skip_levels, 0), g.nlev)];
+        if (o.roi) {
+            fd.has_roi = 1;
+            for (int l = 0; l < g.nlev; l++) {
+                fd.roi_u0[l] = ru0[l]; fd.roi_u1[l] = ru1[l];
+                fd.roi_v0[l] = rv0[l]; fd.roi_v1[l] = rv1[l];
+            }
+        }
         for (int l = 0; l < g.nlev; l++) {
             fd.lev_w[l] = g.lw[l]; fd.lev_h[l] = g.lh[l];
             fd.lev_rx[l] = (double)g.W / (double)g.lw[l];
@@ -583,19 +646,25 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
 void build_tc_bands(PlanBuilder &pb, int num_sms) {
     pb.bands.clear();
     pb.cta_first.clear();
-    if (pb.tcf_levels.empty()) return;
-    struct Strip { int desc, nu, c0, nvs, P; };
+    if (pb.tcf_rects.empty()) return;
+    // strips: window rows [ub, ub + nu), columns [c0, c0 + nvs); P cells per
+    // staged row (the level's width when the strip spans every column)
+    struct Strip { int desc, ub, nu, c0, nvs, P; };
     std::vector<Strip> strips;
-    for (int di : pb.tcf_levels) {
-        const LevelDesc &d = pb.descs[di];
-        const int S = (d.nv + (TCF_PMAX - WIN)) / (TCF_PMAX - WIN + 1);   // ceil(nv / (PMAX - 9))
-        int c0 = 0;
+    for (const auto &r : pb.tcf_rects) {
+        const LevelDesc &d = pb.descs[r.desc];
+        const int nv = r.v1 - r.v0, nu = r.u1 - r.u0;
+        if (nv <= 0 || nu <= 0) continue;
+        const int S = (nv + (TCF_PMAX - WIN)) / (TCF_PMAX - WIN + 1);   // ceil(nv / (PMAX - 9))
+        int c0 = r.v0;
         for (int k = 0; k < S; k++) {
-            const int nvs = d.nv / S + (k < d.nv % S ? 1 : 0);
-            strips.push_back({di, d.nu, c0, nvs, S == 1 ? d.cx : nvs + WIN - 1});
+            const int nvs = nv / S + (k < nv % S ? 1 : 0);
+            const bool full = r.v0 == 0 && nvs == d.nv;
+            strips.push_back({r.desc, r.u0, nu, c0, nvs, full ? d.cx : nvs + WIN - 1});
             c0 += nvs;
         }
     }
+    if (strips.empty()) return;
     // window rows per band for a tile budget M (at least one row)
     auto rows_for = [](const Strip &st, long M) {
         const long h = M * 128 / st.P - (WIN - 1);
@@ -632,7 +701,8 @@ void build_tc_bands(PlanBuilder &pb, int num_sms) {
         const int h0 = rows_for(st, best_M);
         const int nb = (st.nu + h0 - 1) / h0;
         for (int k = 0; k < nb; k++) {
-            const int u0 = (int)((long)st.nu * k / nb), u1 = (int)((long)st.nu * (k + 1) / nb);
+            const int u0 = st.ub + (int)((long)st.nu * k / nb);
+            const int u1 = st.ub + (int)((long)st.nu * (k + 1) / nb);
             all.push_back({st.desc, u0, u1, st.c0, st.P, st.nvs});
             cost.push_back(tcf_tiles(u0, u1, st.P));
         }
@@ -829,15 +899,23 @@ int run_plan(hog_ctx *ctx, PlanBuilder &pb, cudaStream_t stream) {
 // frames (pointer, size, pitch) and frame numbering: a repeated batch (a
 // ring of camera buffers, a benchmark loop) skips plan building and upload.
 int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, cudaStream_t stream,
-                const char **d_out, const PlanInfo **info_out, CachedPlan **entry = nullptr) {
+                const char **d_out, const PlanInfo **info_out, CachedPlan **entry = nullptr,
+                const hog_roi *rois = nullptr) {
     std::vector<uint64_t> sig;
-    sig.reserve(2 + 2 * (size_t)nb);
-    sig.push_back((uint64_t)nb);
+    sig.reserve(2 + 2 * (size_t)nb + (rois ? 5 * (size_t)nb : 0));
+    sig.push_back((uint64_t)nb | (rois ? (1ull << 63) : 0ull));
     sig.push_back((uint64_t)(uint32_t)frame_base);
     for (int i = 0; i < nb; i++) {
         sig.push_back((uint64_t)(uintptr_t)frames[i].data);
         sig.push_back(((uint64_t)(uint32_t)frames[i].w << 40) ^ ((uint64_t)(uint32_t)frames[i].h << 20) ^
                       (uint64_t)(uint32_t)frames[i].pitch);
+        if (rois) {
+            const hog_roi &r = rois[i];
+            uint64_t b[4];
+            std::memcpy(b, &r.x0, sizeof b);   // x0, y0, x1, y1 bit patterns
+            for (uint64_t v : b) sig.push_back(v);
+            sig.push_back(((uint64_t)(uint32_t)r.lmin << 32) | (uint32_t)r.lmax);
+        }
     }
     ctx->plan_clock++;
     for (auto &cp : ctx->plans)
@@ -857,6 +935,7 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
         if (rc) return rc;
         FrameOpts o;
         o.nms = g->npos > 0;
+        o.roi = rois ? &rois[i] : nullptr;
         add_frame(ctx, pb, *g, f, i, frame_base + i, o);
     }
     build_fused_items(pb);
@@ -1006,7 +1085,7 @@ int check_frame(hog_ctx *ctx, const hog_frame *f, bool device) {
 
 int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, hog_det *dets,
                   int det_cap, int *written_out, int32_t *counts, cudaStream_t stream,
-                  int mode = MODE_STAGED, bool use_graph = false) {
+                  int mode = MODE_STAGED, bool use_graph = false, const hog_roi *rois = nullptr) {
     int written = 0;
     bool truncated = false;
     // A pinned (page-locked, mapped) output buffer is written by the device
@@ -1024,7 +1103,8 @@ int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, 
         const char *dplan = nullptr;
         const PlanInfo *info = nullptr;
         CachedPlan *cp = nullptr;
-        int rc = cached_plan(ctx, frames + b0, nb, frame_base + b0, stream, &dplan, &info, &cp);
+        int rc = cached_plan(ctx, frames + b0, nb, frame_base + b0, stream, &dplan, &info, &cp,
+                             rois ? rois + b0 : nullptr);
         if (rc) return rc;
         rc = run_batch(ctx, mode, cp, nb, use_graph, stream);
         if (rc) return rc;
@@ -1380,6 +1460,35 @@ int hog_detect_batched(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, 
     }
     return detect_device(ctx, frames, n_frames, 0, dets, det_cap, nullptr, counts,
                          (cudaStream_t)stream_, ctx->batched_mode, true);
+}
+
+int hog_roi_around(const hog_det *prev, int32_t W, int32_t H, double margin, int32_t dlev,
+                   hog_roi *out) {
+    if (!prev || !out || !(margin >= 0.0) || dlev < 0) return HOG_EINVAL;
+    const double mx = margin * prev->w, my = margin * prev->h;
+    out->x0 = std::max(0.0, prev->x - mx);
+    out->y0 = std::max(0.0, prev->y - my);
+    out->x1 = std::min((double)W, prev->x + prev->w + mx);
+    out->y1 = std::min((double)H, prev->y + prev->h + my);
+    out->lmin = std::max(0, prev->level - dlev);
+    out->lmax = prev->level + dlev;
+    return HOG_OK;
+}
+
+int hog_detect_roi(hog_ctx *ctx, const hog_frame *frames, const hog_roi *rois, int32_t n_frames,
+                   hog_det *dets, int32_t det_cap, int32_t *counts, void *stream_) {
+    if (!ctx) return HOG_EINVAL;
+    if (n_frames < 0 || (n_frames > 0 && (!frames || !rois)) || det_cap < 0 || (det_cap > 0 && !dets))
+        return fail(ctx, HOG_EINVAL, "bad frames/rois/dets arguments");
+    for (int i = 0; i < n_frames; i++) {
+        int rc = check_frame(ctx, &frames[i], true);
+        if (rc) return rc;
+        const hog_roi &r = rois[i];
+        if (!std::isfinite(r.x0) || !std::isfinite(r.y0) || !std::isfinite(r.x1) || !std::isfinite(r.y1))
+            return fail(ctx, HOG_EINVAL, "region of interest %d is not finite", i);
+    }
+    return detect_device(ctx, frames, n_frames, 0, dets, det_cap, nullptr, counts,
+                         (cudaStream_t)stream_, MODE_STAGED, false, rois);
 }
 
 int hog_set_corr_engine(hog_ctx *ctx, int32_t engine) {

@@ -117,6 +117,8 @@ struct FrameDesc {
     int32_t W, H, nlev, npos;
     int32_t frame;                    // batch-relative frame index
     int32_t scan_from;                // first position of a scanned level (earlier ones: no key)
+    int32_t has_roi;                  // 1: only windows in the per-level rectangles below
+    int32_t roi_u0[MAX_LEVELS], roi_u1[MAX_LEVELS], roi_v0[MAX_LEVELS], roi_v1[MAX_LEVELS];
     int32_t lev_w[MAX_LEVELS], lev_h[MAX_LEVELS];
     int32_t lev_nu[MAX_LEVELS], lev_nv[MAX_LEVELS];
     int32_t lev_pos[MAX_LEVELS + 1];

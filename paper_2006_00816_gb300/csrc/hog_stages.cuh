@@ -621,6 +621,17 @@ __host__ __device__ constexpr size_t nms_ws_bytes(int npos, bool in_smem) {
 // Positions a shared-memory workspace can index (16-bit list entries).
 constexpr int NMS_SMEM_MAX_NPOS = 65535;
 
+// Whether window position p of a frame is scanned: at or after the first
+// scanned level, and inside its level's rectangle when the frame has a
+// region of interest.  Other positions carry no key.
+__device__ __forceinline__ bool nms_scanned(const FrameDesc &fd, int p) {
+    if (!fd.has_roi) return p >= fd.scan_from;
+    int l = 0;
+    while (l + 1 < fd.nlev && p >= fd.lev_pos[l + 1]) l++;
+    const int idx = p - fd.lev_pos[l], u = idx / fd.lev_nv[l], v = idx - u * fd.lev_nv[l];
+    return u >= fd.roi_u0[l] && u < fd.roi_u1[l] && v >= fd.roi_v0[l] && v < fd.roi_v1[l];
+}
+
 template <bool SM, int NT, bool COH>
 __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *smem, int *flags,
                                           int *sh /* NT/32 + 4 ints of shared memory */) {
@@ -670,7 +681,7 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
         uint32_t h = NMS_NOKEY;
         if (p < npos) {
             // positions of levels that are not scanned carry no key
-            if (p >= fd.scan_from) h = (uint32_t)(ld_in<COH>(gkeys + p) >> 32);
+            if (nms_scanned(fd, p)) h = (uint32_t)(ld_in<COH>(gkeys + p) >> 32);
             khi[p] = h;
             state[p] = h != NMS_NOKEY ? NMS_ALIVE : NMS_DEAD;
             resume[p] = 0;

@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
         uint32_t h = NMS_NOKEY;
         if (i < nmine) {
             // positions of levels that are not scanned carry no key
-            if (lo + i >= fd.scan_from) h = (uint32_t)(__ldg(gkeys + lo + i) >> 32);
+            if (nms_scanned(fd, lo + i)) h = (uint32_t)(__ldg(gkeys + lo + i) >> 32);
             khi[i] = h;
             state[i] = h != NMS_NOKEY ? NMS_ALIVE : NMS_DEAD;
             resume[i] = 0;

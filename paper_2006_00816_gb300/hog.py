@@ -45,6 +45,27 @@ class Det(C.Structure):
                 ("y", C.c_double), ("w", C.c_double), ("h", C.c_double)]
 
 
+class Roi(C.Structure):
+    """hog_roi: frame-pixel box [x0, x1) x [y0, y1) for window centres and
+    the scanned level range [lmin, lmax]."""
+    _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("x1", C.c_double), ("y1", C.c_double),
+                ("lmin", C.c_int32), ("lmax", C.c_int32)]
+
+
+def roi_around(det, W: int, H: int, margin: float = 0.5, dlev: int = 1) -> Roi:
+    """hog_roi_around: region of interest around one detection record (a
+    DET_DTYPE row): its box grown by margin x its size on each side, levels
+    within dlev of its level."""
+    d = Det(int(det["frame"]), int(det["level"]), int(det["filter"]), int(det["u"]),
+            int(det["v"]), float(det["score"]), float(det["x"]), float(det["y"]),
+            float(det["w"]), float(det["h"]))
+    r = Roi()
+    rc = _lib.hog_roi_around(C.byref(d), int(W), int(H), float(margin), int(dlev), C.byref(r))
+    if rc:
+        raise HogError(rc, "hog_roi_around")
+    return r
+
+
 class StageStat(C.Structure):
     _fields_ = [("ms", C.c_double), ("launches", C.c_int64), ("units", C.c_int64)]
 
@@ -92,6 +113,8 @@ _SIGS = {
     "hog_features": (C.c_int, [_vp, _P(Frame), _vp, C.c_size_t, _P(Level), _i32, _P(_i32), _vp]),
     "hog_scores": (C.c_int, [_vp, _P(Frame), _vp, C.c_size_t, _P(Level), _i32, _P(_i32), _vp]),
     "hog_detect": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
+    "hog_detect_roi": (C.c_int, [_vp, _P(Frame), _P(Roi), _i32, _vp, _i32, _P(_i32), _vp]),
+    "hog_roi_around": (C.c_int, [_P(Det), _i32, _i32, C.c_double, _i32, _P(Roi)]),
     "hog_detect_host": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
     "hog_detect_batched": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
     "hog_set_batched_mode": (C.c_int, [_vp, _i32]),
@@ -365,6 +388,32 @@ class Detector:
         counts = np.zeros(max(n, 1), np.int32)
         rc = fn(self._h, arr, n, dets.ctypes.data_as(_vp), det_cap,
                 counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
+        self._check(rc, allow=(HOG_ECAPACITY,) if allow_capacity else ())
+        total = min(int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum()), det_cap)
+        if out is not None:
+            return dets[:total], counts[:n].copy()
+        return dets[:total].copy(), counts[:n].copy()
+
+    def detect_roi(self, frames, rois, det_cap=None, stream=None, allow_capacity=False, out=None):
+        """hog_detect_roi: as detect, each frame restricted to its region of
+        interest rois[i] = (x0, y0, x1, y1, lmin, lmax) or a Roi."""
+        n = len(frames)
+        assert len(rois) == n
+        arr = (Frame * max(n, 1))(*[_frame_of(f) for f in frames])
+        ra = (Roi * max(n, 1))(*[r if isinstance(r, Roi) else Roi(*[float(x) for x in r[:4]],
+                                                                     int(r[4]), int(r[5]))
+                                 for r in rois])
+        if out is not None:
+            assert out.dtype == DET_DTYPE and out.flags.c_contiguous
+            dets = out
+            det_cap = len(out) if det_cap is None else min(det_cap, len(out))
+        else:
+            if det_cap is None:
+                det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
+            dets = np.empty(max(det_cap, 1), DET_DTYPE)
+        counts = np.zeros(max(n, 1), np.int32)
+        rc = _lib.hog_detect_roi(self._h, arr, ra, n, dets.ctypes.data_as(_vp), det_cap,
+                                 counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
         self._check(rc, allow=(HOG_ECAPACITY,) if allow_capacity else ())
         total = min(int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum()), det_cap)
         if out is not None:
