@@ -267,6 +267,53 @@ int hog_detect_roi(hog_ctx *ctx, const hog_frame *frames, const hog_roi *rois, i
 int hog_roi_around(const hog_det *prev, int32_t W, int32_t H, double margin, int32_t dlev,
                    hog_roi *out);
 
+/* ---- Host landmark stage and the CPU/GPU pipeline (Sections 5.2, 5.3) ----
+ *
+ * The paper fits 68 facial landmarks to each detected face on the CPU with
+ * an ensemble of regression trees (Section 4.2) and pipelines that stage
+ * against the GPU detection of the next images (Table 8).  No trained model
+ * exists here, so hog_ert is a STAND-IN with the same structure and cost:
+ * `cascades` levels, each sampling `features` pixels at offsets from the
+ * current landmarks, and `trees` trees of depth `depth` per level whose
+ * splits compare two sampled pixels' difference with a threshold and whose
+ * leaves add a shape increment.  Every parameter is drawn from `seed`, so
+ * the landmarks carry no meaning; the stage loads the host like the real
+ * one.  From the six landmarks of each eye (68-point layout, 36-41 and
+ * 42-47) it reports the eye aspect ratio, the eyelid-closure signal. */
+typedef struct hog_ert hog_ert;   /* opaque, host memory */
+typedef struct {
+    int32_t landmarks;   /* 68 (fixed)                              */
+    int32_t cascades;    /* 15 levels (Section 4.2)                 */
+    int32_t trees;       /* 500 trees per level (Section 4.2)       */
+    int32_t depth;       /* 4 split levels per tree                 */
+    int32_t features;    /* 400 sampled pixels per level            */
+    uint64_t seed;
+} hog_ert_params;
+
+void hog_default_ert_params(hog_ert_params *p);
+/* HOG_EINVAL for landmarks != 68 or sizes out of range; HOG_ENOMEM. */
+int hog_ert_create(const hog_ert_params *p, hog_ert **out);
+void hog_ert_destroy(hog_ert *m);   /* NULL-safe */
+/* Fit one face (host): img (host, w x h, pitch bytes) and the face box
+ * (box->x, y, w, h in frame pixels); writes landmarks[68][2] (frame pixels)
+ * and, if ear is not NULL, ear[0..1] (the two eyes).  Deterministic. */
+int hog_ert_fit(const hog_ert *m, const uint8_t *img, int32_t w, int32_t h, int32_t pitch,
+                const hog_det *box, float *landmarks, float *ear);
+
+/* Detect faces on n_frames HOST frames in batches of `batch` (<= max_batch)
+ * and fit landmarks to each frame's best detection (highest score) with
+ * n_threads host threads.  pipelined = 0: per batch, copy in, detect, wait,
+ * then fit.  pipelined = 1: the detection of batch k+1 is enqueued before
+ * batch k is fitted, so the GPU and the host threads overlap (Table 8).
+ * Outputs (host): landmarks [n][68][2], ear [n][2], has_face [n] (0: no
+ * detection, landmarks and ear zero); *seconds (may be NULL) = wall time of
+ * the run without its one device allocation.  Both orders give the same
+ * outputs bit for bit.  Uses the context's batched mode; synchronises the
+ * stream. */
+int hog_pipeline_run(hog_ctx *ctx, const hog_ert *m, const hog_frame *frames, int32_t n_frames,
+                     int32_t batch, int32_t n_threads, int32_t pipelined, float *landmarks,
+                     float *ear, int32_t *has_face, double *seconds, void *stream);
+
 /* Same result as hog_detect, from frames in HOST memory: the frames are
  * copied to the device inside the call (pinned staging) and processed like
  * hog_detect_batched. */

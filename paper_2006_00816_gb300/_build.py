@@ -28,7 +28,10 @@ def nvcc() -> str:
 
 
 def _flags(verbose: bool):
+    # host code: no floating-point contraction, so it rounds alike on x86-64
+    # and aarch64 hosts
     f = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC] + ARCH
     if verbose:
         f += ["-Xptxas", "-v"]

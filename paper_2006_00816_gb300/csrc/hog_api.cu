@@ -1178,6 +1178,7 @@ int detect_results(hog_ctx *ctx, const int32_t **counts, const hog_det **dets) {
 }
 
 int ctx_max_dets(const hog_ctx *ctx) { return ctx->p.max_dets_per_frame; }
+int ctx_max_batch(const hog_ctx *ctx) { return ctx->p.max_batch; }
 int ctx_batched_mode(const hog_ctx *ctx) { return ctx->batched_mode; }
 void ctx_set_plan_cache(hog_ctx *ctx, int n) { ctx->plan_cache_max = n < 1 ? 1 : n; }
 const char *ctx_error(const hog_ctx *ctx) { return ctx->err.c_str(); }

@@ -240,6 +240,7 @@ int detect_enqueue(hog_ctx *ctx, const hog_frame *frames, int nb, cudaStream_t s
                    bool use_graph);
 int detect_results(hog_ctx *ctx, const int32_t **counts, const hog_det **dets);
 int ctx_max_dets(const hog_ctx *ctx);
+int ctx_max_batch(const hog_ctx *ctx);
 int ctx_batched_mode(const hog_ctx *ctx);
 void ctx_set_plan_cache(hog_ctx *ctx, int n);
 const char *ctx_error(const hog_ctx *ctx);

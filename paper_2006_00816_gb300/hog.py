@@ -66,6 +66,13 @@ def roi_around(det, W: int, H: int, margin: float = 0.5, dlev: int = 1) -> Roi:
     return r
 
 
+class ErtParams(C.Structure):
+    """hog_ert_params: the landmark stand-in's shape (68 landmarks, cascade
+    levels, trees per level, tree depth, sampled pixels per level, seed)."""
+    _fields_ = [("landmarks", C.c_int32), ("cascades", C.c_int32), ("trees", C.c_int32),
+                ("depth", C.c_int32), ("features", C.c_int32), ("seed", C.c_uint64)]
+
+
 class StageStat(C.Structure):
     _fields_ = [("ms", C.c_double), ("launches", C.c_int64), ("units", C.c_int64)]
 
@@ -114,6 +121,12 @@ _SIGS = {
     "hog_scores": (C.c_int, [_vp, _P(Frame), _vp, C.c_size_t, _P(Level), _i32, _P(_i32), _vp]),
     "hog_detect": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
     "hog_detect_roi": (C.c_int, [_vp, _P(Frame), _P(Roi), _i32, _vp, _i32, _P(_i32), _vp]),
+    "hog_default_ert_params": (None, [_P(ErtParams)]),
+    "hog_ert_create": (C.c_int, [_P(ErtParams), _P(_vp)]),
+    "hog_ert_destroy": (None, [_vp]),
+    "hog_ert_fit": (C.c_int, [_vp, _vp, _i32, _i32, _i32, _P(Det), _vp, _vp]),
+    "hog_pipeline_run": (C.c_int, [_vp, _vp, _P(Frame), _i32, _i32, _i32, _i32, _vp, _vp, _vp,
+                                   _P(C.c_double), _vp]),
     "hog_roi_around": (C.c_int, [_P(Det), _i32, _i32, C.c_double, _i32, _P(Roi)]),
     "hog_detect_host": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
     "hog_detect_batched": (C.c_int, [_vp, _P(Frame), _i32, _vp, _i32, _P(_i32), _vp]),
@@ -452,6 +465,69 @@ def default_server_config(**kw) -> ServerConfig:
             raise AttributeError(k)
         setattr(c, k, v)
     return c
+
+
+class Ert:
+    """Host landmark stage stand-in (hog_ert): regression-tree cascade with
+    seeded parameters, the paper's ERT structure and cost (Section 4.2); its
+    landmarks carry no meaning."""
+
+    def __init__(self, **params):
+        self.params = ErtParams()
+        _lib.hog_default_ert_params(C.byref(self.params))
+        for k, v in params.items():
+            setattr(self.params, k, v)
+        h = _vp()
+        rc = _lib.hog_ert_create(C.byref(self.params), C.byref(h))
+        if rc:
+            raise HogError(rc, "hog_ert_create")
+        self._h = h
+
+    def fit(self, img, det):
+        """Landmarks [68, 2] and EAR [2] for one host uint8 image and one
+        DET_DTYPE record."""
+        img = np.ascontiguousarray(img, dtype=np.uint8)
+        h, w = img.shape
+        d = Det(int(det["frame"]), int(det["level"]), int(det["filter"]), int(det["u"]),
+                int(det["v"]), float(det["score"]), float(det["x"]), float(det["y"]),
+                float(det["w"]), float(det["h"]))
+        lm = np.zeros((68, 2), np.float32)
+        ear = np.zeros(2, np.float32)
+        rc = _lib.hog_ert_fit(self._h, img.ctypes.data_as(_vp), w, h, w, C.byref(d),
+                              lm.ctypes.data_as(_vp), ear.ctypes.data_as(_vp))
+        if rc:
+            raise HogError(rc, "hog_ert_fit")
+        return lm, ear
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hog_ert_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pipeline_run(det, ert, frames, batch, n_threads, pipelined, stream=None):
+    """hog_pipeline_run on host uint8 frames (numpy arrays; pinned ones
+    copy asynchronously).  Returns (landmarks [n, 68, 2], ear [n, 2],
+    has_face [n], seconds)."""
+    n = len(frames)
+    keep = [np.ascontiguousarray(f, dtype=np.uint8) for f in frames]
+    arr = (Frame * max(n, 1))(*[Frame(f.ctypes.data, f.shape[1], f.shape[0], f.strides[0])
+                                  for f in keep])
+    lm = np.zeros((max(n, 1), 68, 2), np.float32)
+    ear = np.zeros((max(n, 1), 2), np.float32)
+    face = np.zeros(max(n, 1), np.int32)
+    sec = C.c_double(0.0)
+    rc = _lib.hog_pipeline_run(det._h, ert._h, arr, n, int(batch), int(n_threads), int(pipelined),
+                               lm.ctypes.data_as(_vp), ear.ctypes.data_as(_vp),
+                               face.ctypes.data_as(_vp), C.byref(sec), _stream_ptr(stream))
+    det._check(rc)
+    return lm[:n], ear[:n], face[:n], sec.value
 
 
 class Server:
