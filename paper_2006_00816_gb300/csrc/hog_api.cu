@@ -95,7 +95,8 @@ namespace {
 struct PlanLayout {
     size_t items = 0;
     size_t descs = 0, frames = 0, hist = 0, feat = 0, corr = 0, corrf = 0, tc = 0, tcr = 0, total = 0;
-    size_t bands = 0, cta_first = 0;
+    size_t bands = 0, cta_first = 0, pyrd = 0;
+    int npyrd = 0;
     std::vector<size_t> pyr;
     std::vector<int> npyr;
 };
@@ -368,6 +369,7 @@ struct PlanBuilder {
     std::vector<LevelDesc> descs;
     std::vector<FrameDesc> frames;
     std::vector<std::vector<Job>> pyr;   // per step (target level)
+    std::vector<Job> pyrd;               // direct-to-size levels (read the frame)
     std::vector<Job> hist, feat, corr;
     std::vector<Job> corrf;              // correlation jobs of the fused launch (8x16, 16x8 tiles)
     std::vector<Job> tc, tcr;            // tensor-core correlation: 128-cell tiles, 256-window blocks
@@ -386,15 +388,19 @@ struct PlanBuilder {
 void build_fused_items(PlanBuilder &pb) {
     const int nd = (int)pb.descs.size();
     std::vector<int> npyr(nd, 0), nhist(nd, 0), nfeat(nd, 0);
-    for (const auto &seg : pb.pyr)
-        for (const Job &j : seg) npyr[j.desc]++;
+    // every pyramid job: the 5/6 steps and the direct-to-size levels
+    std::vector<const std::vector<Job> *> pyr_lists;
+    for (const auto &seg : pb.pyr) pyr_lists.push_back(&seg);
+    pyr_lists.push_back(&pb.pyrd);
+    for (const auto *seg : pyr_lists)
+        for (const Job &j : *seg) npyr[j.desc]++;
     for (const Job &j : pb.hist) nhist[j.desc]++;
     for (const Job &j : pb.feat) nfeat[j.desc]++;
     struct Keyed { int depth, kind, desc, tile; FusedItem it; };
     std::vector<Keyed> v;
     v.reserve(pb.hist.size() + pb.feat.size() + pb.corrf.size() / 4 + 1024);
-    for (const auto &seg : pb.pyr)
-        for (const Job &j : seg) {
+    for (const auto *seg : pyr_lists)
+        for (const Job &j : *seg) {
             const LevelDesc &d = pb.descs[j.desc];
             FusedItem it{FUSED_PYR, j.desc, j.tile, -1, 0, 3 * j.desc + 0};
             // a 5/6 step waits for the previous level; a direct level reads the frame
@@ -533,7 +539,8 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         if (l >= 1 && !absent) {
             if ((int)pb.pyr.size() < l + 1) pb.pyr.resize(l + 1);
             const int nt = ((d.w + PYR_TX - 1) / PYR_TX) * ((d.h + PYR_TY - 1) / PYR_TY);
-            for (int k = 0; k < nt; k++) pb.pyr[l].push_back({di, k});
+            auto &list = d.dpow >= 2 ? pb.pyrd : pb.pyr[l];
+            for (int k = 0; k < nt; k++) list.push_back({di, k});
         }
         // histograms and features: for scanned levels, and for every level
         // whose features or scores the caller asked for (not for levels a
@@ -739,6 +746,8 @@ void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
         L.pyr[s] = take(pb.pyr[s].size() * sizeof(Job));
         L.npyr[s] = (int)pb.pyr[s].size();
     }
+    L.pyrd = take(pb.pyrd.size() * sizeof(Job));
+    L.npyrd = (int)pb.pyrd.size();
     L.hist = take(pb.hist.size() * sizeof(Job));
     L.feat = take(pb.feat.size() * sizeof(Job));
     L.corr = take(pb.corr.size() * sizeof(Job));
@@ -812,6 +821,7 @@ int upload_plan(hog_ctx *ctx, const PlanBuilder &pb, const PlanInfo &info, char 
     std::memcpy(h + L.frames, pb.frames.data(), pb.frames.size() * sizeof(FrameDesc));
     for (size_t s = 0; s < pb.pyr.size(); s++)
         std::memcpy(h + L.pyr[s], pb.pyr[s].data(), pb.pyr[s].size() * sizeof(Job));
+    std::memcpy(h + L.pyrd, pb.pyrd.data(), pb.pyrd.size() * sizeof(Job));
     std::memcpy(h + L.hist, pb.hist.data(), pb.hist.size() * sizeof(Job));
     std::memcpy(h + L.feat, pb.feat.data(), pb.feat.size() * sizeof(Job));
     std::memcpy(h + L.corr, pb.corr.data(), pb.corr.size() * sizeof(Job));
@@ -838,6 +848,11 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
     };
     CUDA_TRY(ctx, mark(0));
     int npyr = 0;
+    if (L.npyrd > 0) {
+        CUDA_TRY(ctx, launch_pyramid_direct(descs, reinterpret_cast<const Job *>(d + L.pyrd), L.npyrd,
+                                            stream));
+        npyr++;
+    }
     for (size_t s = 1; s < L.pyr.size(); s++) {
         CUDA_TRY(ctx, launch_pyramid(descs, reinterpret_cast<const Job *>(d + L.pyr[s]),
                                      L.npyr[s], stream));

@@ -270,6 +270,8 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // ---- launchers (each enqueues on `stream`; return cudaGetLastError()) ----
 cudaError_t launch_pyramid(const LevelDesc *descs, const Job *jobs, int njobs,
                            cudaStream_t stream);
+cudaError_t launch_pyramid_direct(const LevelDesc *descs, const Job *jobs, int njobs,
+                                  cudaStream_t stream);
 cudaError_t launch_hist(const LevelDesc *descs, const Job *jobs, int njobs,
                         cudaStream_t stream);
 cudaError_t launch_feat(const LevelDesc *descs, const Job *jobs, int njobs, float eps,

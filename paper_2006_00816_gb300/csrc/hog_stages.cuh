@@ -63,16 +63,21 @@ __device__ __noinline__ void pyramid_direct_tile(const LevelDesc &d, int x, int 
     }
 }
 
-template <bool COH>
+// DIRECT: the tile may be a direct-to-size level (d.dpow >= 2); the
+// stand-alone 5/6-step kernel leaves that path out (direct levels have a
+// launch of their own), the persistent fused kernel keeps it.
+template <bool COH, bool DIRECT = true>
 __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
     const int ntx = (d.w + PYR_TX - 1) / PYR_TX;
     const int tx = tile % ntx, ty = tile / ntx;
     const int x = tx * PYR_TX + (threadIdx.x & 31) * 4;
     const int y = ty * PYR_TY + (threadIdx.x >> 5);
     if (y >= d.h || x >= d.w) return;
-    if (d.dpow >= 2) {
-        pyramid_direct_tile<COH>(d, x, y);
-        return;
+    if constexpr (DIRECT) {
+        if (d.dpow >= 2) {
+            pyramid_direct_tile<COH>(d, x, y);
+            return;
+        }
     }
     const int Y = 12 * y + 1;
     const int y0 = Y / 10, fy = Y - 10 * (Y / 10);

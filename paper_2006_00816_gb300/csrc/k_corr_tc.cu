@@ -18,10 +18,15 @@
 // computed and never read.
 //
 // Precision: features and weights are split into fp16 hi + lo parts
-// (weights scaled by 2^6 first, so their lo parts stay normal); three MMAs
-// per K step (hi*hi, hi*lo, lo*hi) accumulate in FP32 in tensor memory.
-// The dropped lo*lo term and the split residues are below 2^-21 of each
-// product, so scores agree with the FP32 path to about 1e-6.
+// (weights scaled by 2^6 first, so their lo parts stay normal) and three
+// products are kept, hi*hi, hi*lo and lo*hi, accumulated in FP32 in tensor
+// memory.  The dropped lo*lo term and the split residues are below 2^-21 of
+// each product, so scores agree with the FP32 path to about 1e-6.  Per K
+// step two MMAs: A_hi x [W_hi | W_lo] (N = 2 N0, the two weight planes
+// side by side along N) into accumulator columns [D0 | D1], and A_lo x W_hi
+// (N = N0) into D0; the epilogue takes G = D0 + D1.  The MMA count, not the
+// MMA width, sets the tensor pipe's pace at these sizes (N0 = 64 for five
+// filters), so two wide MMAs beat three narrow ones.
 //
 // One CTA (4 warps) is persistent over 128-cell tiles of all levels of the
 // batch: it loads both B planes once, then per tile stages the hi and lo A
@@ -44,7 +49,11 @@ constexpr int TC_KSTEPS = 2 * WIN;         // K = 10 shifts x 32 channels, 16 pe
 constexpr long long TC_SPIN = 1ll << 24;   // mbarrier polls before giving up
 constexpr size_t TC_A_PLANE = (size_t)4 * TC_ROWS * 16;   // [4 groups][137 cells][16 B]
 
-__host__ __device__ constexpr int tc_cols(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : 128); }
+// TMEM columns for one accumulator pair [D0 | D1] of 2 N0 columns
+__host__ __device__ constexpr int tc_cols(int n) { return 2 * n <= 32 ? 32 : (2 * n <= 64 ? 64 : (2 * n <= 128 ? 128 : 256)); }
+// One weight plane (hi or lo); the two are interleaved per (shift, channel
+// group): [10 shifts][4 groups][hi, lo][N0][16 B], so hi and lo of one
+// (shift, group) are 2 N0 consecutive B rows.
 __host__ __device__ constexpr size_t tc_b_plane(int nf) { return (size_t)WIN * 4 * tc_n(nf) * 16; }
 // Dynamic shared memory: two B planes and two A planes (99.5 KB for up to 5
 // filters: two CTAs per SM, so one CTA's MMAs overlap the other's staging
@@ -134,7 +143,7 @@ __global__ void __launch_bounds__(TC_NT) corr_tc_kernel(const LevelDesc *__restr
     constexpr int N = tc_n(NF), COLS = tc_cols(N);
     constexpr size_t BP = tc_b_plane(NF);
     extern __shared__ __align__(128) unsigned char sm[];
-    unsigned char *Bs = sm;                       // [hi, lo][10 shifts][4 groups][N][16 B]
+    unsigned char *Bs = sm;                       // [10 shifts][4 groups][hi, lo][N][16 B]
     unsigned char *As = sm + 2 * BP;              // [hi, lo][4 groups][137 cells][16 B]
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
@@ -161,7 +170,7 @@ __global__ void __launch_bounds__(TC_NT) corr_tc_kernel(const LevelDesc *__restr
     fence_after();
     const uint32_t tbase = tslot;
     const uint32_t a_s = smem_addr(As), b_s = smem_addr(Bs);
-    constexpr uint32_t IDESC = tc_idesc(N);
+    constexpr uint32_t IDESC = tc_idesc(N), IDESC2 = tc_idesc(2 * N);
     uint32_t parity = 0;
 
     for (int jid = blockIdx.x; jid < njobs; jid += gridDim.x) {
@@ -189,14 +198,12 @@ __global__ void __launch_bounds__(TC_NT) corr_tc_kernel(const LevelDesc *__restr
                 const int b = s >> 1, half = s & 1;
                 // channel groups 2*half, 2*half + 1 of cells b .. b + 127
                 const uint32_t aoff = (uint32_t)((2 * half) * TC_ROWS + b) * 16;
-                const uint32_t boff = (uint32_t)((b * 4 + 2 * half) * N) * 16;
+                const uint32_t boff = (uint32_t)((b * 4 + 2 * half) * 2 * N) * 16;
                 const uint64_t ah = sdesc(a_s + aoff, TC_ROWS * 16, 128);
                 const uint64_t al = sdesc(a_s + (uint32_t)TC_A_PLANE + aoff, TC_ROWS * 16, 128);
-                const uint64_t bh = sdesc(b_s + boff, N * 16, 128);
-                const uint64_t bl = sdesc(b_s + (uint32_t)BP + boff, N * 16, 128);
-                mma_f16(tbase, ah, bh, IDESC, s > 0 ? 1u : 0u);
-                mma_f16(tbase, ah, bl, IDESC, 1u);
-                mma_f16(tbase, al, bh, IDESC, 1u);
+                const uint64_t bhl = sdesc(b_s + boff, 2 * N * 16, 128);   // [W_hi | W_lo]
+                mma_f16(tbase, ah, bhl, IDESC2, s > 0 ? 1u : 0u);        // D0 += hh, D1 += hl
+                mma_f16(tbase, al, bhl, IDESC, 1u);                      // D0 += lh
             }
             mma_commit(mb);
         }
@@ -219,12 +226,16 @@ __global__ void __launch_bounds__(TC_NT) corr_tc_kernel(const LevelDesc *__restr
         float *g = d.gmat;
 #pragma unroll 1
         for (int c0 = 0; c0 < N; c0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
+            uint32_t r0[16], r1[16];
+            const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            tmem_ld16_nowait(ta, r0);
+            tmem_ld16_nowait(ta + N, r1);
+            tmem_wait_ld();
             if (cell < ncells) {
 #pragma unroll
                 for (int j = 0; j < 16; j++)
-                    if (c0 + j < WIN * NF) g[(size_t)(c0 + j) * ncells + cell] = __uint_as_float(r[j]);
+                    if (c0 + j < WIN * NF)
+                        g[(size_t)(c0 + j) * ncells + cell] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
             }
         }
         fence_before();
@@ -274,9 +285,9 @@ __global__ void __launch_bounds__(256) corr_tc_reduce_kernel(const LevelDesc *__
 }
 
 // B planes from the filters (host layout [f][a][b][c], 31 channels):
-// element (n = a*F + f, k = b*32 + c) at ((b*4 + c/8)*N + n)*8 + c%8 of
-// each plane, value 64*W split into fp16 hi and lo; zero for n >= 10 F and
-// for channel 31.
+// element (n = a*F + f, k = b*32 + c) of plane p (0 hi, 1 lo) at
+// (((b*4 + c/8)*2 + p)*N + n)*8 + c%8, value 64*W split into fp16 hi and
+// lo; zero for n >= 10 F and for channel 31.
 template <int NF>
 __global__ void corr_tc_weights_kernel(const float *__restrict__ w, int nf_real, uint16_t *wb) {
     constexpr int N = tc_n(NF);
@@ -291,8 +302,10 @@ __global__ void corr_tc_weights_kernel(const float *__restrict__ w, int nf_real,
         x = 64.0f * w[(((size_t)f * WIN + a) * WIN + b) * NFEAT + c];
     const __half hi = __float2half_rn(x);
     const __half lo = __float2half_rn(x - __half2float(hi));
-    wb[idx] = __half_as_ushort(hi);
-    wb[PLANE + idx] = __half_as_ushort(lo);
+    // [shift b][group][hi, lo][N][8 halves]
+    const size_t o = ((size_t)bg * 2 * N + n) * 8 + c8;
+    wb[o] = __half_as_ushort(hi);
+    wb[o + (size_t)N * 8] = __half_as_ushort(lo);
 }
 
 // ===========================================================================
@@ -332,10 +345,11 @@ constexpr int tf_ring_max() {
     return m;
 }
 constexpr int TF_RING = tf_ring_max();
-// TMEM columns per accumulator: a power of two >= N (accumulator 1 starts there)
-__host__ __device__ constexpr int tf_acc(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : 128); }
+// TMEM columns per accumulator pair [D0 | D1] (2 N): a power of two
+// (accumulator pair 1 starts there)
+__host__ __device__ constexpr int tf_acc(int n) { return tc_cols(n); }
 __host__ __device__ constexpr int tf_alloc(int cols) {
-    return cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : 256));
+    return cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
 }
 __host__ __device__ constexpr size_t tf_smem(int nf) {
     return 2 * tc_b_plane(nf) + TF_STAGES * TF_A_STAGE + sizeof(float) * (size_t)nf * TF_RING;
@@ -392,6 +406,8 @@ __device__ __forceinline__ int band_run(const TcBand &b, int cx, int q, int n, i
 }
 }  // namespace
 
+static_assert(2 * tf_acc(tc_n(8)) <= 512 && 2 * tc_n(8) <= 256, "TMEM / MMA width for 8 filters");
+
 template <int NF>
 __global__ void __launch_bounds__(TF_NT, 1) corr_tcf_kernel(const LevelDesc *__restrict__ descs,
                                                            const TcBand *__restrict__ bands,
@@ -401,7 +417,7 @@ __global__ void __launch_bounds__(TF_NT, 1) corr_tcf_kernel(const LevelDesc *__r
     constexpr int N = tc_n(NF), ACC = tf_acc(N), COLS = tf_alloc(2 * ACC);
     constexpr size_t BP = tc_b_plane(NF);
     extern __shared__ __align__(128) unsigned char sm[];
-    unsigned char *Bs = sm;                                  // [hi, lo][10][4][N][16 B]
+    unsigned char *Bs = sm;                                  // [10][4][hi, lo][N][16 B]
     unsigned char *As = sm + 2 * BP;                         // [stage][hi, lo][4][137][16 B]
     float *ring = reinterpret_cast<float *>(As + TF_STAGES * TF_A_STAGE);   // [NF][TF_RING]
     __shared__ __align__(8) uint64_t bar_full[TF_STAGES], bar_empty[TF_STAGES];
@@ -488,7 +504,7 @@ __global__ void __launch_bounds__(TF_NT, 1) corr_tcf_kernel(const LevelDesc *__r
     } else if (warp == 4) {
         // ---- MMA issuer
         int stage = 0, use = 0, acc = 0, ause = 0;
-        constexpr uint32_t IDESC = tc_idesc(N);
+        constexpr uint32_t IDESC = tc_idesc(N), IDESC2 = tc_idesc(2 * N);
         const uint32_t b_s = smem_addr(Bs);
         bool ok = true;
         for (int bi = first; bi < last && ok; bi++) {
@@ -505,18 +521,17 @@ __global__ void __launch_bounds__(TF_NT, 1) corr_tcf_kernel(const LevelDesc *__r
                     // >> 4) of a base descriptor plus compile-time offsets in
                     // 16-byte units (shared addresses < 256 KB: no carry)
                     const uint64_t ah0 = sdesc(smem_addr(As + stage * TF_A_STAGE), TC_ROWS * 16, 128);
-                    const uint64_t bh0 = sdesc(b_s, N * 16, 128);
+                    const uint64_t b0 = sdesc(b_s, 2 * N * 16, 128);
                     const uint32_t d_t = tbase + (uint32_t)(acc * ACC);
 #pragma unroll
                     for (int s = 0; s < TC_KSTEPS; s++) {
                         const int bsh = s >> 1, half = s & 1;
                         const uint64_t aoff = (uint64_t)((2 * half) * TC_ROWS + bsh);
-                        const uint64_t boff = (uint64_t)((bsh * 4 + 2 * half) * N);
+                        const uint64_t boff = (uint64_t)((bsh * 4 + 2 * half) * 2 * N);
                         const uint64_t ah = ah0 + aoff, al = ah0 + (TC_A_PLANE >> 4) + aoff;
-                        const uint64_t bh = bh0 + boff, bl = bh0 + (BP >> 4) + boff;
-                        mma_f16(d_t, ah, bh, IDESC, s > 0 ? 1u : 0u);
-                        mma_f16(d_t, ah, bl, IDESC, 1u);
-                        mma_f16(d_t, al, bh, IDESC, 1u);
+                        const uint64_t bhl = b0 + boff;                       // [W_hi | W_lo]
+                        mma_f16(d_t, ah, bhl, IDESC2, s > 0 ? 1u : 0u);     // D0 += hh, D1 += hl
+                        mma_f16(d_t, al, bhl, IDESC, 1u);                   // D0 += lh
                     }
                     mma_commit(smem_addr(&bar_empty[stage]));   // A stage free once read
                     mma_commit(smem_addr(&bar_tfull[acc]));     // accumulator ready
@@ -545,15 +560,18 @@ __global__ void __launch_bounds__(TF_NT, 1) corr_tcf_kernel(const LevelDesc *__r
                     constexpr int NL = (WIN * NF + 15) / 16;
                     const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * ACC);
 #pragma unroll
-                    uint32_t r[NL][16];
+                    // G = D0 + D1, 16 columns at a time
 #pragma unroll
-                    for (int c = 0; c < NL; c++) tmem_ld16_nowait(ta + 16 * c, r[c]);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int c = 0; c < NL; c++)
+                    for (int c = 0; c < NL; c++) {
+                        uint32_t r0[16], r1[16];
+                        tmem_ld16_nowait(ta + 16 * c, r0);
+                        tmem_ld16_nowait(ta + N + 16 * c, r1);
+                        tmem_wait_ld();
 #pragma unroll
                         for (int j = 0; j < 16; j++)
-                            if (16 * c + j < WIN * NF) G[16 * c + j] = __uint_as_float(r[c][j]);
+                            if (16 * c + j < WIN * NF)
+                                G[16 * c + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    }
                 }
                 fence_before();
                 __syncwarp();

@@ -15,13 +15,32 @@ namespace hogk {
 __global__ void __launch_bounds__(256) pyramid_step_kernel(const LevelDesc *__restrict__ descs,
                                                            const Job *__restrict__ jobs) {
     const Job jb = jobs[blockIdx.x];
-    pyramid_tile<false>(descs[jb.desc], jb.tile);
+    pyramid_tile<false, false>(descs[jb.desc], jb.tile);
+}
+
+// Direct-to-size levels (hog_params.direct_first): read the frame, so they
+// run before the 5/6 steps.
+__global__ void __launch_bounds__(256) pyramid_direct_kernel(const LevelDesc *__restrict__ descs,
+                                                             const Job *__restrict__ jobs) {
+    const Job jb = jobs[blockIdx.x];
+    const LevelDesc &d = descs[jb.desc];
+    const int ntx = (d.w + PYR_TX - 1) / PYR_TX;
+    const int x = (jb.tile % ntx) * PYR_TX + (threadIdx.x & 31) * 4;
+    const int y = (jb.tile / ntx) * PYR_TY + (threadIdx.x >> 5);
+    if (y < d.h && x < d.w) pyramid_direct_tile<false>(d, x, y);
 }
 
 cudaError_t launch_pyramid(const LevelDesc *descs, const Job *jobs, int njobs,
                            cudaStream_t stream) {
     if (njobs <= 0) return cudaSuccess;
     pyramid_step_kernel<<<njobs, 256, 0, stream>>>(descs, jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pyramid_direct(const LevelDesc *descs, const Job *jobs, int njobs,
+                                  cudaStream_t stream) {
+    if (njobs <= 0) return cudaSuccess;
+    pyramid_direct_kernel<<<njobs, 256, 0, stream>>>(descs, jobs);
     return cudaGetLastError();
 }
 
