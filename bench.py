@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--frames", type=int, default=1000)
-    ap.add_argument("--batch", type=int, default=250)
+    ap.add_argument("--batch", type=int, default=1000)
     ap.add_argument("--plain-frames", type=int, default=200)
     ap.add_argument("--cpu-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")

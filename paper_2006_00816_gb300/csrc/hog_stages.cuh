@@ -296,15 +296,23 @@ __device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float ep
     const int j0 = (tile % ntx) * FEAT_TX, i0 = (tile / ntx) * FEAT_TY;
     const int t = threadIdx.x;
 
-    for (int k = t; k < HY * HX * NBIN; k += NT) {
-        const int r = k / (HX * NBIN);
-        const int rem = k - r * HX * NBIN;
-        const int c = rem / NBIN, b = rem - c * NBIN;
+    // stage the tile's cells and their one-cell halo, one cell (18 floats,
+    // 72 bytes: nine 8-byte loads) per thread and step; zero outside the grid
+    for (int k = t; k < HY * HX; k += NT) {
+        const int r = k / HX, c = k - r * HX;
         const int i = i0 - 1 + r, j = j0 - 1 + c;
-        float v = 0.0f;
-        if (i >= 0 && i < d.cy && j >= 0 && j < d.cx)
-            v = ld_in<COH>(d.hist + ((size_t)i * d.cx + j) * NBIN + b);
-        hS[(r * HX + c) * CS + b] = v;
+        float *dst = hS + k * CS;
+        if (i >= 0 && i < d.cy && j >= 0 && j < d.cx) {
+            const float2 *src = reinterpret_cast<const float2 *>(d.hist + ((size_t)i * d.cx + j) * NBIN);
+            float2 v[NBIN / 2];
+#pragma unroll
+            for (int q = 0; q < NBIN / 2; q++) v[q] = ld_in<COH>(src + q);
+#pragma unroll
+            for (int q = 0; q < NBIN / 2; q++) { dst[2 * q] = v[q].x; dst[2 * q + 1] = v[q].y; }
+        } else {
+#pragma unroll
+            for (int b = 0; b < NBIN; b++) dst[b] = 0.0f;
+        }
     }
     __syncthreads();
     for (int k = t; k < HY * HX; k += NT) {
