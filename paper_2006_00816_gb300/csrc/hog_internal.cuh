@@ -20,7 +20,7 @@ constexpr int MAX_LEVELS = HOG_MAX_LEVELS;
 constexpr int MAXN = 192;           // suppression neighbours per window position (<= 150 seen at IoU 0.45)
 
 // Tile shapes of the plain kernels.
-constexpr int PYR_TX = 128, PYR_TY = 8;          // output pixels per CTA (256 threads)
+constexpr int PYR_TX = 160, PYR_TY = 32;         // output pixels per CTA (256 threads x 20)
 constexpr int HIST_BX = 16, HIST_BY = 16;        // 8x8-pixel blocks per CTA (256 threads)
 constexpr int HIST_TX = HIST_BX - 1, HIST_TY = HIST_BY - 1;   // 15 x 15 cells per CTA
 constexpr int FEAT_TX = 32, FEAT_TY = 8;         // cells per CTA (256 threads)

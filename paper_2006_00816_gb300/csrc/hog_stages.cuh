@@ -27,11 +27,21 @@ __device__ __forceinline__ T ld_in(const T *p) {
 // Pyramid (Section 4.1.1, first step; Section 5.1, image-scaling kernel).
 // Output pixel (x, y) of level l+1 samples level l at ((12x+1)/10,
 // (12y+1)/10) with exact weights in tenths, rounded half up (integer-exact).
-// 256 threads: 4 output pixels each, tile PYR_TX x PYR_TY.
+//
+// The mapping repeats every 5 output pixels: x = 5k + i samples source
+// column 6k + i with weight fx = 2i + 1 tenths.  So 20 consecutive outputs
+// x = 20k .. 20k+19 read exactly the 24 source bytes 24k .. 24k+23 of each
+// of their two source rows: six aligned 32-bit loads per row, byte offsets
+// and weights known at compile time, five 32-bit stores.  Tile PYR_TX x
+// PYR_TY = 160 x 32 outputs, 256 threads (8 x 20 columns, 32 rows); edge
+// groups and unaligned sources (a caller's frame) take the per-pixel path.
+//
 // Direct-to-size level (Section 6.6, future work): level s straight from
 // the frame with the ratio (6/5)^s, source coordinate ((2x+1) 6^s - 5^s) /
 // (2 5^s), weights in units of 1/(2 5^s), rounded half up; 64-bit integer
 // arithmetic, exact.  s = d.dpow (2..8).
+constexpr int PYR_GROUP = 20;   // output pixels per thread
+
 template <bool COH>
 __device__ __noinline__ void pyramid_direct_tile(const LevelDesc &d, int x, int y) {
     long long p6 = 1, p5 = 1;
@@ -41,26 +51,21 @@ __device__ __noinline__ void pyramid_direct_tile(const LevelDesc &d, int x, int 
     const long long y0 = Y / D, fy = Y - D * y0;
     const uint8_t *r0 = d.src + (size_t)y0 * d.spitch;
     const uint8_t *r1 = r0 + d.spitch;
-    uint32_t packed = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int xx = x + k;
-        if (xx < d.w) {
-            const long long X = (2 * (long long)xx + 1) * p6 - p5;
-            const long long x0 = X / D, fx = X - D * x0;
-            const long long p00 = ld_in<COH>(r0 + x0), p10 = ld_in<COH>(r0 + x0 + 1);
-            const long long p01 = ld_in<COH>(r1 + x0), p11 = ld_in<COH>(r1 + x0 + 1);
-            const long long acc = (D - fx) * (D - fy) * p00 + fx * (D - fy) * p10 +
-                                  (D - fx) * fy * p01 + fx * fy * p11;
-            packed |= (uint32_t)((acc + D * D / 2) / (D * D)) << (8 * k);
-        }
+    uint8_t *out = d.dst + (size_t)y * d.pitch;
+    for (int xx = x; xx < x + PYR_GROUP && xx < d.w; xx++) {
+        const long long X = (2 * (long long)xx + 1) * p6 - p5;
+        const long long x0 = X / D, fx = X - D * x0;
+        const long long p00 = ld_in<COH>(r0 + x0), p10 = ld_in<COH>(r0 + x0 + 1);
+        const long long p01 = ld_in<COH>(r1 + x0), p11 = ld_in<COH>(r1 + x0 + 1);
+        const long long acc = (D - fx) * (D - fy) * p00 + fx * (D - fy) * p10 +
+                              (D - fx) * fy * p01 + fx * fy * p11;
+        out[xx] = (uint8_t)((acc + D * D / 2) / (D * D));
     }
-    uint8_t *out = d.dst + (size_t)y * d.pitch + x;
-    if (x + 3 < d.w) {
-        *reinterpret_cast<uint32_t *>(out) = packed;
-    } else {
-        for (int k = 0; k < 4 && x + k < d.w; k++) out[k] = (uint8_t)(packed >> (8 * k));
-    }
+}
+
+// Byte o (compile-time) of the 24-byte window held in six words.
+__device__ __forceinline__ int pyr_byte(const uint32_t (&w)[6], int o) {
+    return (int)((w[o >> 2] >> (8 * (o & 3))) & 0xffu);
 }
 
 // DIRECT: the tile may be a direct-to-size level (d.dpow >= 2); the
@@ -70,8 +75,8 @@ template <bool COH, bool DIRECT = true>
 __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
     const int ntx = (d.w + PYR_TX - 1) / PYR_TX;
     const int tx = tile % ntx, ty = tile / ntx;
-    const int x = tx * PYR_TX + (threadIdx.x & 31) * 4;
-    const int y = ty * PYR_TY + (threadIdx.x >> 5);
+    const int x = tx * PYR_TX + (threadIdx.x & 7) * PYR_GROUP;
+    const int y = ty * PYR_TY + (threadIdx.x >> 3);
     if (y >= d.h || x >= d.w) return;
     if constexpr (DIRECT) {
         if (d.dpow >= 2) {
@@ -80,28 +85,42 @@ __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
         }
     }
     const int Y = 12 * y + 1;
-    const int y0 = Y / 10, fy = Y - 10 * (Y / 10);
+    const int y0 = Y / 10, fy = Y - 10 * y0;
+    const int wy0 = 10 - fy, wy1 = fy;
     const uint8_t *r0 = d.src + (size_t)y0 * d.spitch;
     const uint8_t *r1 = r0 + d.spitch;
-    uint32_t packed = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int xx = x + k;
-        if (xx < d.w) {
-            const int X = 12 * xx + 1;
-            const int x0 = X / 10, fx = X - 10 * (X / 10);
-            const int p00 = ld_in<COH>(r0 + x0), p10 = ld_in<COH>(r0 + x0 + 1);
-            const int p01 = ld_in<COH>(r1 + x0), p11 = ld_in<COH>(r1 + x0 + 1);
-            const int acc = (10 - fx) * (10 - fy) * p00 + fx * (10 - fy) * p10 +
-                            (10 - fx) * fy * p01 + fx * fy * p11;
-            packed |= (uint32_t)((acc + 50) / 100) << (8 * k);
-        }
-    }
     uint8_t *out = d.dst + (size_t)y * d.pitch + x;
-    if (x + 3 < d.w) {
-        *reinterpret_cast<uint32_t *>(out) = packed;   // pitch and x are multiples of 4
-    } else {
-        for (int k = 0; k < 4 && x + k < d.w; k++) out[k] = (uint8_t)(packed >> (8 * k));
+    const int sx = (x / 5) * 6;   // first source column of the group
+    const bool fast = x + PYR_GROUP <= d.w && sx + 24 <= d.sw &&
+                      ((reinterpret_cast<uintptr_t>(r0 + sx) | (uintptr_t)d.spitch) & 3u) == 0;
+    if (fast) {
+        uint32_t a[6], b[6];
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+            a[q] = ld_in<COH>(reinterpret_cast<const uint32_t *>(r0 + sx) + q);
+            b[q] = ld_in<COH>(reinterpret_cast<const uint32_t *>(r1 + sx) + q);
+        }
+        uint32_t packed[5] = {0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int i = 0; i < PYR_GROUP; i++) {
+            const int o = (12 * i + 1) / 10, fx = (12 * i + 1) % 10;   // constants
+            const int top = (10 - fx) * pyr_byte(a, o) + fx * pyr_byte(a, o + 1);
+            const int bot = (10 - fx) * pyr_byte(b, o) + fx * pyr_byte(b, o + 1);
+            const int acc = wy0 * top + wy1 * bot;
+            packed[i >> 2] |= (uint32_t)((acc + 50) / 100) << (8 * (i & 3));
+        }
+#pragma unroll
+        for (int q = 0; q < 5; q++) reinterpret_cast<uint32_t *>(out)[q] = packed[q];   // x, pitch: 4 | .
+        return;
+    }
+    for (int i = 0; i < PYR_GROUP && x + i < d.w; i++) {
+        const int X = 12 * (x + i) + 1;
+        const int x0 = X / 10, fx = X - 10 * x0;
+        const int p00 = ld_in<COH>(r0 + x0), p10 = ld_in<COH>(r0 + x0 + 1);
+        const int p01 = ld_in<COH>(r1 + x0), p11 = ld_in<COH>(r1 + x0 + 1);
+        const int acc = (10 - fx) * (10 - fy) * p00 + fx * (10 - fy) * p10 +
+                        (10 - fx) * fy * p01 + fx * fy * p11;
+        out[i] = (uint8_t)((acc + 50) / 100);
     }
 }
 

@@ -7,7 +7,8 @@
 //   ((10-fx)(10-fy) p00 + fx(10-fy) p10 + (10-fx) fy p01 + fx fy p11 + 50) / 100
 // (integer division) is the exact bilinear sample rounded half up, so the
 // pyramid is integer-exact: no texture unit, no float rounding.
-// For x < floor(5w/6), x0 + 1 <= w - 1, so no clamping is needed.
+// For x < floor(5w/6), x0 + 1 <= w - 1, so no clamping is needed.  Each
+// thread computes 20 consecutive outputs (pyramid_tile in hog_stages.cuh).
 #include "hog_stages.cuh"
 
 namespace hogk {
@@ -25,8 +26,8 @@ __global__ void __launch_bounds__(256) pyramid_direct_kernel(const LevelDesc *__
     const Job jb = jobs[blockIdx.x];
     const LevelDesc &d = descs[jb.desc];
     const int ntx = (d.w + PYR_TX - 1) / PYR_TX;
-    const int x = (jb.tile % ntx) * PYR_TX + (threadIdx.x & 31) * 4;
-    const int y = (jb.tile / ntx) * PYR_TY + (threadIdx.x >> 5);
+    const int x = (jb.tile % ntx) * PYR_TX + (threadIdx.x & 7) * PYR_GROUP;
+    const int y = (jb.tile / ntx) * PYR_TY + (threadIdx.x >> 3);
     if (y < d.h && x < d.w) pyramid_direct_tile<false>(d, x, y);
 }
 
