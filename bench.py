@@ -43,8 +43,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # correlation stage for one 250-frame 640x480 batch, per engine, from one ncu
 # capture (--set full, 250-frame batch); valid while k_corr_tc.cu is the
 # source captured (first 16 hex digits of its SHA-256); None: not captured
-CORR_TC_TRAFFIC_250 = {1: 479.732224e6 + 20.142848e6, 2: None}
-CORR_TC_SOURCE_SHA = "315e1f729aa039ff"
+CORR_TC_TRAFFIC_250 = {1: 479.547648e6 + 20.450816e6, 2: None}
+CORR_TC_SOURCE_SHA = "2b41c1116f1dad71"
 PAPER_CONTEXT = {"ms_per_frame": 0.333, "frames_per_s": 3003,
                  "hardware": "NVIDIA Titan X (Pascal), 16 frames/launch, incl. transfers"}
 

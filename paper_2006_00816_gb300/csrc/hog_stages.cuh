@@ -42,8 +42,45 @@ __device__ __forceinline__ T ld_in(const T *p) {
 // arithmetic, exact.  s = d.dpow (2..8).
 constexpr int PYR_GROUP = 20;   // output pixels per thread
 
+// n / d for 0 <= n < 2^31, 0 < d < 2^31: an FP32 reciprocal estimate
+// (within a few units of the quotient), then corrected to the exact floor.
+__device__ __forceinline__ unsigned udiv_exact(unsigned n, unsigned d, float rd) {
+    unsigned q = __float2uint_rz((float)n * rd);
+    while (q > 0 && q * d > n) q--;          // q*d <= n < 2^31: no wrap
+    while ((q + 1) * d <= n) q++;
+    return q;
+}
+
 template <bool COH>
 __device__ __noinline__ void pyramid_direct_tile(const LevelDesc &d, int x, int y) {
+    if (d.dpow <= 4) {
+        // 32-bit exact: X < 2^31 for widths up to 16384 (6^4 (2x+1) <
+        // 4.3e7), D^2 * 255 * 4 < 2^31 (D = 2 * 5^4 = 1250)
+        unsigned p6 = 1, p5 = 1;
+        for (int k = 0; k < d.dpow; k++) { p6 *= 6; p5 *= 5; }
+        const unsigned D = 2 * p5, D2 = D * D;
+        const float rD = 1.0f / (float)D, rD2 = 1.0f / (float)D2;
+        const unsigned Y = (2 * (unsigned)y + 1) * p6 - p5;
+        const unsigned y0 = udiv_exact(Y, D, rD), fy = Y - D * y0;
+        const uint8_t *r0 = d.src + (size_t)y0 * d.spitch;
+        const uint8_t *r1 = r0 + d.spitch;
+        uint8_t *out = d.dst + (size_t)y * d.pitch;
+        // X advances by 2 * 6^s per output pixel: step x0 and fx without a
+        // division per pixel
+        const unsigned X0 = (2 * (unsigned)x + 1) * p6 - p5;
+        unsigned x0 = udiv_exact(X0, D, rD), fx = X0 - D * x0;
+        const unsigned qs = (2 * p6) / D, rs = (2 * p6) - D * qs;
+        for (int xx = x; xx < x + PYR_GROUP && xx < d.w; xx++) {
+            const unsigned p00 = ld_in<COH>(r0 + x0), p10 = ld_in<COH>(r0 + x0 + 1);
+            const unsigned p01 = ld_in<COH>(r1 + x0), p11 = ld_in<COH>(r1 + x0 + 1);
+            const unsigned acc = (D - fy) * ((D - fx) * p00 + fx * p10) + fy * ((D - fx) * p01 + fx * p11);
+            out[xx] = (uint8_t)udiv_exact(acc + D2 / 2, D2, rD2);
+            x0 += qs;
+            fx += rs;
+            if (fx >= D) { fx -= D; x0++; }
+        }
+        return;
+    }
     long long p6 = 1, p5 = 1;
     for (int k = 0; k < d.dpow; k++) { p6 *= 6; p5 *= 5; }
     const long long D = 2 * p5;
