@@ -679,7 +679,7 @@ def main():
         ms, dets = [], 0
         for _ in range(k):
             t0 = time.perf_counter()
-            d, c = det.detect(frames, out=out_np, batched=batched)
+            d, c = det.detect(frames_dev, out=out_np, batched=batched)
             ms.append((time.perf_counter() - t0) * 1e3)
             dets += int(c.sum())
         return ms, dets
@@ -753,12 +753,12 @@ def main():
 
     # ---- e2e: host frames in pinned memory through hog_detect_host
     for _ in range(max(1, args.warmup // 2)):
-        det.detect_host(host_frames, out=out_np)
+        det.detect_host(pinned_np, out=out_np)
     barrier()
     t0 = time.perf_counter()
     e2e_dets = 0
     for _ in range(args.steps):
-        d, c = det.detect_host(host_frames, out=out_np)
+        d, c = det.detect_host(pinned_np, out=out_np)
         e2e_dets += int(c.sum())
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     e2e_fps = whole_job_rate(ws, nfr * args.steps, e2e_s)

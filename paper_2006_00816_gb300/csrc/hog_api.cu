@@ -174,6 +174,9 @@ struct hog_ctx {
     size_t cells_slot = 0, fh_slot = 0, gm_slot = 0;
     int plan_cache_max = 8;         // cached batch plans (a server raises it)
     cudaStream_t cap_stream = nullptr;
+    // hog_detect_host: copy stream and events of the double-buffered staging
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_done[2] = {nullptr, nullptr}, stage_free = nullptr;
     // training arena (hog_backward), grown on demand
     char *d_train = nullptr;
     size_t train_cap = 0;
@@ -287,6 +290,10 @@ void free_ctx(hog_ctx *ctx) {
     F(ctx->d_train);
     F(ctx->d_wuser); F(ctx->d_wtc); F(ctx->d_fh); F(ctx->d_gm);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (cudaEvent_t e : ctx->copy_done)
+        if (e) cudaEventDestroy(e);
+    if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
     for (Geometry *g : ctx->geoms) {
         F(g->d_nbr);
         F(g->d_cnt);
@@ -1553,6 +1560,10 @@ int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog
     if (!ctx) return HOG_EINVAL;
     if (n_frames < 0 || (n_frames > 0 && !frames) || det_cap < 0 || (det_cap > 0 && !dets))
         return fail(ctx, HOG_EINVAL, "bad frames/dets arguments");
+    for (int i = 0; i < n_frames; i++) {
+        int rc = check_frame(ctx, &frames[i], false);
+        if (rc) return rc;
+    }
     cudaStream_t stream = (cudaStream_t)stream_;
     const size_t fbytes = (size_t)ctx->p.max_w * ctx->p.max_h;
     if (!ctx->d_stage) {
@@ -1560,40 +1571,94 @@ int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog
         CUDA_TRY(ctx, cudaMalloc(&ctx->d_stage, ctx->stage_cap));
         CUDA_TRY(ctx, cudaMallocHost(&ctx->h_stage, ctx->stage_cap));
     }
-    int total = 0;
-    bool truncated = false;
+    if (!ctx->copy_stream) {
+        CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->copy_done[0], cudaEventDisableTiming));
+        CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->copy_done[1], cudaEventDisableTiming));
+        CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->stage_free, cudaEventDisableTiming));
+    }
+    // Chunks: with more frames than half the staging slots, the frames go
+    // in chunks of up to max_batch / 2 through two halves of the staging
+    // area, so that the host-to-device copy of chunk k+1 (on the copy
+    // stream) overlaps the detection of chunk k.
+    const int half = std::max(1, ctx->p.max_batch / 2);
+    const int chunk = n_frames > half ? std::min(half, (n_frames + 3) / 4) : std::max(n_frames, 1);
+    const int nchunks = (n_frames + chunk - 1) / chunk;
     std::vector<hog_frame> dev((size_t)ctx->p.max_batch);
-    for (int b0 = 0; b0 < n_frames; b0 += ctx->p.max_batch) {
-        const int nb = std::min(ctx->p.max_batch, n_frames - b0);
-        for (int i = 0; i < nb; i++) {
+
+    // enqueue the copy of chunk k into staging half (k & 1) on the copy
+    // stream.  Frames that are dense (pitch = w), follow each other in
+    // pinned host memory and fill their device slot exactly (w * h =
+    // fbytes) move as one copy; pinned-ness is looked up once per run.
+    auto copy_chunk = [&](int k) -> int {
+        const int b0 = k * chunk, nb = std::min(chunk, n_frames - b0);
+        const size_t base = (size_t)(nchunks > 1 ? (k & 1) * chunk : 0);
+        cudaStream_t cs = ctx->copy_stream;
+        for (int i = 0; i < nb;) {
             const hog_frame &f = frames[b0 + i];
-            int rc = check_frame(ctx, &f, false);
-            if (rc) return rc;
-            uint8_t *d = ctx->d_stage + (size_t)i * fbytes;
-            dev[i] = hog_frame{d, f.w, f.h, f.w};
-            if (f.w == 0 || f.h == 0) continue;
+            uint8_t *d = ctx->d_stage + (base + i) * fbytes;
+            if (f.w == 0 || f.h == 0) { i++; continue; }
             cudaPointerAttributes attr;
             const bool pinned = cudaPointerGetAttributes(&attr, f.data) == cudaSuccess &&
                                 attr.type == cudaMemoryTypeHost;
             cudaGetLastError();
+            const size_t fb = (size_t)f.w * f.h;
+            int run = 1;
+            if (pinned && f.pitch == f.w && fb == fbytes) {
+                while (i + run < nb) {
+                    const hog_frame &g = frames[b0 + i + run];
+                    if (g.w != f.w || g.h != f.h || g.pitch != f.pitch || g.data != f.data + run * fb) break;
+                    run++;
+                }
+                CUDA_TRY(ctx, cudaMemcpyAsync(d, f.data, fb * run, cudaMemcpyHostToDevice, cs));
+                i += run;
+                continue;
+            }
             const uint8_t *srcp = f.data;
             size_t spitch = (size_t)f.pitch;
             if (!pinned) {   // stage through pinned memory so the copy is asynchronous
-                uint8_t *h = ctx->h_stage + (size_t)i * fbytes;
+                uint8_t *h = ctx->h_stage + (base + i) * fbytes;
                 for (int y = 0; y < f.h; y++) std::memcpy(h + (size_t)y * f.w, f.data + (size_t)y * f.pitch, f.w);
                 srcp = h;
                 spitch = (size_t)f.w;
             }
             CUDA_TRY(ctx, cudaMemcpy2DAsync(d, (size_t)f.w, srcp, spitch, (size_t)f.w, (size_t)f.h,
-                                            cudaMemcpyHostToDevice, stream));
+                                            cudaMemcpyHostToDevice, cs));
+            i++;
         }
+        CUDA_TRY(ctx, cudaEventRecord(ctx->copy_done[k & 1], cs));
+        return HOG_OK;
+    };
+
+    // the copy stream may only overwrite staging that no earlier work on
+    // `stream` still reads
+    CUDA_TRY(ctx, cudaEventRecord(ctx->stage_free, stream));
+    CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->stage_free, 0));
+    int total = 0;
+    bool truncated = false;
+    int rc = nchunks > 0 ? copy_chunk(0) : HOG_OK;
+    for (int k = 0; k < nchunks && !rc; k++) {
+        // chunk k+1 goes into the other half, whose last reader (chunk k-1)
+        // has finished: detect_device synchronised `stream` before returning
+        if (k + 1 < nchunks) rc = copy_chunk(k + 1);
+        if (rc) break;
+        const int b0 = k * chunk, nb = std::min(chunk, n_frames - b0);
+        const size_t base = (size_t)(nchunks > 1 ? (k & 1) * chunk : 0);
+        for (int i = 0; i < nb; i++) {
+            const hog_frame &f = frames[b0 + i];
+            dev[i] = hog_frame{ctx->d_stage + (base + i) * fbytes, f.w, f.h, f.w};
+        }
+        CUDA_TRY(ctx, cudaStreamWaitEvent(stream, ctx->copy_done[k & 1], 0));
         const int cap = dets ? std::max(det_cap - total, 0) : 0;
         int wrote = 0;
-        int rc = detect_device(ctx, dev.data(), nb, b0, dets ? dets + total : nullptr, cap, &wrote,
-                               counts ? counts + b0 : nullptr, stream, ctx->batched_mode, true);
-        if (rc == HOG_ECAPACITY) truncated = true;
-        else if (rc) return rc;
+        rc = detect_device(ctx, dev.data(), nb, b0, dets ? dets + total : nullptr, cap, &wrote,
+                           counts ? counts + b0 : nullptr, stream, ctx->batched_mode, true);
+        if (rc == HOG_ECAPACITY) { truncated = true; rc = HOG_OK; }
         total += wrote;
+    }
+    if (rc) {
+        cudaStreamSynchronize(ctx->copy_stream);   // no copy still writes the staging area
+        return rc;
     }
     return truncated ? fail(ctx, HOG_ECAPACITY, "detections truncated") : HOG_OK;
 }

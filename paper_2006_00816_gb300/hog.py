@@ -229,6 +229,63 @@ def _frame_of(t) -> Frame:
     return Frame(C.c_void_p(t.data_ptr()), int(t.shape[1]), int(t.shape[0]), int(t.stride(0)))
 
 
+# hog_frame as a numpy record, so that a batch of descriptors is built with
+# array operations rather than one ctypes object per frame
+FRAME_DTYPE = np.dtype({"names": ["data", "w", "h", "pitch"],
+                        "formats": ["<u8", "<i4", "<i4", "<i4"],
+                        "offsets": [Frame.data.offset, Frame.w.offset, Frame.h.offset,
+                                    Frame.pitch.offset],
+                        "itemsize": C.sizeof(Frame)})
+
+
+def _frame_table(frames, on_device):
+    """hog_frame descriptors of a batch of uint8 frames, as a FRAME_DTYPE
+    array (at least one entry; the caller passes the true count).  ``frames``
+    is a list of [h, w] frames or one [n, h, w] array whose frame i starts at
+    base + i * stride 0.  on_device: CUDA tensors (torch); else host numpy
+    arrays (a list entry that is not a row-strided uint8 array is copied to
+    one, and the copy is kept alive in the second return value)."""
+    if on_device:
+        import torch
+        if isinstance(frames, torch.Tensor):
+            t = frames
+            if t.dtype != torch.uint8 or t.dim() != 3 or not t.is_cuda or (t.numel() and t.stride(2) != 1):
+                raise ValueError("want a CUDA uint8 tensor [n, h, w] with unit column stride")
+            n = int(t.shape[0])
+            tab = np.zeros(max(n, 1), FRAME_DTYPE)
+            tab["data"][:n] = t.data_ptr() + np.arange(n, dtype=np.uint64) * np.uint64(t.stride(0))
+            tab["w"][:n], tab["h"][:n], tab["pitch"][:n] = t.shape[2], t.shape[1], t.stride(1)
+            return tab, None
+        rows = []
+        for t in frames:
+            if t.dtype != torch.uint8 or t.dim() != 2 or not t.is_cuda:
+                raise ValueError("want CUDA uint8 tensors [h, w]")
+            rows.append((t.data_ptr(), t.shape[1], t.shape[0], t.stride(0)))
+        return np.array(rows or [(0, 0, 0, 0)], FRAME_DTYPE), None
+    if isinstance(frames, np.ndarray) and frames.ndim == 3:
+        a = frames
+        if a.dtype != np.uint8 or (a.size and (a.strides[2] != 1 or a.strides[1] < a.shape[2]
+                                               or a.strides[0] < 0)):
+            a = np.ascontiguousarray(a, dtype=np.uint8)
+        n = a.shape[0]
+        tab = np.zeros(max(n, 1), FRAME_DTYPE)
+        tab["data"][:n] = a.ctypes.data + np.arange(n, dtype=np.uint64) * np.uint64(a.strides[0])
+        tab["w"][:n], tab["h"][:n], tab["pitch"][:n] = a.shape[2], a.shape[1], a.strides[1]
+        return tab, a
+    keep, rows = [], []
+    for f in frames:
+        if not (isinstance(f, np.ndarray) and f.dtype == np.uint8 and f.ndim == 2
+                and f.strides[1] == 1 and f.strides[0] >= f.shape[1]):
+            f = np.ascontiguousarray(f, dtype=np.uint8)
+        keep.append(f)
+        rows.append((f.ctypes.data, f.shape[1], f.shape[0], f.strides[0]))
+    return np.array(rows or [(0, 0, 0, 0)], FRAME_DTYPE), keep
+
+
+def _tab_ptr(tab):
+    return tab.ctypes.data_as(_P(Frame))
+
+
 class Detector:
     """One libhog context (filters on the device, arenas allocated once)."""
 
@@ -314,9 +371,10 @@ class Detector:
     def autotune(self, frames, cache_path=None, stream=None):
         """Run the autotuner on a sample batch of device frames; returns
         (batched_mode, corr_policy)."""
-        arr = (Frame * len(frames))(*[_frame_of(f) for f in frames])
+        tab, _ = _frame_table(frames, True)
         path = cache_path.encode() if cache_path else None
-        self._check(_lib.hog_autotune(self._h, arr, len(frames), path, _stream_ptr(stream)))
+        self._check(_lib.hog_autotune(self._h, _tab_ptr(tab), len(frames), path,
+                                      _stream_ptr(stream)))
         return self.tuning()
 
     def tuning(self):
@@ -380,16 +438,9 @@ class Detector:
             res.append(out[lv[i].offset:lv[i].offset + F * nu * nv].view(F, nu, nv))
         return res
 
-    def detect(self, frames, det_cap=None, stream=None, allow_capacity=False, out=None,
-               batched=False):
-        """Detect on a list of device uint8 frames.  Returns (dets, counts):
-        dets a numpy structured array (DET_DTYPE), counts int32 per frame.
-        With ``out`` (a DET_DTYPE array, e.g. a view of pinned memory, which
-        the device then fills directly), dets is a view of ``out``.
-        ``batched``: hog_detect_batched (persistent fused launch, graphs)."""
-        fn = _lib.hog_detect_batched if batched else _lib.hog_detect
-        n = len(frames)
-        arr = (Frame * max(n, 1))(*[_frame_of(f) for f in frames])
+    def _detect_call(self, call, n, det_cap, allow_capacity, out):
+        """Shared tail of the detect entry points: the output buffer, the
+        call (call(dets_ptr, det_cap, counts_ptr) -> rc) and the kept rows."""
         if out is not None:
             assert out.dtype == DET_DTYPE and out.flags.c_contiguous
             dets = out
@@ -399,62 +450,52 @@ class Detector:
                 det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
             dets = np.empty(max(det_cap, 1), DET_DTYPE)
         counts = np.zeros(max(n, 1), np.int32)
-        rc = fn(self._h, arr, n, dets.ctypes.data_as(_vp), det_cap,
-                counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
+        rc = call(dets.ctypes.data_as(_vp), det_cap, counts.ctypes.data_as(_P(_i32)))
         self._check(rc, allow=(HOG_ECAPACITY,) if allow_capacity else ())
         total = min(int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum()), det_cap)
         if out is not None:
             return dets[:total], counts[:n].copy()
         return dets[:total].copy(), counts[:n].copy()
+
+    def detect(self, frames, det_cap=None, stream=None, allow_capacity=False, out=None,
+               batched=False):
+        """Detect on device uint8 frames: a list of [h, w] tensors or one
+        [n, h, w] tensor.  Returns (dets, counts): dets a numpy structured
+        array (DET_DTYPE), counts int32 per frame.  With ``out`` (a DET_DTYPE
+        array, e.g. a view of pinned memory, which the device then fills
+        directly), dets is a view of ``out``.  ``batched``:
+        hog_detect_batched (persistent fused launch, graphs)."""
+        fn = _lib.hog_detect_batched if batched else _lib.hog_detect
+        n = len(frames)
+        tab, _ = _frame_table(frames, True)
+        sp = _stream_ptr(stream)
+        return self._detect_call(lambda d, cap, c: fn(self._h, _tab_ptr(tab), n, d, cap, c, sp),
+                                 n, det_cap, allow_capacity, out)
 
     def detect_roi(self, frames, rois, det_cap=None, stream=None, allow_capacity=False, out=None):
         """hog_detect_roi: as detect, each frame restricted to its region of
         interest rois[i] = (x0, y0, x1, y1, lmin, lmax) or a Roi."""
         n = len(frames)
         assert len(rois) == n
-        arr = (Frame * max(n, 1))(*[_frame_of(f) for f in frames])
+        tab, _ = _frame_table(frames, True)
         ra = (Roi * max(n, 1))(*[r if isinstance(r, Roi) else Roi(*[float(x) for x in r[:4]],
                                                                      int(r[4]), int(r[5]))
                                  for r in rois])
-        if out is not None:
-            assert out.dtype == DET_DTYPE and out.flags.c_contiguous
-            dets = out
-            det_cap = len(out) if det_cap is None else min(det_cap, len(out))
-        else:
-            if det_cap is None:
-                det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
-            dets = np.empty(max(det_cap, 1), DET_DTYPE)
-        counts = np.zeros(max(n, 1), np.int32)
-        rc = _lib.hog_detect_roi(self._h, arr, ra, n, dets.ctypes.data_as(_vp), det_cap,
-                                 counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
-        self._check(rc, allow=(HOG_ECAPACITY,) if allow_capacity else ())
-        total = min(int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum()), det_cap)
-        if out is not None:
-            return dets[:total], counts[:n].copy()
-        return dets[:total].copy(), counts[:n].copy()
+        sp = _stream_ptr(stream)
+        return self._detect_call(
+            lambda d, cap, c: _lib.hog_detect_roi(self._h, _tab_ptr(tab), ra, n, d, cap, c, sp),
+            n, det_cap, allow_capacity, out)
 
     def detect_host(self, frames, det_cap=None, stream=None, allow_capacity=False, out=None):
-        """Same as detect, from host numpy uint8 frames [h, w] (copied in the call)."""
+        """Same as detect, from host uint8 frames (a list of [h, w] numpy
+        arrays or one [n, h, w] array), copied in the call; frames in pinned
+        memory that follow each other move in one copy."""
         n = len(frames)
-        frames = [np.ascontiguousarray(f, dtype=np.uint8) for f in frames]
-        arr = (Frame * max(n, 1))(*[Frame(f.ctypes.data_as(_vp), f.shape[1], f.shape[0],
-                                          f.strides[0]) for f in frames])
-        if out is not None:
-            assert out.dtype == DET_DTYPE and out.flags.c_contiguous
-            dets = out
-            det_cap = len(out) if det_cap is None else min(det_cap, len(out))
-        else:
-            if det_cap is None:
-                det_cap = max(n, 1) * int(self.params.max_dets_per_frame)
-            dets = np.empty(max(det_cap, 1), DET_DTYPE)
-        counts = np.zeros(max(n, 1), np.int32)
-        rc = _lib.hog_detect_host(self._h, arr, n, dets.ctypes.data_as(_vp), det_cap,
-                                  counts.ctypes.data_as(_P(_i32)), _stream_ptr(stream))
-        self._check(rc, allow=(HOG_ECAPACITY,) if allow_capacity else ())
-        total = min(int(np.minimum(counts[:n], self.params.max_dets_per_frame).sum()), det_cap)
-        if out is not None:
-            return dets[:total], counts[:n].copy()
-        return dets[:total].copy(), counts[:n].copy()
+        tab, keep = _frame_table(frames, False)
+        sp = _stream_ptr(stream)
+        return self._detect_call(
+            lambda d, cap, c: _lib.hog_detect_host(self._h, _tab_ptr(tab), n, d, cap, c, sp),
+            n, det_cap, allow_capacity, out)
 
 
 def default_server_config(**kw) -> ServerConfig:
@@ -516,14 +557,12 @@ def pipeline_run(det, ert, frames, batch, n_threads, pipelined, stream=None):
     copy asynchronously).  Returns (landmarks [n, 68, 2], ear [n, 2],
     has_face [n], seconds)."""
     n = len(frames)
-    keep = [np.ascontiguousarray(f, dtype=np.uint8) for f in frames]
-    arr = (Frame * max(n, 1))(*[Frame(f.ctypes.data, f.shape[1], f.shape[0], f.strides[0])
-                                  for f in keep])
+    tab, keep = _frame_table(frames, False)
     lm = np.zeros((max(n, 1), 68, 2), np.float32)
     ear = np.zeros((max(n, 1), 2), np.float32)
     face = np.zeros(max(n, 1), np.int32)
     sec = C.c_double(0.0)
-    rc = _lib.hog_pipeline_run(det._h, ert._h, arr, n, int(batch), int(n_threads), int(pipelined),
+    rc = _lib.hog_pipeline_run(det._h, ert._h, _tab_ptr(tab), n, int(batch), int(n_threads), int(pipelined),
                                lm.ctypes.data_as(_vp), ear.ctypes.data_as(_vp),
                                face.ctypes.data_as(_vp), C.byref(sec), _stream_ptr(stream))
     det._check(rc)

@@ -115,3 +115,36 @@ def test_server_rejects_bad_params_and_nulls(hog):
     assert hog._lib.hog_server_submit(None, None, 1, 1, 1, 0, None) == hog.HOG_EINVAL
     assert hog._lib.hog_server_poll(None, None, 0, None, 0, C.byref(n), 0) == hog.HOG_EINVAL
     hog._lib.hog_server_destroy(None)
+
+
+def test_frame_table_layout_and_forms(hog):
+    """The numpy hog_frame table has the C struct's layout, and a list of
+    frames and one [n, h, w] array give the same descriptors; arrays that
+    are not row-strided uint8 are copied to ones that are."""
+    import numpy as np
+    assert hog.FRAME_DTYPE.itemsize == C.sizeof(hog.Frame)
+    for name, _ in hog.Frame._fields_:
+        assert hog.FRAME_DTYPE.fields[name][1] == getattr(hog.Frame, name).offset
+    a = np.arange(4 * 6 * 9, dtype=np.uint8).reshape(4, 6, 9)
+    t3, _ = hog._frame_table(a, False)
+    tl, _ = hog._frame_table(list(a), False)
+    assert t3.tolist() == tl.tolist()
+    assert t3["data"].tolist() == [a.ctypes.data + i * 54 for i in range(4)]
+    assert (t3["w"] == 9).all() and (t3["h"] == 6).all() and (t3["pitch"] == 9).all()
+    sub = a[:, 1:5, 2:7]                      # row-strided view: kept as is, pitch 9
+    ts, _ = hog._frame_table(sub, False)
+    assert ts["data"].tolist() == [a.ctypes.data + i * 54 + 11 for i in range(4)]
+    assert (ts["w"] == 5).all() and (ts["h"] == 4).all() and (ts["pitch"] == 9).all()
+    for bad in (a[:, ::-1], a[:, :, ::2], a.astype(np.int16), a[::-1]):
+        tb, keep = hog._frame_table(bad, False)
+        want = np.ascontiguousarray(bad, dtype=np.uint8)
+        for i in range(4):                    # descriptors point at a dense copy
+            got = np.ctypeslib.as_array(C.cast(int(tb["data"][i]), C.POINTER(C.c_uint8)),
+                                        (int(tb["h"][i]), int(tb["pitch"][i])))
+            assert np.array_equal(got[:, :int(tb["w"][i])], want[i])
+        tlist, keep2 = hog._frame_table(list(bad), False)
+        assert (tlist["w"] == tb["w"]).all() and (tlist["pitch"] == tlist["w"]).all()
+    t0, _ = hog._frame_table([], False)
+    assert len(t0) == 1 and int(t0["data"][0]) == 0
+    e, _ = hog._frame_table(np.zeros((0, 4, 4), np.uint8), False)
+    assert len(e) == 1

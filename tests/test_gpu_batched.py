@@ -80,3 +80,33 @@ def test_autotune_keeps_results_and_caches(H, synth, tmp_path):
     det2 = H.Detector(W, max_w=1280, max_h=1024, max_batch=8)
     assert det2.autotune(frames, cache_path=path) == (mode, pol)
     os.remove(path)
+
+
+def test_batch_tensor_and_chunked_host_copies(H, synth):
+    """One [n, h, w] tensor gives the same detections as the list of its
+    frames, per frame and batched; hog_detect_host, which moves host frames
+    in chunks of max_batch / 2 through two staging halves (copies of the
+    next chunk overlapping detection of this one), gives the device result
+    for a pinned [n, h, w] array (one copy per chunk), for plain numpy
+    frames of several sizes and for row-strided views."""
+    W = synth.filters(5)
+    det = H.Detector(W, max_w=640, max_h=480, max_batch=4)
+    host = synth.eyeblink_stream(11)
+    fd = dev(host)
+    ref, rc = det.detect([fd[i] for i in range(11)])
+    for batched in (False, True):
+        got, gc = det.detect(fd, batched=batched)
+        assert gc.tolist() == rc.tolist() and np.array_equal(got, ref), batched
+    pinned = torch.from_numpy(host).pin_memory().numpy()
+    for frames in (pinned, list(pinned), list(host), host):
+        got, gc = det.detect_host(frames)
+        assert gc.tolist() == rc.tolist() and np.array_equal(got, ref)
+    mixed = [host[0], host[1][:300, :500], np.ascontiguousarray(host[2][::2, ::2]),
+             host[3][17:400, 33:600], np.full((90, 100), 7, np.uint8), host[4],
+             np.zeros((0, 0), np.uint8), pinned[5][:, :320], host[6]]
+    want, wc = det.detect([dev(f) for f in mixed])
+    for _ in range(2):
+        got, gc = det.detect_host(mixed)
+        assert gc.tolist() == wc.tolist() and np.array_equal(got, want)
+    got, gc = det.detect_host(mixed[:1])                 # one frame: no chunking
+    assert gc[0] == wc[0]
