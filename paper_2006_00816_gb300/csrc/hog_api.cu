@@ -33,6 +33,7 @@ struct Geometry {
     int W = 0, H = 0, nlev = 0;
     int lw[MAX_LEVELS], lh[MAX_LEVELS], cx[MAX_LEVELS], cy[MAX_LEVELS];
     int nu[MAX_LEVELS], nv[MAX_LEVELS], pitch[MAX_LEVELS];
+    int hbw[MAX_LEVELS];           // histogram tile width in blocks
     size_t pyr_off[MAX_LEVELS];    // bytes, levels >= 1, in a slot's pyramid arena
     size_t hist_off[MAX_LEVELS];   // floats
     size_t feat_off[MAX_LEVELS];   // floats, internal layout
@@ -59,6 +60,7 @@ int compute_geometry(const hog_params &p, int W, int H, Geometry &g) {
         g.lh[n] = h;
         g.cx[n] = w / CELL;
         g.cy[n] = h / CELL;
+        g.hbw[n] = hist_tile_bw(g.cx[n], g.cy[n], h);
         g.nu[n] = std::max(g.cy[n] - WIN + 1, 0);
         g.nv[n] = std::max(g.cx[n] - WIN + 1, 0);
         g.pitch[n] = (int)align_up((size_t)w, 16);
@@ -516,6 +518,7 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         std::memset(&d, 0, sizeof d);
         d.w = g.lw[l]; d.h = g.lh[l];
         d.cx = g.cx[l]; d.cy = g.cy[l]; d.nu = g.nu[l]; d.nv = g.nv[l];
+        d.hist_bw = g.hbw[l];
         d.frame = frame_index; d.level = l;
         d.scan = l >= ctx->p.skip_levels ? 1 : 0;
         if (o.roi) d.scan = ru0[l] < ru1[l] ? 1 : 0;
@@ -556,12 +559,13 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         if (o.feat && want && !absent && o.roi) {
             // only the cells the scanned windows read: features of cell rows
             // [u0, u1 + 9) x cols [v0, v1 + 9), histograms one cell wider
-            tiles_meeting(d.cx, d.cy, HIST_TX, HIST_TY, ru0[l] - 1, ru1[l] + WIN, rv0[l] - 1,
-                          rv1[l] + WIN, [&](int k) { pb.hist.push_back({di, k}); });
+            tiles_meeting(d.cx, d.cy, d.hist_bw - 1, hist_bh(d.hist_bw) - 1, ru0[l] - 1,
+                          ru1[l] + WIN, rv0[l] - 1, rv1[l] + WIN,
+                          [&](int k) { pb.hist.push_back({di, k}); });
             tiles_meeting(d.cx, d.cy, FEAT_TX, FEAT_TY, ru0[l], ru1[l] + WIN - 1, rv0[l],
                           rv1[l] + WIN - 1, [&](int k) { pb.feat.push_back({di, k}); });
         } else if (o.feat && want && !absent) {
-            const int nh = ((d.cx + HIST_TX - 1) / HIST_TX) * ((d.cy + HIST_TY - 1) / HIST_TY);
+            const int nh = hist_ntiles(d.cx, d.cy, d.hist_bw);
             for (int k = 0; k < nh; k++) pb.hist.push_back({di, k});
             const int nfj = ((d.cx + FEAT_TX - 1) / FEAT_TX) * ((d.cy + FEAT_TY - 1) / FEAT_TY);
             for (int k = 0; k < nfj; k++) pb.feat.push_back({di, k});

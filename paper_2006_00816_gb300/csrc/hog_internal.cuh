@@ -21,8 +21,14 @@ constexpr int MAXN = 192;           // suppression neighbours per window positio
 
 // Tile shapes of the plain kernels.
 constexpr int PYR_TX = 160, PYR_TY = 32;         // output pixels per CTA (256 threads x 20)
-constexpr int HIST_BX = 16, HIST_BY = 16;        // 8x8-pixel blocks per CTA (256 threads)
-constexpr int HIST_TX = HIST_BX - 1, HIST_TY = HIST_BY - 1;   // 15 x 15 cells per CTA
+// Histogram tiles: bw x (256 / bw) blocks of 8x8 pixels (one per thread)
+// emit (bw - 1) x (256 / bw - 1) cells; bw is chosen per level (hist_tile_bw).
+constexpr int HIST_NT = 256;
+constexpr int HIST_BW_MIN = 7, HIST_BW_MAX = 32;
+__host__ __device__ constexpr int hist_bh(int bw) { return HIST_NT / bw; }
+inline int hist_ntiles(int cx, int cy, int bw) {
+    return ((cx + bw - 2) / (bw - 1)) * ((cy + hist_bh(bw) - 2) / (hist_bh(bw) - 1));
+}
 constexpr int FEAT_TX = 32, FEAT_TY = 8;         // cells per CTA (256 threads)
 // Correlation warp tiles (windows): shape id 0: 8x16, 1: 4x32, 2: 16x8; the
 // shape is stored in bits 28..29 of the job's tile field.
@@ -100,6 +106,7 @@ struct LevelDesc {
     int32_t dpow;           // pyramid job: 0 = 5/6 step from src; s >= 2 = direct
                             // from the frame (src) with the ratio (6/5)^s
     int32_t pos_off;        // first window position of this level in the frame
+    int32_t hist_bw;        // histogram tile width in blocks (hist_tile_bw)
     float *hist;            // [cy][cx][18]
     float *feat;            // [4][cy][cx][8] internal layout
     float *feat_user;       // optional [cy][cx][31] copy (hog_features)
@@ -295,5 +302,51 @@ cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *
                        cudaStream_t stream, int cluster_request);
 // Cluster size launch_nms uses for such a batch (1 = one CTA per frame).
 int nms_cluster_size(int nframes, int max_npos, int request);
+
+// Histogram tile width (blocks) for a level of cx x cy cells and height h
+// pixels: the bw in [HIST_BW_MIN, HIST_BW_MAX] whose tiles issue the fewest
+// warp row steps over the level, plus 3 per tile for staging, zeroing and
+// the combine.  A thread runs its block's 8 pixel rows in [1, min(h - 2,
+// 8 cy - 1)] if the block meets a cell of the level; a warp takes a row
+// step if one of its threads does.  Tiles of one row class (first, inner,
+// last tile row) and column class (inner, last) cost the same, so one
+// tile of each class is counted.  Ties keep the smaller bw.
+inline int hist_tile_bw(int cx, int cy, int h) {
+    const int ymax = (h - 2 < CELL * cy - 1) ? h - 2 : CELL * cy - 1;
+    long best_cost = -1;
+    int best_bw = 16;
+    for (int bw = HIST_BW_MIN; bw <= HIST_BW_MAX; bw++) {
+        const int bh = hist_bh(bw), tw = bw - 1, th = bh - 1;
+        const int ntx = (cx + tw - 1) / tw, nty = (cy + th - 1) / th;
+        auto tile_cost = [&](int ti, int tj) {
+            const int i0 = ti * th, j0 = tj * tw;
+            long c = 3;
+            for (int w0 = 0; w0 < HIST_NT; w0 += 32) {
+                unsigned rows = 0;
+                const int t1 = (w0 + 32 < bw * bh ? w0 + 32 : bw * bh) - 1;
+                for (int t = w0; t <= t1; t++) {
+                    const int by = t / bw, bx = t - by * bw;
+                    if (i0 + by > cy || j0 + bx > cx) continue;
+                    for (int oy = 0; oy < CELL; oy++) {
+                        const int Y = CELL * (i0 + by) - 4 + oy;
+                        if (Y >= 1 && Y <= ymax) rows |= 1u << oy;
+                    }
+                }
+                c += __builtin_popcount(rows);
+            }
+            return c;
+        };
+        long cost = 0;
+        const int ti_rep[3] = {0, 1, nty - 1};
+        const long ti_mul[3] = {1, nty > 2 ? nty - 2 : 0, nty > 1 ? 1 : 0};
+        for (int a = 0; a < 3; a++) {
+            if (!ti_mul[a]) continue;
+            if (ntx > 1) cost += ti_mul[a] * (ntx - 1) * tile_cost(ti_rep[a], 0);
+            cost += ti_mul[a] * tile_cost(ti_rep[a], ntx - 1);
+        }
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best_bw = bw; }
+    }
+    return best_bw;
+}
 
 }  // namespace hogk

@@ -177,8 +177,10 @@ __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
 // private partial histograms (one per corner cell) in shared memory, laid
 // out [corner][bin][thread] so a warp's lanes hit 32 banks.  A cell is the
 // fixed-order sum of its four blocks' partials: deterministic, no atomics,
-// no sum longer than 64 terms.  256 threads own 16x16 blocks and emit the
-// 15x15 cells whose four blocks they hold.
+// no sum longer than 64 terms.  256 threads own bw x (256 / bw) blocks and
+// emit the (bw - 1) x (256 / bw - 1) cells whose four blocks they hold; bw
+// is chosen per level to waste the fewest thread slots on the level's
+// ragged edges (the cells' sums do not depend on it).
 //
 // Orientation: fold (dx, dy) into the first quadrant; the sector q is the
 // number of bin boundaries (10, 30, 50, 70 degrees) the vector lies beyond,
@@ -188,15 +190,27 @@ __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
 // product at most 4e-5.  dx == 0 (the only exact tie) goes to bin 4 (dy > 0)
 // or 13.  Branch-free: the quadrant is resolved with selects.
 namespace hist_cfg {
-constexpr int NT = HIST_BX * HIST_BY;          // 256 threads, one per block
-constexpr int PX = HIST_BX * CELL + 2;         // 130 staged columns (blocks + 1-px halo)
-constexpr int PY = HIST_BY * CELL + 2;         // 130 staged rows
-constexpr int NCH = 10;                        // 16-byte chunks per staged row (130 + 15 <= 160)
-constexpr int SROWB = NCH * 16;                // 160 bytes per staged row
-constexpr size_t SMEM_SRC = (size_t)PY * SROWB;                     // 20,800
+constexpr int NT = HIST_NT;                    // 256 threads, one per block
+// staged rows of a bw-wide tile: its 8 * bh pixel rows + a 1-px halo; row
+// bytes: 8 bw + 2 columns + up to 15 bytes of 16-byte alignment slack
+__host__ __device__ constexpr int py_of(int bw) { return CELL * hist_bh(bw) + 2; }
+__host__ __device__ constexpr int nch_of(int bw) { return (CELL * bw + 32) / 16; }
+constexpr size_t src_bytes_max() {
+    size_t m = 0;
+    for (int bw = HIST_BW_MIN; bw <= HIST_BW_MAX; bw++) {
+        const size_t b = (size_t)py_of(bw) * nch_of(bw) * 16;
+        const size_t o = sizeof(float) * NBIN * (bw - 1) * (hist_bh(bw) - 1);   // combined cells
+        m = b > m ? b : m;
+        m = o > m ? o : m;
+    }
+    return m;
+}
+constexpr int PY_MAX = py_of(HIST_BW_MIN);                          // 290 rows
+constexpr size_t SMEM_SRC = src_bytes_max();                        // 24,768 (bw = 8)
 constexpr size_t SMEM_PART = sizeof(float) * 4 * NBIN * NT;         // 73,728
-constexpr size_t SMEM_XB = sizeof(int) * 132;
-constexpr size_t SMEM = SMEM_PART + SMEM_SRC + SMEM_XB;             // 95,056
+constexpr size_t SMEM_XB = sizeof(int) * ((PY_MAX + 3) / 4 * 4);    // 1,168
+constexpr size_t SMEM = SMEM_PART + SMEM_SRC + SMEM_XB;             // 99,664
+static_assert(SMEM_SRC % 16 == 0, "staging must keep 16-byte alignment");
 }  // namespace hist_cfg
 
 __device__ __forceinline__ int orientation_bin_f(int dx, int dy) {
@@ -223,45 +237,50 @@ __host__ __device__ constexpr float tent16(int t) {
 __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned char *smem) {
     using namespace hist_cfg;
     float *part = reinterpret_cast<float *>(smem);             // [4][18][NT]
-    uint8_t *srcS = smem + SMEM_PART;                          // [PY][SROWB]
+    uint8_t *srcS = smem + SMEM_PART;                          // [py][srowb]
     int *xbase = reinterpret_cast<int *>(smem + SMEM_PART + SMEM_SRC);
 
-    const int ntx = (d.cx + HIST_TX - 1) / HIST_TX;
-    const int j0 = (tile % ntx) * HIST_TX, i0 = (tile / ntx) * HIST_TY;
+    const int bw = d.hist_bw, bh = hist_bh(bw), tw = bw - 1, th = bh - 1;
+    const int nch = nch_of(bw), srowb = 16 * nch, py = py_of(bw);
+    const int ntx = (d.cx + tw - 1) / tw;
+    const int j0 = (tile % ntx) * tw, i0 = (tile / ntx) * th;
     const int t = threadIdx.x;
     const int xmax = min(d.w - 2, CELL * d.cx - 1);
     const int ymax = min(d.h - 2, CELL * d.cy - 1);
 
-    // Stage rows Ys .. Ys+PY-1, columns Xs .. Xs+PX-1 (clipped to the image)
-    // with 16-byte cp.async copies of the aligned chunks covering them.  A
-    // 16-byte-aligned chunk holding at least one byte of the frame lies on
-    // that byte's memory page, so the copies stay in mapped memory even
-    // where they reach past the clipped range; those bytes are never read.
-    // xbase[r] = image column of staged byte 0 of staged row r.
+    // Stage rows Ys .. Ys+py-1, columns Xs .. Xs+8bw+1 (clipped to the
+    // image) with 16-byte cp.async copies of the aligned chunks covering
+    // them.  A 16-byte-aligned chunk holding at least one byte of the frame
+    // lies on that byte's memory page, so the copies stay in mapped memory
+    // even where they reach past the clipped range; those bytes are never
+    // read.  xbase[r] = image column of staged byte 0 of staged row r.
     const int Xs = CELL * j0 - 5, Ys = CELL * i0 - 5;
-    const int xa = max(Xs, 0), xb = min(Xs + PX, d.w);
-    for (int idx = t; idx < PY * NCH; idx += NT) {
-        const int r = idx / NCH, ci = idx - r * NCH;
+    const int xa = max(Xs, 0), xb = min(Xs + CELL * bw + 2, d.w);
+    for (int idx = t; idx < py * nch; idx += NT) {
+        const int r = idx / nch, ci = idx - r * nch;
         const int Y = Ys + r;
         if (Y < 0 || Y >= d.h || xa >= xb) continue;
         const uintptr_t rp = (uintptr_t)(d.img + (size_t)Y * d.pitch);
         const uintptr_t c0 = (rp + (uintptr_t)xa) & ~(uintptr_t)15;
         const uintptr_t a = c0 + 16 * (uintptr_t)ci;
         if (ci == 0) xbase[r] = (int)((intptr_t)c0 - (intptr_t)rp);
-        if (a <= rp + (uintptr_t)(xb - 1)) cp_async16(srcS + r * SROWB + 16 * ci, (const void *)a);
+        if (a <= rp + (uintptr_t)(xb - 1)) cp_async16(srcS + r * srowb + 16 * ci, (const void *)a);
     }
     for (int k = t; k < NBIN * NT; k += NT) reinterpret_cast<float4 *>(part)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     cp_async_wait_all();
     __syncthreads();
 
-    // one 8x8 block per thread: pixels X = 8 bj - 4 + ox, Y = 8 bi - 4 + oy.
-    // Pixels outside the voting range (X < 1, X > xmax) read staged bytes
-    // that exist but vote with weight 0 (their column's tent weights are
-    // zeroed); zero gradients vote 0 as well (adding +0 leaves the
+    // one 8x8 block per thread (t < bw * bh): pixels X = 8 bj - 4 + ox,
+    // Y = 8 bi - 4 + oy.  A block that meets no cell of the level (bi > cy
+    // or bj > cx) is skipped; its partials stay 0 and no stored cell reads
+    // them.  Pixels outside the voting range (X < 1, X > xmax) read staged
+    // bytes that exist but vote with weight 0 (their column's tent weights
+    // are zeroed); zero gradients vote 0 as well (adding +0 leaves the
     // non-negative partials unchanged).  Magnitude sqrt(s) of the exact
     // integer s = dx^2 + dy^2 as s * rsqrt(s).
-    const int by = t / HIST_BX, bx = t - by * HIST_BX;
+    const int by = t / bw, bx = t - by * bw;
     const int X0 = CELL * (j0 + bx) - 4, Y0 = CELL * (i0 + by) - 4;
+    const bool active = t < bw * bh && i0 + by <= d.cy && j0 + bx <= d.cx;
     float wx0v[8], wx1v[8];   // column tent weights to cell cols bj-1, bj (0: no vote)
 #pragma unroll
     for (int ox = 0; ox < 8; ox++) {
@@ -273,11 +292,11 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
 #pragma unroll 1
     for (int oy = 0; oy < 8; oy++) {
         const int Y = Y0 + oy;
-        if (Y < 1 || Y > ymax) continue;
+        if (!active || Y < 1 || Y > ymax) continue;
         const int r = Y - Ys;                       // staged row of Y
-        const uint8_t *up = srcS + (r - 1) * SROWB - xbase[r - 1];
-        const uint8_t *mid = srcS + r * SROWB - xbase[r];
-        const uint8_t *dn = srcS + (r + 1) * SROWB - xbase[r + 1];
+        const uint8_t *up = srcS + (r - 1) * srowb - xbase[r - 1];
+        const uint8_t *mid = srcS + r * srowb - xbase[r];
+        const uint8_t *dn = srcS + (r + 1) * srowb - xbase[r + 1];
         const float wy1 = tent16(oy), wy0 = tent16(oy + 8);   // to cell rows bi, bi-1
 #pragma unroll
         for (int ox = 0; ox < 8; ox++) {
@@ -299,26 +318,26 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
 
     // cell (ci, cj) = blocks (ci,cj) corner 3 + (ci,cj+1) corner 2 + (ci+1,cj)
     // corner 1 + (ci+1,cj+1) corner 0; staged for a coalesced store
-    float *outS = reinterpret_cast<float *>(srcS);   // [15*15][18] = 16,200 bytes
-    if (t < HIST_TX * HIST_TY) {
-        const int ci = t / HIST_TX, cj = t - ci * HIST_TX;
-        const int b00 = ci * HIST_BX + cj;
+    float *outS = reinterpret_cast<float *>(srcS);   // [tw*th][18]
+    if (t < tw * th) {
+        const int ci = t / tw, cj = t - ci * tw;
+        const int b00 = ci * bw + cj;
 #pragma unroll
         for (int b = 0; b < NBIN; b++) {
             const float s3 = part[(3 * NBIN + b) * NT + b00];
             const float s2 = part[(2 * NBIN + b) * NT + b00 + 1];
-            const float s1 = part[(1 * NBIN + b) * NT + b00 + HIST_BX];
-            const float s0 = part[(0 * NBIN + b) * NT + b00 + HIST_BX + 1];
+            const float s1 = part[(1 * NBIN + b) * NT + b00 + bw];
+            const float s0 = part[(0 * NBIN + b) * NT + b00 + bw + 1];
             outS[t * NBIN + b] = (s3 + s2) + (s1 + s0);
         }
     }
     __syncthreads();
-    const int ncol = min(HIST_TX, d.cx - j0);
-    for (int r = 0; r < HIST_TY; r++) {
+    const int ncol = min(tw, d.cx - j0);
+    for (int r = 0; r < th; r++) {
         const int i = i0 + r;
         if (i >= d.cy) break;
         float *dst = d.hist + ((size_t)i * d.cx + j0) * NBIN;
-        const float *srcr = outS + r * HIST_TX * NBIN;
+        const float *srcr = outS + r * tw * NBIN;
         for (int k = t; k < ncol * NBIN; k += NT) dst[k] = srcr[k];
     }
     __syncthreads();   // shared memory may be reused by the caller's next tile

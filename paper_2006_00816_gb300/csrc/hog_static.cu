@@ -146,6 +146,7 @@ extern "C" int hog_features_static(const hog_params *p, const hog_frame *frame, 
         d.h = lh[l];
         d.cx = lw[l] / CELL;
         d.cy = lh[l] / CELL;
+        d.hist_bw = hist_tile_bw(d.cx, d.cy, d.h);
         d.level = l;
         if (l == 0) {
             d.img = frame->data;
@@ -171,7 +172,7 @@ extern "C" int hog_features_static(const hog_params *p, const hog_frame *frame, 
     }
     const int hist_beg = nj;
     for (int l = 0; l < L; l++) {
-        const int nt = ((descs[l].cx + HIST_TX - 1) / HIST_TX) * ((descs[l].cy + HIST_TY - 1) / HIST_TY);
+        const int nt = hist_ntiles(descs[l].cx, descs[l].cy, descs[l].hist_bw);
         for (int k = 0; k < nt && nj < STATIC_MAX_JOBS; k++) jobs[nj++] = Job{l, k};
     }
     const int feat_beg = nj;
