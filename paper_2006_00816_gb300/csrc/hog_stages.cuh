@@ -236,7 +236,8 @@ __host__ __device__ constexpr float tent16(int t) {
 // image with cp.async.cg (through L2), so it is coherent within a launch.
 __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned char *smem) {
     using namespace hist_cfg;
-    float *part = reinterpret_cast<float *>(smem);             // [4][18][NT]
+    // partials [corner pair][18][NT] of float2: .x corner 2p, .y corner 2p+1
+    float2 *part = reinterpret_cast<float2 *>(smem);
     uint8_t *srcS = smem + SMEM_PART;                          // [py][srowb]
     int *xbase = reinterpret_cast<int *>(smem + SMEM_PART + SMEM_SRC);
 
@@ -288,7 +289,7 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         wx0v[ox] = ok ? tent16(ox + 8) : 0.0f;
         wx1v[ox] = ok ? tent16(ox) : 0.0f;
     }
-    float *p0 = part + t;
+    float2 *p0 = part + t;
     // Word reads: where the level's rows are 8-byte aligned in memory (image
     // base and pitch multiples of 8), byte X0 of every staged row lies at a
     // shared address = 4 (mod 8).  A thread then reads its 10 middle-row
@@ -311,11 +312,14 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
             const float sf = (float)(dx * dx + dy * dy);
             const float m = sf * rsqrtf(fmaxf(sf, 1.0f));
             const float m0 = m * wy0, m1 = m * wy1;
-            float *pb = p0 + b * NT;
-            pb[0 * NBIN * NT] = fmaf(m0, wx0v[ox], pb[0 * NBIN * NT]);   // cell (bi-1, bj-1)
-            pb[1 * NBIN * NT] = fmaf(m0, wx1v[ox], pb[1 * NBIN * NT]);   // cell (bi-1, bj)
-            pb[2 * NBIN * NT] = fmaf(m1, wx0v[ox], pb[2 * NBIN * NT]);   // cell (bi,   bj-1)
-            pb[3 * NBIN * NT] = fmaf(m1, wx1v[ox], pb[3 * NBIN * NT]);   // cell (bi,   bj)
+            float2 *pb = p0 + b * NT;
+            float2 a = pb[0], c = pb[NBIN * NT];
+            a.x = fmaf(m0, wx0v[ox], a.x);   // cell (bi-1, bj-1)
+            a.y = fmaf(m0, wx1v[ox], a.y);   // cell (bi-1, bj)
+            c.x = fmaf(m1, wx0v[ox], c.x);   // cell (bi,   bj-1)
+            c.y = fmaf(m1, wx1v[ox], c.y);   // cell (bi,   bj)
+            pb[0] = a;
+            pb[NBIN * NT] = c;
         };
         if (words) {
             const uint2 ma = *reinterpret_cast<const uint2 *>(mid + X0 - 4);   // X0-4 .. X0+3
@@ -352,10 +356,10 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         const int b00 = ci * bw + cj;
 #pragma unroll
         for (int b = 0; b < NBIN; b++) {
-            const float s3 = part[(3 * NBIN + b) * NT + b00];
-            const float s2 = part[(2 * NBIN + b) * NT + b00 + 1];
-            const float s1 = part[(1 * NBIN + b) * NT + b00 + bw];
-            const float s0 = part[(0 * NBIN + b) * NT + b00 + bw + 1];
+            const float s3 = part[(1 * NBIN + b) * NT + b00].y;
+            const float s2 = part[(1 * NBIN + b) * NT + b00 + 1].x;
+            const float s1 = part[(0 * NBIN + b) * NT + b00 + bw].y;
+            const float s0 = part[(0 * NBIN + b) * NT + b00 + bw + 1].x;
             outS[t * NBIN + b] = (s3 + s2) + (s1 + s0);
         }
     }
