@@ -42,7 +42,7 @@ struct Geometry {
     int pos_off[MAX_LEVELS + 1];
     int npos = 0;
     size_t pyr_bytes = 0, hist_floats = 0, feat_floats = 0, ufeat_floats = 0, pyr_px = 0;
-    int32_t *d_nbr = nullptr;
+    int32_t *d_nbr = nullptr, *d_nbr_t = nullptr;
     uint8_t *d_cnt = nullptr;
 };
 
@@ -298,6 +298,7 @@ void free_ctx(hog_ctx *ctx) {
     if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
     for (Geometry *g : ctx->geoms) {
         F(g->d_nbr);
+        F(g->d_nbr_t);
         F(g->d_cnt);
         delete g;
     }
@@ -318,8 +319,10 @@ int get_geometry(hog_ctx *ctx, int W, int H, cudaStream_t stream, Geometry **out
     if (g->npos > 0) {
         cudaError_t e1 = cudaMalloc(&g->d_nbr, (size_t)g->npos * MAXN * sizeof(int32_t));
         cudaError_t e2 = cudaMalloc(&g->d_cnt, (size_t)g->npos);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaError_t e3 = cudaMalloc(&g->d_nbr_t, (size_t)g->npos * MAXN * sizeof(int32_t));
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
             cudaFree(g->d_nbr);
+            cudaFree(g->d_nbr_t);
             cudaFree(g->d_cnt);
             delete g;
             return fail(ctx, HOG_ENOMEM, "neighbour table allocation failed");
@@ -347,16 +350,16 @@ int get_geometry(hog_ctx *ctx, int W, int H, cudaStream_t stream, Geometry **out
         }
         *ctx->h_flags = 0;
         cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), stream);
-        cudaError_t e = launch_nms_geometry(gd, g->d_nbr, g->d_cnt, ctx->d_flags, stream);
+        cudaError_t e = launch_nms_geometry(gd, g->d_nbr, g->d_nbr_t, g->d_cnt, ctx->d_flags, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int),
                                                   cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) {
-            cudaFree(g->d_nbr); cudaFree(g->d_cnt); delete g;
+            cudaFree(g->d_nbr); cudaFree(g->d_nbr_t); cudaFree(g->d_cnt); delete g;
             return fail(ctx, HOG_ECUDA, "suppression geometry: %s", cudaGetErrorString(e));
         }
         if (*ctx->h_flags) {
-            cudaFree(g->d_nbr); cudaFree(g->d_cnt); delete g;
+            cudaFree(g->d_nbr); cudaFree(g->d_nbr_t); cudaFree(g->d_cnt); delete g;
             return fail(ctx, HOG_EINVAL, "nms_iou %.3f gives more than %d overlapping windows",
                         (double)ctx->p.nms_iou, MAXN);
         }
@@ -645,6 +648,7 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         fd.keys = keys;
         fd.ws = ctx->d_nmsws + (size_t)slot * ctx->pos_slot * 4;
         fd.nbr = g.d_nbr;
+        fd.nbr_t = g.d_nbr_t;
         fd.nbr_cnt = g.d_cnt;
         fd.out = ctx->d_dets + (size_t)slot * ctx->p.max_dets_per_frame;
         fd.out_cap = ctx->p.max_dets_per_frame;

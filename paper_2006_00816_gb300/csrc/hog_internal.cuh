@@ -133,6 +133,7 @@ struct FrameDesc {
     const uint64_t *keys;             // [npos]
     uint32_t *ws;                     // suppression workspace (global mode), 14 B per position
     const int32_t *nbr;               // [MAXN][npos] neighbour lists, slot-major
+    const int32_t *nbr_t;             // [npos][MAXN] the same lists, position-major
     const uint8_t *nbr_cnt;           // [npos]
     hog_det *out;                     // [out_cap]
     int32_t out_cap;
@@ -286,8 +287,8 @@ cudaError_t launch_feat(const LevelDesc *descs, const Job *jobs, int njobs, floa
 cudaError_t launch_corr(const LevelDesc *descs, const Job *jobs, int njobs,
                         const float *wchunks, int nf_kernel, int nf_real, float threshold,
                         cudaStream_t stream);
-cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, uint8_t *cnt, int *overflow,
-                                cudaStream_t stream);
+cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, int32_t *nbr_t, uint8_t *cnt,
+                                int *overflow, cudaStream_t stream);
 // Gather the kept boxes of nframes frames (slot i holds counts[i] boxes at
 // dets + i*per_frame, at most per_frame) into out[0..out_cap) frame after
 // frame, and copy the exact counts to counts_out; out and counts_out may be

@@ -705,8 +705,10 @@ __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ desc
 // candidate's slots are scanned about once in all.
 //
 // Overlap lists (IoU > nms_iou, FP64) come from the per-frame-size geometry
-// in slot-major order nbr[s * npos + p]: one thread per candidate, so a
-// warp's load of slot s reads consecutive entries.  Each round walks a
+// twice: slot-major nbr[s * npos + p], read by one thread per candidate (a
+// warp's load of slot s reads consecutive entries), and position-major
+// nbr_t[p * MAXN + s], read by a warp walking one candidate's slots (a
+// lane per slot: consecutive entries again).  Each round walks a
 // compacted list of the still-undecided candidates, so sparse late rounds
 // cost little.  Ranks compare the key's high word (the score order) held in
 // shared memory; equal high words fall back to the full key in global
@@ -774,6 +776,7 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
     uint8_t *resume = base + off_supp + 4 * (size_t)nwords + npos;
     const uint64_t *gkeys = fd.keys;
     const int32_t *__restrict__ nbr = fd.nbr;                        // [slot][npos]
+    const int32_t *__restrict__ nbr_t = fd.nbr_t;                    // [npos][slot]
     const uint8_t *__restrict__ nbr_cnt = fd.nbr_cnt;
     const int lane = t & 31;
     int *s_n = sh + NT / 32 + 1;                                     // list sizes [2]
@@ -862,7 +865,7 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
                     const int sl = sb + lane;
                     uint32_t cls = 0;
                     if (sl < nn) {
-                        const int q = __ldg(nbr + (size_t)sl * npos + pp);
+                        const int q = __ldg(nbr_t + (size_t)pp * MAXN + sl);
                         const uint32_t hq = khi[q];
                         if (hq != NMS_NOKEY && above(q, pp, hq, hpp)) {
                             const uint8_t sq = state[q];
@@ -901,7 +904,7 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
                 const int pk = __shfl_sync(0xffffffffu, p, __ffs(km) - 1);
                 const int nk = __ldg(nbr_cnt + pk);
                 for (int s = lane; s < nk; s += 32) {
-                    const int q = __ldg(nbr + (size_t)s * npos + pk);
+                    const int q = __ldg(nbr_t + (size_t)pk * MAXN + s);
                     atomicOr(const_cast<uint32_t *>(supp) + (q >> 5), 1u << (q & 31));
                 }
             }

@@ -52,7 +52,8 @@ __device__ __forceinline__ int level_of(const int32_t *lev_pos, int nlev, int p)
 }  // namespace
 
 __global__ void __launch_bounds__(256) nms_geometry_kernel(GeomDesc g, int32_t *nbr,
-                                                           uint8_t *cnt, int *overflow) {
+                                                           int32_t *nbr_t, uint8_t *cnt,
+                                                           int *overflow) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.npos) return;
     const int l = level_of(g.lev_pos, g.nlev, p);
@@ -80,7 +81,10 @@ __global__ void __launch_bounds__(256) nms_geometry_kernel(GeomDesc g, int32_t *
                 if (q == p) continue;
                 const WinBox bq = window_box(g.lev_rx[m], g.lev_ry[m], uu, vv);
                 if (box_iou(bq, bp) > g.iou) {
-                    if (n < MAXN) nbr[(size_t)n * g.npos + p] = q;   // slot-major
+                    if (n < MAXN) {
+                        nbr[(size_t)n * g.npos + p] = q;     // slot-major
+                        nbr_t[(size_t)p * MAXN + n] = q;     // position-major
+                    }
                     n++;
                 }
             }
@@ -133,10 +137,11 @@ cudaError_t launch_pack(const hog_det *dets, int per_frame, const int32_t *count
     return cudaGetLastError();
 }
 
-cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, uint8_t *cnt, int *overflow,
+cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, int32_t *nbr_t, uint8_t *cnt,
+                                int *overflow,
                                 cudaStream_t stream) {
     if (g.npos <= 0) return cudaSuccess;
-    nms_geometry_kernel<<<(g.npos + 255) / 256, 256, 0, stream>>>(g, nbr, cnt, overflow);
+    nms_geometry_kernel<<<(g.npos + 255) / 256, 256, 0, stream>>>(g, nbr, nbr_t, cnt, overflow);
     return cudaGetLastError();
 }
 
@@ -232,6 +237,7 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
     uint8_t *resume = nsm + (size_t)P * 13 + 4 * (size_t)PW;                                 // [P]
     const uint64_t *gkeys = fd.keys;
     const int32_t *__restrict__ nbr = fd.nbr;
+    const int32_t *__restrict__ nbr_t = fd.nbr_t;
     const uint8_t *__restrict__ nbr_cnt = fd.nbr_cnt;
     int *s_n = sh + NMS_NT / 32 + 1;
     const float invP = P > 0 ? 1.0f / (float)P : 0.f;
@@ -326,7 +332,7 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
                 const int pk = __shfl_sync(0xffffffffu, p, __ffs(km) - 1);
                 const int nk = __ldg(nbr_cnt + pk);
                 for (int s = lane; s < nk; s += 32) {
-                    const int q = __ldg(nbr + (size_t)s * npos + pk);
+                    const int q = __ldg(nbr_t + (size_t)pk * MAXN + s);
                     const int o = owner(q);
                     const int lq = q - o * P;
                     cl_or_u32(s_rsupp[o] + 4u * (uint32_t)(lq >> 5), 1u << (lq & 31));
