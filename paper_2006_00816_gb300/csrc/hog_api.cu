@@ -350,6 +350,9 @@ int get_geometry(hog_ctx *ctx, int W, int H, cudaStream_t stream, Geometry **out
         }
         *ctx->h_flags = 0;
         cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), stream);
+        // slots past a position's count read -1 (the list's end)
+        cudaMemsetAsync(g->d_nbr, 0xff, (size_t)g->npos * MAXN * sizeof(int32_t), stream);
+        cudaMemsetAsync(g->d_nbr_t, 0xff, (size_t)g->npos * MAXN * sizeof(int32_t), stream);
         cudaError_t e = launch_nms_geometry(gd, g->d_nbr, g->d_nbr_t, g->d_cnt, ctx->d_flags, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int),
                                                   cudaMemcpyDeviceToHost, stream);

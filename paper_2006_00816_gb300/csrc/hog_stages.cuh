@@ -777,7 +777,6 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
     const uint64_t *gkeys = fd.keys;
     const int32_t *__restrict__ nbr = fd.nbr;                        // [slot][npos]
     const int32_t *__restrict__ nbr_t = fd.nbr_t;                    // [npos][slot]
-    const uint8_t *__restrict__ nbr_cnt = fd.nbr_cnt;
     const int lane = t & 31;
     int *s_n = sh + NT / 32 + 1;                                     // list sizes [2]
 
@@ -821,28 +820,30 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
         __syncthreads();
         for (int i0 = 0; i0 < n_cur; i0 += NT) {     // whole warps iterate together
             const int i = i0 + t;
-            bool undecided = false, kept = false, dead = false, wait = false;
-            int p = -1, n = 0, settled = 0;
+            bool undecided = false, kept = false, dead = false, wait = false, done = false;
+            int p = -1, settled = 0;
             uint32_t hp = 0;
             if (i < n_cur) {
                 p = list[cur][i];
-                n = __ldg(nbr_cnt + p);
                 hp = khi[p];
                 dead = (supp[p >> 5] >> (p & 31)) & 1u;
                 // scan the unsettled slots up to the first higher-ranked
                 // neighbour that is kept (p is suppressed) or undecided (p
                 // waits; a neighbour kept later marks p in the bitmask):
                 // four slots here, the rest by the whole warp below
+                // (a list ends at its first -1 slot: the tables are filled
+                // with -1 past each position's count, so no count is read)
                 const int r0 = resume[p];
                 settled = r0;   // end of the settled prefix of the slots
                 if (!dead) {
                     int q[4];
 #pragma unroll
                     for (int k = 0; k < 4; k++)
-                        q[k] = r0 + k < n ? __ldg(nbr + (size_t)(r0 + k) * npos + p) : -1;
+                        q[k] = r0 + k < MAXN ? __ldg(nbr + (size_t)(r0 + k) * npos + p) : -1;
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
-                        if (q[k] < 0 || dead || wait) continue;
+                        if (done || dead || wait) continue;
+                        if (q[k] < 0) { done = true; continue; }
                         const uint32_t hq = khi[q[k]];
                         uint8_t sq = NMS_DEAD;   // not above p: settled like a suppressed one
                         if (hq != NMS_NOKEY && above(q[k], p, hq, hp)) sq = state[q[k]];
@@ -854,18 +855,18 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
             }
             // candidates with slots left: the warp scans them one at a time,
             // a lane per slot, and takes the first unsettled slot in order
-            for (unsigned um = __ballot_sync(0xffffffffu, p >= 0 && !dead && !wait && settled < n); um;
+            for (unsigned um = __ballot_sync(0xffffffffu, p >= 0 && !dead && !wait && !done); um;
                  um &= um - 1) {
                 const int src = __ffs(um) - 1;
                 const int pp = __shfl_sync(0xffffffffu, p, src);
-                const int nn = __shfl_sync(0xffffffffu, n, src);
                 const uint32_t hpp = __shfl_sync(0xffffffffu, hp, src);
-                int res = 0, at = nn;   // 0: all settled, 1: kept neighbour, 2: undecided one
-                for (int sb = __shfl_sync(0xffffffffu, settled, src); sb < nn; sb += 32) {
+                int res = 0, at = 0;   // 0: all settled, 1: kept neighbour, 2: undecided one
+                for (int sb = __shfl_sync(0xffffffffu, settled, src);; sb += 32) {
                     const int sl = sb + lane;
+                    const int q = sl < MAXN ? __ldg(nbr_t + (size_t)pp * MAXN + sl) : -1;
+                    const unsigned end = __ballot_sync(0xffffffffu, q < 0);
                     uint32_t cls = 0;
-                    if (sl < nn) {
-                        const int q = __ldg(nbr_t + (size_t)pp * MAXN + sl);
+                    if (q >= 0) {
                         const uint32_t hq = khi[q];
                         if (hq != NMS_NOKEY && above(q, pp, hq, hpp)) {
                             const uint8_t sq = state[q];
@@ -873,10 +874,14 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
                         }
                     }
                     const unsigned hit = __ballot_sync(0xffffffffu, cls != 0);
-                    if (hit) {
+                    if (hit) {   // slots after the list's end are -1: a hit comes first
                         const int f = __ffs(hit) - 1;
                         res = (int)__shfl_sync(0xffffffffu, cls, f);
                         at = sb + f;
+                        break;
+                    }
+                    if (end) {
+                        at = sb + __ffs(end) - 1;
                         break;
                     }
                 }
@@ -902,10 +907,10 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
             // already: it could not be kept while one was undecided)
             for (unsigned km = __ballot_sync(0xffffffffu, kept); km; km &= km - 1) {
                 const int pk = __shfl_sync(0xffffffffu, p, __ffs(km) - 1);
-                const int nk = __ldg(nbr_cnt + pk);
-                for (int s = lane; s < nk; s += 32) {
-                    const int q = __ldg(nbr_t + (size_t)pk * MAXN + s);
-                    atomicOr(const_cast<uint32_t *>(supp) + (q >> 5), 1u << (q & 31));
+                for (int s = lane;; s += 32) {
+                    const int q = s < MAXN ? __ldg(nbr_t + (size_t)pk * MAXN + s) : -1;
+                    if (q >= 0) atomicOr(const_cast<uint32_t *>(supp) + (q >> 5), 1u << (q & 31));
+                    if (__ballot_sync(0xffffffffu, q < 0)) break;   // the list ended here
                 }
             }
             append(undecided, p, cur ^ 1);
