@@ -183,12 +183,14 @@ __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
 // ragged edges (the cells' sums do not depend on it).
 //
 // Orientation: fold (dx, dy) into the first quadrant; the sector q is the
-// number of bin boundaries (10, 30, 50, 70 degrees) the vector lies beyond,
-// tested in FP32 as |dy| > fl(|dx| tan(boundary)).  For every 8-bit
-// gradient this equals the exact test: the gap between |dy| and |dx|
-// tan(boundary) is at least 2.0e-3 on the integer grid, the rounding of the
-// product at most 4e-5.  dx == 0 (the only exact tie) goes to bin 4 (dy > 0)
-// or 13.  Branch-free: the quadrant is resolved with selects.
+// number of bin boundaries (10, 30, 50, 70 degrees) the vector lies beyond.
+// Each boundary test |dy| > |dx| tan(boundary) is one saturated FMA on the
+// floating-point pipe: sat(2^20 |dy| - 1024 - |dx| T), T = fl32(2^20
+// tan(boundary)), is exactly 1 or 0.  For every 8-bit gradient this equals
+// the exact test: |dy| - |dx| tan(boundary) is at least 2.0e-3 away from 0
+// on the integer grid (2097 after scaling), the margin is 1024 and the
+// error of T times |dx| at most 32, so the FMA's value is >= 1057 or <= -1024.
+// dx == 0 (the only exact tie) goes to bin 4 (dy > 0) or 13.
 namespace hist_cfg {
 constexpr int NT = HIST_NT;                    // 256 threads, one per block
 // staged rows of a bw-wide tile: its 8 * bh pixel rows + a 1-px halo; row
@@ -213,18 +215,19 @@ constexpr size_t SMEM = SMEM_PART + SMEM_SRC + SMEM_XB;             // 99,664
 static_assert(SMEM_SRC % 16 == 0, "staging must keep 16-byte alignment");
 }  // namespace hist_cfg
 
-__device__ __forceinline__ int orientation_bin_f(int dx, int dy) {
-    const float fx = (float)(dx < 0 ? -dx : dx);
-    const float fy = (float)(dy < 0 ? -dy : dy);
-    // tan 10, 30, 50, 70 degrees rounded to FP32
-    const int q = (fy > fx * 0.17632698f) + (fy > fx * 0.57735026f) + (fy > fx * 1.19175363f) +
-                  (fy > fx * 2.74747753f);
+// ax = |dx|, ay = |dy| as floats.
+__device__ __forceinline__ int orientation_bin_f(int dx, int dy, float ax, float ay) {
+    const float y = fmaf(ay, 1048576.0f, -1024.0f);   // 2^20 |dy| - 1024, exact
+    // 2^20 tan 10, 30, 50, 70 degrees rounded to FP32
+    const float q = __saturatef(fmaf(ax, -184892.234f, y)) + __saturatef(fmaf(ax, -605395.625f, y)) +
+                    __saturatef(fmaf(ax, -1249644.25f, y)) + __saturatef(fmaf(ax, -2880939.0f, y));
     // right half-plane (dx == 0: dy > 0 is on the right): bins q or 18 - q;
     // left: 9 - q or 9 + q
-    const bool right = dx > 0 || (dx == 0 && dy > 0);
-    const int base = right ? 0 : 9;
-    const int b = (right == (dy >= 0)) ? base + q : base - q;
-    return b < 0 ? b + 18 : b;
+    const bool up = dy >= 0, right = dx > 0 || (dx == 0 && dy > 0);
+    const float c = right ? (up ? 0.0f : 18.0f) : 9.0f;
+    const float s = right == up ? 1.0f : -1.0f;
+    const int b = __float_as_int(fmaf(s, q, c) + 8388608.0f) & 31;   // c + s q in 0..18
+    return b == 18 ? 0 : b;
 }
 
 // Tent weight of footprint offset t (0..15) in sixteenths: 16 - |2t - 15|.
@@ -308,9 +311,10 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         const uint8_t *dn = srcS + (r + 1) * srowb - xbase[r + 1];
         const float wy1 = tent16(oy), wy0 = tent16(oy + 8);   // to cell rows bi, bi-1
         auto vote = [&](int dx, int dy, int ox) {
-            const int b = orientation_bin_f(dx, dy);
-            const float sf = (float)(dx * dx + dy * dy);
-            const float m = sf * rsqrtf(fmaxf(sf, 1.0f));
+            const float ax = fabsf((float)dx), ay = fabsf((float)dy);
+            const int b = orientation_bin_f(dx, dy, ax, ay);
+            const float sf = fmaf(ax, ax, ay * ay);           // dx^2 + dy^2, exact
+            const float m = sf * rsqrtf(sf + 1e-30f);         // sqrt(sf); 0 for sf = 0
             const float m0 = m * wy0, m1 = m * wy1;
             float2 *pb = p0 + b * NT;
             float2 a = pb[0], c = pb[NBIN * NT];

@@ -1,11 +1,12 @@
-"""The CUDA histogram stage decides each pixel's orientation sector with the
-FP32 test |dy| > fl(|dx| tan(b)) for the four sector boundaries b = 10, 30,
-50, 70 degrees (Section 4.1.1: one of eighteen signed directions, nearest
-centre).  This checks, on the host, that the constants written in the
-kernel source make that test agree with the exact rule for every 8-bit
-gradient, i.e. that FP32 rounding never moves a vote to another bin, and
-that the resulting bin equals the oracle's FP64 bin for all 511^2 integer
-gradients."""
+"""The CUDA histogram stage decides each pixel's orientation sector with
+four saturated FP32 FMAs, sat(2^20 |dy| - 1024 - |dx| T) with T =
+fl32(2^20 tan(b)), for the sector boundaries b = 10, 30, 50, 70 degrees
+(Section 4.1.1: one of eighteen signed directions, nearest centre).  This
+checks, on the host, that the constants written in the kernel source make
+each FMA exactly 0 or 1 and equal to the exact test |dy| > |dx| tan(b) for
+every 8-bit gradient, i.e. that FP32 rounding never moves a vote to another
+bin, and that the resulting bin equals the oracle's FP64 bin for all 511^2
+integer gradients."""
 import math
 import os
 import re
@@ -18,32 +19,48 @@ SRC = os.path.join(os.path.dirname(__file__), "..", "paper_2006_00816_gb300", "c
 
 def _kernel_constants():
     txt = open(SRC).read()
-    body = txt[txt.index("orientation_bin_f(int dx, int dy)"):]
+    body = txt[txt.index("orientation_bin_f(int dx, int dy, float ax, float ay)"):]
     body = body[:body.index("}")]
-    vals = [float(v) for v in re.findall(r"fx \* ([0-9.]+)f", body)]
+    vals = [float(v) for v in re.findall(r"fmaf\(ax, -([0-9.]+)f, y\)", body)]
     assert len(vals) == 4, vals
+    assert "fmaf(ay, 1048576.0f, -1024.0f)" in body
     return np.array(vals, dtype=np.float32)
 
 
+def _fma_values(ax, ay, T):
+    """fl32(fma(|dx|, -T, 2^20 |dy| - 1024)) for each boundary: the product and
+    the difference are exact in FP64 (at most 32 significant bits), so one
+    rounding to FP32 is the FMA's."""
+    y = ay.astype(np.float64) * 1048576.0 - 1024.0
+    return [(y - ax.astype(np.float64) * np.float64(t)).astype(np.float32) for t in T]
+
+
 def _sector_fp32(ax, ay, T):
-    fx = ax.astype(np.float32)
-    fy = ay.astype(np.float32)
     q = np.zeros(ax.shape, np.int64)
-    for t in T:
-        q += fy > (fx * t).astype(np.float32)      # one FP32 product, then an exact compare
+    for v in _fma_values(ax, ay, T):
+        q += np.clip(v, 0.0, 1.0).astype(np.int64)     # saturate: 0 or 1 (checked below)
     return q
 
 
 def _bin(dx, dy, q):
     right = (dx > 0) | ((dx == 0) & (dy > 0))
-    base = np.where(right, 0, 9)
-    b = np.where(right == (dy >= 0), base + q, base - q)
-    return np.where(b < 0, b + 18, b)
+    up = dy >= 0
+    c = np.where(right, np.where(up, 0, 18), 9)
+    b = np.where(right == up, c + q, c - q)
+    return np.where(b == 18, 0, b)
 
 
-def test_fp32_sector_test_is_exact_on_8bit_gradients():
+def test_fma_values_saturate_to_0_or_1():
     T = _kernel_constants()
-    assert np.allclose(T, np.tan(np.deg2rad([10, 30, 50, 70])), rtol=1e-7)
+    assert np.allclose(T / 1048576.0, np.tan(np.deg2rad([10, 30, 50, 70])), rtol=1e-7)
+    ax, ay = np.meshgrid(np.arange(256), np.arange(256), indexing="ij")
+    for v in _fma_values(ax, ay, T):
+        assert not ((v > 0.0) & (v < 1.0)).any()
+        assert v[v > 0].min() > 1000.0 and v[v <= 0].max() <= -1000.0
+
+
+def test_fma_sector_test_is_exact_on_8bit_gradients():
+    T = _kernel_constants()
     ax, ay = np.meshgrid(np.arange(256), np.arange(256), indexing="ij")
     q = _sector_fp32(ax, ay, T)
     exact = np.zeros_like(q)
@@ -53,7 +70,7 @@ def test_fp32_sector_test_is_exact_on_8bit_gradients():
     assert np.array_equal(q, exact)
 
 
-def test_fp32_bins_equal_oracle_bins(oracle):
+def test_fma_bins_equal_oracle_bins(oracle):
     T = _kernel_constants()
     dx, dy = np.meshgrid(np.arange(-255, 256), np.arange(-255, 256), indexing="ij")
     dx, dy = dx.ravel(), dy.ravel()
