@@ -215,19 +215,29 @@ constexpr size_t SMEM = SMEM_PART + SMEM_SRC + SMEM_XB;             // 99,664
 static_assert(SMEM_SRC % 16 == 0, "staging must keep 16-byte alignment");
 }  // namespace hist_cfg
 
-// ax = |dx|, ay = |dy| as floats.
-__device__ __forceinline__ int orientation_bin_f(int dx, int dy, float ax, float ay) {
+// dxf, dyf: the gradient as floats (exact integers, +0 for a zero part).
+__device__ __forceinline__ int orientation_bin_f(float dxf, float dyf) {
+    const float ax = fabsf(dxf), ay = fabsf(dyf);
     const float y = fmaf(ay, 1048576.0f, -1024.0f);   // 2^20 |dy| - 1024, exact
     // 2^20 tan 10, 30, 50, 70 degrees rounded to FP32
     const float q = __saturatef(fmaf(ax, -184892.234f, y)) + __saturatef(fmaf(ax, -605395.625f, y)) +
                     __saturatef(fmaf(ax, -1249644.25f, y)) + __saturatef(fmaf(ax, -2880939.0f, y));
-    // right half-plane (dx == 0: dy > 0 is on the right): bins q or 18 - q;
-    // left: 9 - q or 9 + q
-    const bool up = dy >= 0, right = dx > 0 || (dx == 0 && dy > 0);
-    const float c = right ? (up ? 0.0f : 18.0f) : 9.0f;
-    const float s = right == up ? 1.0f : -1.0f;
-    const int b = __float_as_int(fmaf(s, q, c) + 8388608.0f) & 31;   // c + s q in 0..18
+    // quadrant: right half-plane (dx > 0, or dx == 0 and dy > 0): q or
+    // 18 - q; left: 9 - q (dy >= 0) or 9 + q.  With sR, sU = +-1 for right
+    // and dy >= 0 that is b = 9 + sU (sR (q - 4.5) - 4.5), the signs applied
+    // as sign-bit flips; dx + 2^-20 dy carries the sign of dx, or of dy
+    // where dx == 0.
+    const uint32_t sr = __float_as_uint(fmaf(dyf, 9.5367431640625e-07f, dxf)) & 0x80000000u;
+    const uint32_t su = __float_as_uint(dyf) & 0x80000000u;
+    const float t = __uint_as_float(__float_as_uint(q - 4.5f) ^ sr) - 4.5f;
+    const int b = __float_as_int(__uint_as_float(__float_as_uint(t) ^ su) + 8388617.0f) & 31;   // 0..18
     return b == 18 ? 0 : b;
+}
+
+// Byte k (0..3) of w as the float 2^23 + byte: the difference of two such
+// floats is the bytes' difference, exactly.
+__device__ __forceinline__ float byte_f23(uint32_t w, int k) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (unsigned)k));
 }
 
 // Tent weight of footprint offset t (0..15) in sixteenths: 16 - |2t - 15|.
@@ -297,9 +307,10 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
     // base and pitch multiples of 8), byte X0 of every staged row lies at a
     // shared address = 4 (mod 8).  A thread then reads its 10 middle-row
     // bytes (X0-1 .. X0+8) inside two 8-byte words and its 8 upper and lower
-    // bytes as two 4-byte words each, and takes the bytes apart in
-    // registers: 6 shared loads per pixel row instead of 26 byte loads,
-    // whose 8-byte lane stride put a warp's two block rows on the same banks.
+    // bytes as two 4-byte words each: 6 shared loads per pixel row instead
+    // of 26 byte loads, whose 8-byte lane stride put a warp's two block rows
+    // on the same banks.  Each byte becomes the float 2^23 + byte with one
+    // byte permute, so dx and dy are float subtractions (byte_f23).
     const bool words = ((uintptr_t)d.img & 7) == 0 && (d.pitch & 7) == 0;
 #pragma unroll 1
     for (int oy = 0; oy < 8; oy++) {
@@ -310,10 +321,9 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         const uint8_t *mid = srcS + r * srowb - xbase[r];
         const uint8_t *dn = srcS + (r + 1) * srowb - xbase[r + 1];
         const float wy1 = tent16(oy), wy0 = tent16(oy + 8);   // to cell rows bi, bi-1
-        auto vote = [&](int dx, int dy, int ox) {
-            const float ax = fabsf((float)dx), ay = fabsf((float)dy);
-            const int b = orientation_bin_f(dx, dy, ax, ay);
-            const float sf = fmaf(ax, ax, ay * ay);           // dx^2 + dy^2, exact
+        auto vote = [&](float dxf, float dyf, int ox) {
+            const int b = orientation_bin_f(dxf, dyf);
+            const float sf = fmaf(dxf, dxf, dyf * dyf);       // dx^2 + dy^2, exact
             const float m = sf * rsqrtf(sf + 1e-30f);         // sqrt(sf); 0 for sf = 0
             const float m0 = m * wy0, m1 = m * wy1;
             float2 *pb = p0 + b * NT;
@@ -336,17 +346,14 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
 #pragma unroll
             for (int ox = 0; ox < 8; ox++) {
                 const int kr = ox + 5, kl = ox + 3;     // bytes X0+ox+1, X0+ox-1 of mw
-                const int dx = (int)((mw[kr >> 2] >> (8 * (kr & 3))) & 255u) -
-                               (int)((mw[kl >> 2] >> (8 * (kl & 3))) & 255u);
-                const int dy = (int)((dw[ox >> 2] >> (8 * (ox & 3))) & 255u) -
-                               (int)((uw[ox >> 2] >> (8 * (ox & 3))) & 255u);
-                vote(dx, dy, ox);
+                vote(byte_f23(mw[kr >> 2], kr & 3) - byte_f23(mw[kl >> 2], kl & 3),
+                     byte_f23(dw[ox >> 2], ox & 3) - byte_f23(uw[ox >> 2], ox & 3), ox);
             }
         } else {
 #pragma unroll
             for (int ox = 0; ox < 8; ox++) {
                 const int X = X0 + ox;
-                vote((int)mid[X + 1] - (int)mid[X - 1], (int)dn[X] - (int)up[X], ox);
+                vote((float)((int)mid[X + 1] - (int)mid[X - 1]), (float)((int)dn[X] - (int)up[X]), ox);
             }
         }
     }

@@ -19,11 +19,13 @@ SRC = os.path.join(os.path.dirname(__file__), "..", "paper_2006_00816_gb300", "c
 
 def _kernel_constants():
     txt = open(SRC).read()
-    body = txt[txt.index("orientation_bin_f(int dx, int dy, float ax, float ay)"):]
-    body = body[:body.index("}")]
+    body = txt[txt.index("orientation_bin_f(float dxf, float dyf)"):]
+    body = body[:body.index("\n}")]
     vals = [float(v) for v in re.findall(r"fmaf\(ax, -([0-9.]+)f, y\)", body)]
     assert len(vals) == 4, vals
     assert "fmaf(ay, 1048576.0f, -1024.0f)" in body
+    assert "fmaf(dyf, 9.5367431640625e-07f, dxf)" in body and "- 4.5f" in body
+    assert "+ 8388617.0f" in body
     return np.array(vals, dtype=np.float32)
 
 
@@ -43,10 +45,13 @@ def _sector_fp32(ax, ay, T):
 
 
 def _bin(dx, dy, q):
-    right = (dx > 0) | ((dx == 0) & (dy > 0))
-    up = dy >= 0
-    c = np.where(right, np.where(up, 0, 18), 9)
-    b = np.where(right == up, c + q, c - q)
+    """The kernel's quadrant step: b = 9 + sU (sR (q - 4.5) - 4.5), sR the sign
+    of dx + 2^-20 dy (exact here in FP64; its sign is the FP32 FMA's), sU the
+    sign of dy, +1 for zero; 18 wraps to 0."""
+    xs = dx.astype(np.float64) + dy.astype(np.float64) * 2.0 ** -20
+    sr = np.where(xs < 0, -1.0, 1.0)
+    su = np.where(dy < 0, -1.0, 1.0)
+    b = (9.0 + su * (sr * (q - 4.5) - 4.5)).astype(np.int64)
     return np.where(b == 18, 0, b)
 
 
