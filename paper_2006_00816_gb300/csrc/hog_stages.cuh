@@ -209,14 +209,20 @@ constexpr size_t src_bytes_max() {
 }
 constexpr int PY_MAX = py_of(HIST_BW_MIN);                          // 290 rows
 constexpr size_t SMEM_SRC = src_bytes_max();                        // 24,768 (bw = 8)
-constexpr size_t SMEM_PART = sizeof(float) * 4 * NBIN * NT;         // 73,728
+constexpr int PB = NBIN + 1;                   // partial rows: bins 0..17 and 18 (= bin 0)
+constexpr size_t SMEM_PART = sizeof(float) * 4 * PB * NT;           // 77,824
 constexpr size_t SMEM_XB = sizeof(int) * ((PY_MAX + 3) / 4 * 4);    // 1,168
-constexpr size_t SMEM = SMEM_PART + SMEM_SRC + SMEM_XB;             // 99,664
+constexpr size_t SMEM = SMEM_PART + SMEM_SRC + SMEM_XB;             // 103,760
 static_assert(SMEM_SRC % 16 == 0, "staging must keep 16-byte alignment");
 }  // namespace hist_cfg
 
 // dxf, dyf: the gradient as floats (exact integers, +0 for a zero part).
-__device__ __forceinline__ int orientation_bin_f(float dxf, float dyf) {
+// Returns b * S for the bin b in 0..18 (18 is bin 0, taken apart by the
+// caller) and a power of two S <= 2^18: 2^23 + b S is formed exactly in a
+// float and its low mantissa bits are b S.
+template <uint32_t S>
+__device__ __forceinline__ uint32_t orientation_bin_f(float dxf, float dyf) {
+    static_assert(S > 0 && S <= (1u << 18) && (S & (S - 1)) == 0, "S: a power of two <= 2^18");
     const float ax = fabsf(dxf), ay = fabsf(dyf);
     const float y = fmaf(ay, 1048576.0f, -1024.0f);   // 2^20 |dy| - 1024, exact
     // 2^20 tan 10, 30, 50, 70 degrees rounded to FP32
@@ -230,8 +236,8 @@ __device__ __forceinline__ int orientation_bin_f(float dxf, float dyf) {
     const uint32_t sr = __float_as_uint(fmaf(dyf, 9.5367431640625e-07f, dxf)) & 0x80000000u;
     const uint32_t su = __float_as_uint(dyf) & 0x80000000u;
     const float t = __uint_as_float(__float_as_uint(q - 4.5f) ^ sr) - 4.5f;
-    const int b = __float_as_int(__uint_as_float(__float_as_uint(t) ^ su) + 8388617.0f) & 31;   // 0..18
-    return b == 18 ? 0 : b;
+    return __float_as_uint(fmaf(__uint_as_float(__float_as_uint(t) ^ su), (float)S,
+                                8388608.0f + 9.0f * (float)S)) & 0x7FFFFFu;   // (9 + sU t) S
 }
 
 // Byte k (0..3) of w as the float 2^23 + byte: the difference of two such
@@ -249,7 +255,9 @@ __host__ __device__ constexpr float tent16(int t) {
 // image with cp.async.cg (through L2), so it is coherent within a launch.
 __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned char *smem) {
     using namespace hist_cfg;
-    // partials [corner pair][18][NT] of float2: .x corner 2p, .y corner 2p+1
+    // partials [corner pair][19][NT] of float2: .x corner 2p, .y corner 2p+1;
+    // row 18 collects bin 0's votes from below the positive x axis (bin
+    // 18 - q at q = 0) and is added to row 0 when the cells are combined
     float2 *part = reinterpret_cast<float2 *>(smem);
     uint8_t *srcS = smem + SMEM_PART;                          // [py][srowb]
     int *xbase = reinterpret_cast<int *>(smem + SMEM_PART + SMEM_SRC);
@@ -280,7 +288,7 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         if (ci == 0) xbase[r] = (int)((intptr_t)c0 - (intptr_t)rp);
         if (a <= rp + (uintptr_t)(xb - 1)) cp_async16(srcS + r * srowb + 16 * ci, (const void *)a);
     }
-    for (int k = t; k < NBIN * NT; k += NT) reinterpret_cast<float4 *>(part)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = t; k < PB * NT; k += NT) reinterpret_cast<float4 *>(part)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     cp_async_wait_all();
     __syncthreads();
 
@@ -322,18 +330,18 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         const uint8_t *dn = srcS + (r + 1) * srowb - xbase[r + 1];
         const float wy1 = tent16(oy), wy0 = tent16(oy + 8);   // to cell rows bi, bi-1
         auto vote = [&](float dxf, float dyf, int ox) {
-            const int b = orientation_bin_f(dxf, dyf);
+            const uint32_t boff = orientation_bin_f<NT * sizeof(float2)>(dxf, dyf);   // bytes
             const float sf = fmaf(dxf, dxf, dyf * dyf);       // dx^2 + dy^2, exact
             const float m = sf * rsqrtf(sf + 1e-30f);         // sqrt(sf); 0 for sf = 0
             const float m0 = m * wy0, m1 = m * wy1;
-            float2 *pb = p0 + b * NT;
-            float2 a = pb[0], c = pb[NBIN * NT];
+            float2 *pb = reinterpret_cast<float2 *>(reinterpret_cast<char *>(p0) + boff);
+            float2 a = pb[0], c = pb[PB * NT];
             a.x = fmaf(m0, wx0v[ox], a.x);   // cell (bi-1, bj-1)
             a.y = fmaf(m0, wx1v[ox], a.y);   // cell (bi-1, bj)
             c.x = fmaf(m1, wx0v[ox], c.x);   // cell (bi,   bj-1)
             c.y = fmaf(m1, wx1v[ox], c.y);   // cell (bi,   bj)
             pb[0] = a;
-            pb[NBIN * NT] = c;
+            pb[PB * NT] = c;
         };
         if (words) {
             const uint2 ma = *reinterpret_cast<const uint2 *>(mid + X0 - 4);   // X0-4 .. X0+3
@@ -367,10 +375,16 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         const int b00 = ci * bw + cj;
 #pragma unroll
         for (int b = 0; b < NBIN; b++) {
-            const float s3 = part[(1 * NBIN + b) * NT + b00].y;
-            const float s2 = part[(1 * NBIN + b) * NT + b00 + 1].x;
-            const float s1 = part[(0 * NBIN + b) * NT + b00 + bw].y;
-            const float s0 = part[(0 * NBIN + b) * NT + b00 + bw + 1].x;
+            float s3 = part[(1 * PB + b) * NT + b00].y;
+            float s2 = part[(1 * PB + b) * NT + b00 + 1].x;
+            float s1 = part[(0 * PB + b) * NT + b00 + bw].y;
+            float s0 = part[(0 * PB + b) * NT + b00 + bw + 1].x;
+            if (b == 0) {   // row 18: the rest of bin 0
+                s3 += part[(1 * PB + NBIN) * NT + b00].y;
+                s2 += part[(1 * PB + NBIN) * NT + b00 + 1].x;
+                s1 += part[(0 * PB + NBIN) * NT + b00 + bw].y;
+                s0 += part[(0 * PB + NBIN) * NT + b00 + bw + 1].x;
+            }
             outS[t * NBIN + b] = (s3 + s2) + (s1 + s0);
         }
     }

@@ -25,7 +25,7 @@ def _kernel_constants():
     assert len(vals) == 4, vals
     assert "fmaf(ay, 1048576.0f, -1024.0f)" in body
     assert "fmaf(dyf, 9.5367431640625e-07f, dxf)" in body and "- 4.5f" in body
-    assert "+ 8388617.0f" in body
+    assert "8388608.0f + 9.0f * (float)S" in body and "& 0x7FFFFFu" in body
     return np.array(vals, dtype=np.float32)
 
 
@@ -47,12 +47,12 @@ def _sector_fp32(ax, ay, T):
 def _bin(dx, dy, q):
     """The kernel's quadrant step: b = 9 + sU (sR (q - 4.5) - 4.5), sR the sign
     of dx + 2^-20 dy (exact here in FP64; its sign is the FP32 FMA's), sU the
-    sign of dy, +1 for zero; 18 wraps to 0."""
+    sign of dy, +1 for zero; 18 is bin 0."""
     xs = dx.astype(np.float64) + dy.astype(np.float64) * 2.0 ** -20
     sr = np.where(xs < 0, -1.0, 1.0)
     su = np.where(dy < 0, -1.0, 1.0)
     b = (9.0 + su * (sr * (q - 4.5) - 4.5)).astype(np.int64)
-    return np.where(b == 18, 0, b)
+    return np.where(b == 18, 0, b)          # the kernel's partial row 18 is added to bin 0
 
 
 def test_fma_values_saturate_to_0_or_1():
