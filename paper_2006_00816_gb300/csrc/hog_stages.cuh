@@ -737,10 +737,18 @@ __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ desc
 // compacted list of the still-undecided candidates, so sparse late rounds
 // cost little.  Ranks compare the key's high word (the score order) held in
 // shared memory; equal high words fall back to the full key in global
-// memory.  Workspace (nms_ws_bytes): in shared memory (SM, candidate lists of
-// 16-bit positions) or in fd.ws (32-bit positions).  NT threads.
+// memory; a decision overwrites the candidate's high word (kept: 0, above
+// every key; suppressed: all ones, below every key), so no state is kept
+// apart.  After each round the list of undecided candidates is rebuilt from
+// the high words in position order.  Workspace (nms_ws_bytes): in shared
+// memory (SM, a list of 16-bit positions) or in fd.ws (32-bit positions).
+// NT threads.
+// candidate states of the cluster form's state bytes
 constexpr uint8_t NMS_ALIVE = 1, NMS_KEPT = 2, NMS_DEAD = 0;
-constexpr uint32_t NMS_NOKEY = 0xffffffffu;   // key high word of a non-candidate
+constexpr uint32_t NMS_NOKEY = 0xffffffffu;   // key high word of a non-candidate (or a suppressed one)
+// key high word of a kept candidate: below every real high word, which is at
+// least 0x00800000 (the complemented order of a finite score)
+constexpr uint32_t NMS_KEPTKEY = 0u;
 
 struct WinBox {
     double x, y, w, h;
@@ -759,11 +767,12 @@ __device__ __forceinline__ WinBox window_box(double rx, double ry, int u, int v)
     return b;
 }
 
-// Workspace per frame: key high words (4 B per position), two candidate
-// lists (2 B per position each in shared memory, 4 B in global memory), the
-// suppression bitmask (1 bit), state and resume slot (1 B each).
+// Workspace per frame: key high words, which also record decisions (4 B per
+// position), the candidate list (2 B per position in shared memory, 4 B in
+// global memory), the suppression bitmask (1 bit) and the resume slot (1 B).
+// 640x480 frames (9,537 positions) take 68 KB: three CTAs per SM.
 __host__ __device__ constexpr size_t nms_ws_bytes(int npos, bool in_smem) {
-    return (size_t)npos * (in_smem ? 10 : 14) + 4 * (size_t)((npos + 31) / 32) + 64;
+    return (size_t)npos * (in_smem ? 7 : 9) + 4 * (size_t)((npos + 31) / 32) + 64;
 }
 // Positions a shared-memory workspace can index (16-bit list entries).
 constexpr int NMS_SMEM_MAX_NPOS = 65535;
@@ -786,70 +795,93 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
     const int t = threadIdx.x;
     const int npos = fd.npos;
     unsigned char *base = SM ? smem : reinterpret_cast<unsigned char *>(fd.ws);
-    uint32_t *khi = reinterpret_cast<uint32_t *>(base);              // key high words
-    idx_t *list[2] = {reinterpret_cast<idx_t *>(base + 4 * (size_t)npos),   // undecided
-                      reinterpret_cast<idx_t *>(base + 4 * (size_t)npos) + npos};   // (double buffer)
+    // key high word of each position while it is undecided; its decision
+    // overwrites it: NMS_KEPTKEY (above every key) or NMS_NOKEY (below every
+    // key, as for a position that never had one)
+    volatile uint32_t *khi = reinterpret_cast<volatile uint32_t *>(base);
+    idx_t *list = reinterpret_cast<idx_t *>(base + 4 * (size_t)npos);   // undecided, position order
     // suppression bitmask: bit q set once a neighbour of q has been kept, so
     // q (if ranked below it) is suppressed without scanning its neighbours
     const int nwords = (npos + 31) / 32;
-    const size_t off_supp = (size_t)npos * (4 + 2 * sizeof(idx_t));
+    const size_t off_supp = ((size_t)npos * (4 + sizeof(idx_t)) + 3) & ~(size_t)3;
     volatile uint32_t *supp = reinterpret_cast<volatile uint32_t *>(base + off_supp);
-    volatile uint8_t *state = base + off_supp + 4 * (size_t)nwords;
     // per candidate: how many leading neighbour slots are settled for good
     // (not a candidate, ranked below, or suppressed); later rounds resume
     // the scan there.  Written and read by the candidate's own thread only.
-    uint8_t *resume = base + off_supp + 4 * (size_t)nwords + npos;
+    uint8_t *resume = base + off_supp + 4 * (size_t)nwords;
     const uint64_t *gkeys = fd.keys;
     const int32_t *__restrict__ nbr = fd.nbr;                        // [slot][npos]
     const int32_t *__restrict__ nbr_t = fd.nbr_t;                    // [npos][slot]
-    const int lane = t & 31;
-    int *s_n = sh + NT / 32 + 1;                                     // list sizes [2]
+    const int lane = t & 31, wid = t >> 5;
+    int *s_total = sh + NT / 32;
 
     // q ranked above p (smaller key)
     auto above = [&](int q, int p, uint32_t hq, uint32_t hp) -> bool {
         if (hq != hp) return hq < hp;
         return ld_in<COH>(gkeys + q) < ld_in<COH>(gkeys + p);
     };
-    // warp-aggregated append of p (when flag) to list[which]
-    auto append = [&](bool flag, int p, int which) {
-        const unsigned m = __ballot_sync(0xffffffffu, flag);
-        if (!m) return;
-        int b0 = 0;
-        if (lane == __ffs(m) - 1) b0 = atomicAdd(s_n + which, __popc(m));
-        b0 = __shfl_sync(0xffffffffu, b0, __ffs(m) - 1);
-        if (flag) list[which][b0 + __popc(m & ((1u << lane) - 1))] = (idx_t)p;
+    // exclusive prefix sum of one count per thread over the block (thread
+    // order); *s_total = the sum
+    auto block_scan = [&](int mine) -> int {
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) sh[wid] = incl;
+        __syncthreads();
+        if (t == 0) {
+            int run = 0;
+            for (int k = 0; k < NT / 32; k++) {
+                const int x = sh[k];
+                sh[k] = run;
+                run += x;
+            }
+            *s_total = run;
+        }
+        __syncthreads();
+        return sh[wid] + incl - mine;
+    };
+    // thread t's share of the positions: [beg, end)
+    const int per = (npos + NT - 1) / NT;
+    const int beg = min(t * per, npos), end = min(beg + per, npos);
+    auto undecided_at = [&](int p) {
+        const uint32_t h = khi[p];
+        return h != NMS_KEPTKEY && h != NMS_NOKEY;
+    };
+    // the list of undecided positions, rebuilt from the key words (a stable
+    // scan: it reads khi and writes the list, so no entry is overwritten
+    // before it is read); returns its length
+    auto build_list = [&]() -> int {
+        int mine = 0;
+        for (int p = beg; p < end; p++) mine += undecided_at(p);
+        int o = block_scan(mine);
+        const int n = *s_total;
+        for (int p = beg; p < end; p++)
+            if (undecided_at(p)) list[o++] = (idx_t)p;
+        __syncthreads();
+        return n;
     };
 
-    if (t == 0) { s_n[0] = 0; s_n[1] = 0; }
     for (int k = t; k < nwords; k += NT) supp[k] = 0u;
-    __syncthreads();
-    for (int p0 = 0; p0 < npos; p0 += NT) {          // whole warps iterate together
-        const int p = p0 + t;
-        uint32_t h = NMS_NOKEY;
-        if (p < npos) {
-            // positions of levels that are not scanned carry no key
-            if (nms_scanned(fd, p)) h = (uint32_t)(ld_in<COH>(gkeys + p) >> 32);
-            khi[p] = h;
-            state[p] = h != NMS_NOKEY ? NMS_ALIVE : NMS_DEAD;
-            resume[p] = 0;
-        }
-        append(h != NMS_NOKEY, p, 0);
+    for (int p = t; p < npos; p += NT) {
+        // positions of levels that are not scanned carry no key
+        khi[p] = nms_scanned(fd, p) ? (uint32_t)(ld_in<COH>(gkeys + p) >> 32) : NMS_NOKEY;
+        resume[p] = 0;
     }
     __syncthreads();
+    int n_cur = build_list();
 
-    int cur = 0, round = 0;
-    for (; round <= npos; round++) {
-        const int n_cur = s_n[cur];
-        if (n_cur == 0) break;
-        if (t == 0) s_n[cur ^ 1] = 0;
-        __syncthreads();
+    int round = 0;
+    for (; round <= npos && n_cur > 0; round++) {
         for (int i0 = 0; i0 < n_cur; i0 += NT) {     // whole warps iterate together
             const int i = i0 + t;
-            bool undecided = false, kept = false, dead = false, wait = false, done = false;
+            bool kept = false, dead = false, wait = false, done = false;
             int p = -1, settled = 0;
             uint32_t hp = 0;
             if (i < n_cur) {
-                p = list[cur][i];
+                p = list[i];
                 hp = khi[p];
                 dead = (supp[p >> 5] >> (p & 31)) & 1u;
                 // scan the unsettled slots up to the first higher-ranked
@@ -869,11 +901,12 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
                     for (int k = 0; k < 4; k++) {
                         if (done || dead || wait) continue;
                         if (q[k] < 0) { done = true; continue; }
+                        // a kept neighbour ranks above p (p could not be
+                        // undecided otherwise); an undecided one above p
+                        // makes p wait; the rest are settled
                         const uint32_t hq = khi[q[k]];
-                        uint8_t sq = NMS_DEAD;   // not above p: settled like a suppressed one
-                        if (hq != NMS_NOKEY && above(q[k], p, hq, hp)) sq = state[q[k]];
-                        if (sq == NMS_KEPT) dead = true;
-                        else if (sq == NMS_ALIVE) wait = true;
+                        if (hq == NMS_KEPTKEY) dead = true;
+                        else if (hq != NMS_NOKEY && above(q[k], p, hq, hp)) wait = true;
                         else settled = r0 + k + 1;
                     }
                 }
@@ -893,10 +926,8 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
                     uint32_t cls = 0;
                     if (q >= 0) {
                         const uint32_t hq = khi[q];
-                        if (hq != NMS_NOKEY && above(q, pp, hq, hpp)) {
-                            const uint8_t sq = state[q];
-                            cls = sq == NMS_KEPT ? 1u : (sq == NMS_ALIVE ? 2u : 0u);
-                        }
+                        if (hq == NMS_KEPTKEY) cls = 1u;
+                        else if (hq != NMS_NOKEY && above(q, pp, hq, hpp)) cls = 2u;
                     }
                     const unsigned hit = __ballot_sync(0xffffffffu, cls != 0);
                     if (hit) {   // slots after the list's end are -1: a hit comes first
@@ -918,12 +949,11 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
             }
             if (p >= 0) {
                 if (dead) {
-                    state[p] = NMS_DEAD;
+                    khi[p] = NMS_NOKEY;
                 } else if (!wait) {
-                    state[p] = NMS_KEPT;
+                    khi[p] = NMS_KEPTKEY;
                     kept = true;
                 } else {
-                    undecided = true;
                     resume[p] = (uint8_t)settled;
                 }
             }
@@ -938,41 +968,18 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
                     if (__ballot_sync(0xffffffffu, q < 0)) break;   // the list ended here
                 }
             }
-            append(undecided, p, cur ^ 1);
         }
         __syncthreads();
-        cur ^= 1;
+        n_cur = build_list();
     }
 
-    // compact kept positions in position order
-    const int wid = t >> 5;
-    int *s_total = sh + NT / 32;
-    const int per = (npos + NT - 1) / NT;
-    const int beg = min(t * per, npos), end = min(beg + per, npos);
+    // kept positions in position order
     int mine = 0;
-    for (int p = beg; p < end; p++) mine += state[p] == NMS_KEPT;
-    int incl = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) sh[wid] = incl;
-    __syncthreads();
-    if (t == 0) {
-        int run = 0;
-        for (int k = 0; k < NT / 32; k++) {
-            const int x = sh[k];
-            sh[k] = run;
-            run += x;
-        }
-        *s_total = run;
-    }
-    __syncthreads();
+    for (int p = beg; p < end; p++) mine += khi[p] == NMS_KEPTKEY;
+    int pos = block_scan(mine);
     const int total = *s_total;
-    int pos = sh[wid] + incl - mine;
     for (int p = beg; p < end; p++) {
-        if (state[p] != NMS_KEPT) continue;
+        if (khi[p] != NMS_KEPTKEY) continue;
         if (pos < fd.out_cap) {
             const uint64_t k = ld_in<COH>(gkeys + p);
             const int l = key_level(k);

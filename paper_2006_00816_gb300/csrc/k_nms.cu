@@ -27,7 +27,7 @@ namespace hogk {
 
 namespace {
 constexpr int NMS_NT = 1024;         // cluster form: threads per CTA
-constexpr int NMS_BATCH_NT = 512;    // one CTA per frame: two CTAs per SM for 640x480 frames
+constexpr int NMS_BATCH_NT = 512;    // one CTA per frame: three CTAs per SM for 640x480 frames
 constexpr int NMS_SMEM_MAX = 200 * 1024;   // dynamic shared memory for keys and states
 
 __device__ __forceinline__ double box_iou(const WinBox &a, const WinBox &b) {
@@ -97,11 +97,12 @@ __global__ void __launch_bounds__(256) nms_geometry_kernel(GeomDesc g, int32_t *
     cnt[p] = (uint8_t)n;
 }
 
+// Three CTAs per SM with the workspace in shared memory (40 registers).
 template <bool SM>
-__global__ void __launch_bounds__(NMS_BATCH_NT) nms_kernel(const FrameDesc *__restrict__ frames,
-                                                           int *flags) {
+__global__ void __launch_bounds__(NMS_BATCH_NT, SM ? 3 : 2)
+    nms_kernel(const FrameDesc *__restrict__ frames, int *flags) {
     extern __shared__ __align__(16) unsigned char nsm[];
-    __shared__ int sh[NMS_BATCH_NT / 32 + 4];   // warp sums, total, two list sizes
+    __shared__ int sh[NMS_BATCH_NT / 32 + 4];   // warp sums, total
     nms_frame<SM, NMS_BATCH_NT, false>(frames[blockIdx.x], nsm, flags, sh);
 }
 
@@ -493,6 +494,9 @@ cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(nms_kernel<true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, NMS_SMEM_MAX);
+        if (e == cudaSuccess)   // all of the unified L1 as shared memory: three frames per SM
+            e = cudaFuncSetAttribute(nms_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         configured = true;
     }
