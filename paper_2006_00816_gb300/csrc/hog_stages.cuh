@@ -428,22 +428,34 @@ __device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float ep
     const int j0 = (tile % ntx) * FEAT_TX, i0 = (tile / ntx) * FEAT_TY;
     const int t = threadIdx.x;
 
-    // stage the tile's cells and their one-cell halo, one cell (18 floats,
-    // 72 bytes: nine 8-byte loads) per thread and step; zero outside the grid
-    for (int k = t; k < HY * HX; k += NT) {
+    // stage the tile's cells and their one-cell halo (HY * HX <= 2 NT cells):
+    // a thread takes cells t and t + NT, 18 floats (72 bytes: nine 8-byte
+    // loads) each, and issues all its loads before storing, so the tile's
+    // loads are in flight together; zero outside the grid
+    static_assert(HY * HX <= 2 * NT, "two halo cells per thread");
+    float2 v[2][NBIN / 2];
+    bool in[2];
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        const int k = t + s * NT;
         const int r = k / HX, c = k - r * HX;
         const int i = i0 - 1 + r, j = j0 - 1 + c;
-        float *dst = hS + k * CS;
-        if (i >= 0 && i < d.cy && j >= 0 && j < d.cx) {
+        in[s] = k < HY * HX && i >= 0 && i < d.cy && j >= 0 && j < d.cx;
+        if (in[s]) {
             const float2 *src = reinterpret_cast<const float2 *>(d.hist + ((size_t)i * d.cx + j) * NBIN);
-            float2 v[NBIN / 2];
 #pragma unroll
-            for (int q = 0; q < NBIN / 2; q++) v[q] = ld_in<COH>(src + q);
+            for (int q = 0; q < NBIN / 2; q++) v[s][q] = ld_in<COH>(src + q);
+        }
+    }
 #pragma unroll
-            for (int q = 0; q < NBIN / 2; q++) { dst[2 * q] = v[q].x; dst[2 * q + 1] = v[q].y; }
-        } else {
+    for (int s = 0; s < 2; s++) {
+        const int k = t + s * NT;
+        if (k >= HY * HX) continue;
+        float *dst = hS + k * CS;
 #pragma unroll
-            for (int b = 0; b < NBIN; b++) dst[b] = 0.0f;
+        for (int q = 0; q < NBIN / 2; q++) {
+            dst[2 * q] = in[s] ? v[s][q].x : 0.0f;
+            dst[2 * q + 1] = in[s] ? v[s][q].y : 0.0f;
         }
     }
     __syncthreads();

@@ -5,9 +5,10 @@
 
 namespace hogk {
 
-__global__ void __launch_bounds__(feat_cfg::NT) feat_kernel(const LevelDesc *__restrict__ descs,
-                                                            const Job *__restrict__ jobs, float eps,
-                                                            float tau) {
+// Five CTAs per SM (48 registers): measured faster than four CTAs at 62
+// registers with the two-cell halo staging.
+__global__ void __launch_bounds__(feat_cfg::NT, 5)
+    feat_kernel(const LevelDesc *__restrict__ descs, const Job *__restrict__ jobs, float eps, float tau) {
     __shared__ __align__(16) unsigned char smem[feat_cfg::SMEM];
     const Job jb = jobs[blockIdx.x];
     feat_tile<false>(descs[jb.desc], jb.tile, eps, tau, smem);
