@@ -825,7 +825,6 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
     const int32_t *__restrict__ nbr = fd.nbr;                        // [slot][npos]
     const int32_t *__restrict__ nbr_t = fd.nbr_t;                    // [npos][slot]
     const int lane = t & 31, wid = t >> 5;
-    int *s_total = sh + NT / 32;
 
     // q ranked above p (smaller key)
     auto above = [&](int q, int p, uint32_t hq, uint32_t hp) -> bool {
@@ -833,8 +832,11 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
         return ld_in<COH>(gkeys + q) < ld_in<COH>(gkeys + p);
     };
     // exclusive prefix sum of one count per thread over the block (thread
-    // order); *s_total = the sum
-    auto block_scan = [&](int mine) -> int {
+    // order); *total = the sum.  One barrier: every warp scans the warp
+    // totals itself.  Two calls must be separated by a barrier (sh is
+    // rewritten).
+    static_assert(NT / 32 <= 32, "warp totals scanned by one warp");
+    auto block_scan = [&](int mine, int *total) -> int {
         int incl = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -843,17 +845,15 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
         }
         if (lane == 31) sh[wid] = incl;
         __syncthreads();
-        if (t == 0) {
-            int run = 0;
-            for (int k = 0; k < NT / 32; k++) {
-                const int x = sh[k];
-                sh[k] = run;
-                run += x;
-            }
-            *s_total = run;
+        const int w = lane < NT / 32 ? sh[lane] : 0;
+        int winc = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, winc, o);
+            if (lane >= o) winc += y;
         }
-        __syncthreads();
-        return sh[wid] + incl - mine;
+        *total = __shfl_sync(0xffffffffu, winc, NT / 32 - 1);
+        return __shfl_sync(0xffffffffu, winc - w, wid) + incl - mine;
     };
     // thread t's share of the positions: [beg, end)
     const int per = (npos + NT - 1) / NT;
@@ -868,8 +868,8 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
     auto build_list = [&]() -> int {
         int mine = 0;
         for (int p = beg; p < end; p++) mine += undecided_at(p);
-        int o = block_scan(mine);
-        const int n = *s_total;
+        int n = 0;
+        int o = block_scan(mine, &n);
         for (int p = beg; p < end; p++)
             if (undecided_at(p)) list[o++] = (idx_t)p;
         __syncthreads();
@@ -988,8 +988,8 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
     // kept positions in position order
     int mine = 0;
     for (int p = beg; p < end; p++) mine += khi[p] == NMS_KEPTKEY;
-    int pos = block_scan(mine);
-    const int total = *s_total;
+    int total = 0;
+    int pos = block_scan(mine, &total);
     for (int p = beg; p < end; p++) {
         if (khi[p] != NMS_KEPTKEY) continue;
         if (pos < fd.out_cap) {
