@@ -315,8 +315,15 @@ int hog_pipeline_run(hog_ctx *ctx, const hog_ert *m, const hog_frame *frames, in
                      float *ear, int32_t *has_face, double *seconds, void *stream);
 
 /* Same result as hog_detect, from frames in HOST memory: the frames are
- * copied to the device inside the call (pinned staging) and processed like
- * hog_detect_batched. */
+ * copied to the device inside the call and processed like
+ * hog_detect_batched.  All frames are checked first (HOG_EINVAL, nothing
+ * copied).  With more frames than max_batch / 2 they move in chunks of up to
+ * max_batch / 2 through two halves of the device staging area on a copy
+ * stream of the context, so the copy of chunk k+1 overlaps the detection of
+ * chunk k.  Frames in page-locked memory are copied directly (dense frames
+ * that follow each other in one copy); others are first copied into pinned
+ * host staging.  The frames must stay valid until the call returns; it
+ * synchronises the stream. */
 int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
                     int32_t det_cap, int32_t *counts, void *stream);
 
