@@ -243,8 +243,9 @@ def _frame_table(frames, on_device):
     array (at least one entry; the caller passes the true count).  ``frames``
     is a list of [h, w] frames or one [n, h, w] array whose frame i starts at
     base + i * stride 0.  on_device: CUDA tensors (torch); else host numpy
-    arrays (a list entry that is not a row-strided uint8 array is copied to
-    one, and the copy is kept alive in the second return value)."""
+    arrays or host torch tensors (a list entry that is not a row-strided
+    uint8 array is copied to one, and the copy is kept alive in the second
+    return value)."""
     if on_device:
         import torch
         if isinstance(frames, torch.Tensor):
@@ -262,6 +263,8 @@ def _frame_table(frames, on_device):
                 raise ValueError("want CUDA uint8 tensors [h, w]")
             rows.append((t.data_ptr(), t.shape[1], t.shape[0], t.stride(0)))
         return np.array(rows or [(0, 0, 0, 0)], FRAME_DTYPE), None
+    if not isinstance(frames, (list, tuple, np.ndarray)) and hasattr(frames, "numpy"):
+        frames = frames.numpy()        # a host torch tensor: a view, pinned memory stays pinned
     if isinstance(frames, np.ndarray) and frames.ndim == 3:
         a = frames
         if a.dtype != np.uint8 or (a.size and (a.strides[2] != 1 or a.strides[1] < a.shape[2]

@@ -148,3 +148,17 @@ def test_frame_table_layout_and_forms(hog):
     assert len(t0) == 1 and int(t0["data"][0]) == 0
     e, _ = hog._frame_table(np.zeros((0, 4, 4), np.uint8), False)
     assert len(e) == 1
+
+
+def test_frame_table_host_torch_tensor(hog):
+    """A host torch tensor [n, h, w] is taken as a view of its memory (no
+    copy), the same descriptors as its numpy view."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    t = torch.arange(3 * 5 * 16, dtype=torch.int64).remainder(256).to(torch.uint8).reshape(3, 5, 16)
+    tab, _ = hog._frame_table(t, False)
+    ref, _ = hog._frame_table(t.numpy(), False)
+    assert tab.tolist() == ref.tolist()
+    assert int(tab["data"][0]) == t.data_ptr()
+    tl, _ = hog._frame_table(list(t), False)   # a list of 2-D tensors
+    assert (tl["w"] == 16).all() and (tl["h"] == 5).all()
