@@ -131,7 +131,7 @@ struct FrameDesc {
     int32_t lev_pos[MAX_LEVELS + 1];
     double lev_rx[MAX_LEVELS], lev_ry[MAX_LEVELS];   // W/Wl, H/Hl (FP64, host-divided)
     const uint64_t *keys;             // [npos]
-    uint32_t *ws;                     // suppression workspace (global mode), 14 B per position
+    uint32_t *ws;                     // suppression workspace (global mode), 9 B per position
     const int32_t *nbr;               // [MAXN][npos] neighbour lists, slot-major
     const int32_t *nbr_t;             // [npos][MAXN] the same lists, position-major
     const uint8_t *nbr_cnt;           // [npos]
