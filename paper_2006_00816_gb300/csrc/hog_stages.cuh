@@ -758,8 +758,9 @@ __device__ __forceinline__ void corr_warp_job(const LevelDesc *__restrict__ desc
 // candidate states of the cluster form's state bytes
 constexpr uint8_t NMS_ALIVE = 1, NMS_KEPT = 2, NMS_DEAD = 0;
 constexpr uint32_t NMS_NOKEY = 0xffffffffu;   // key high word of a non-candidate (or a suppressed one)
-// key high word of a kept candidate: below every real high word, which is at
-// least 0x00800000 (the complemented order of a finite score)
+// key high word of a kept candidate: below every real high word.  A real one
+// is the complemented order of a non-NaN score, in [0x007FFFFF (+inf),
+// 0xFF800000 (-inf)], so neither 0 nor NMS_NOKEY is a key.
 constexpr uint32_t NMS_KEPTKEY = 0u;
 
 struct WinBox {
