@@ -11,9 +11,15 @@ timed region starts.
 Prints ONE JSON line (rank 0).  value = batched frames/s over all ranks;
 "plain" = the per-frame path (one call per frame) with its p50/p99 latency;
 "e2e" = the same batched metric through hog_detect_host from pinned host
-frames (copies inside the timed region); "roofline" = the correlation
-kernel's FP32 FLOP rate from CUDA events on its stream against the FP32
-FMA peak; "cpu_baseline" = the FP64 oracle on a bounded sample on the host.
+frames (copies inside the timed region); "roofline" = the dominant kernel of
+the step (the stage with the most CUDA-event time on the launching stream)
+against its own bound -- the FP32 ALU peak (derived from SM count, lanes and
+clock) for the gradient-histogram kernel, the measured bf16/fp16 tensor peak
+for the tensor-core correlation, the measured copy bandwidth for the
+memory-bound stages; "roofline_corr" = the correlation's figure when it is
+not the dominant one; "roofline_headline" = correlation + feature FLOP/s
+against the FP32 peak; "cpu_baseline" = the FP64 oracle on a bounded sample
+on the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -45,6 +51,18 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # source captured (first 16 hex digits of its SHA-256); None: not captured
 CORR_TC_TRAFFIC_250 = {1: 479.547648e6 + 20.450816e6, 2: None}
 CORR_TC_SOURCE_SHA = "2b41c1116f1dad71"
+# Gradient + histogram work per pyramid pixel: central differences, the
+# magnitude, the orientation test and four bilinear votes, about 60 FLOP
+# (the paper's per-pixel steps counted as FP32 operations)
+HIST_FLOP_PER_PX = 60
+# Normalisation and the 31 features, per cell (energy, 4 block sums and
+# normalisers, 27 x 4 truncated products and their sums)
+FEAT_FLOP_PER_CELL = 300
+# DRAM bytes of hist_kernel per 250-frame 640x480 batch from one ncu capture
+# (--set full) of the source whose SHA-256 starts with HIST_SOURCE_SHA (the
+# stage code lives in hog_stages.cuh); None: not captured
+HIST_TRAFFIC_250 = 249.0e6 + 226.8e6
+HIST_SOURCE_SHA = None
 PAPER_CONTEXT = {"ms_per_frame": 0.333, "frames_per_s": 3003,
                  "hardware": "NVIDIA Titan X (Pascal), 16 frames/launch, incl. transfers"}
 
@@ -326,6 +344,74 @@ def corr_roofline(hog, stats, mode, engine, nfr, steps, peaks):
             "flop_per_launch": flops / batches, "avg_launch_ms": ms / batches,
             "flop_note": "correlation FLOPs only (6,200 per window x filter)",
             "peak_note": "derived FP32 FMA peak (152 SM x 128 lanes x 2 x 2.07 GHz)"}
+
+
+def _src_sha(*names):
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        h.update(open(os.path.join(ROOT, "paper_2006_00816_gb300", "csrc", n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def kernel_roofline(hog, stage, stats, stages, nfr, steps, peaks):
+    """Roofline entry of one stage's kernel (per-stage mode): achieved =
+    algorithmic work per launch / average launch time (CUDA events on the
+    launching stream).  The gradient-histogram kernel is issue-bound ALU
+    work, measured against the derived FP32 peak with its HBM fraction
+    beside it; the memory-bound stages against the measured copy
+    bandwidth."""
+    ms, launches, _ = stats[stage]
+    if launches == 0 or ms <= 0:
+        return None
+    per_launch_ms = ms / launches
+    frames_per_launch = nfr * steps / launches
+    lv = level_cells(hog, W0, H0)
+    px = sum(p for _, _, p in lv)
+    st = stages.get(stage, {})
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if stage == "hist":
+        flop = HIST_FLOP_PER_PX * px * frames_per_launch
+        achieved = flop / (per_launch_ms / 1e3) / 1e12
+        same = HIST_SOURCE_SHA is not None and _src_sha("hog_stages.cuh", "k_hist.cu") == HIST_SOURCE_SHA
+        return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": HIST_TRAFFIC_250 * frames_per_launch / 250 if same else None,
+                "kernel": "hist_kernel (gradients, 18-bin orientation, bilinear cell votes)",
+                "flop_per_launch": flop, "avg_launch_ms": per_launch_ms,
+                "hbm_gbs": st.get("gbs"), "hbm_frac": st.get("hbm_frac"),
+                "flop_note": "%d FLOP per pyramid pixel x %d pixels per 640x480 frame"
+                             % (HIST_FLOP_PER_PX, px),
+                "peak_note": "derived FP32 peak: 152 SM x 128 lanes x 2 FLOP x 2.07 GHz "
+                             "(no FP32 figure in MEASURED_PEAKS.json)",
+                "traffic_note": "ncu dram read+write of a 250-frame launch scaled to this "
+                                "launch (null: the captured source has changed since)"}
+    gbs = st.get("gbs")
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+            "frac": gbs / hbm if gbs else None, "traffic": None,
+            "kernel": stage, "avg_launch_ms": per_launch_ms,
+            "bytes_per_launch": (st.get("algorithmic_bytes_per_frame") or 0) * frames_per_launch,
+            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)"}
+
+
+def headline_roofline(hog, stats, nfr, steps):
+    """The path's arithmetic (correlation 6,200 FLOP per window x filter,
+    gradient-histogram 60 FLOP per pixel, features 300 FLOP per cell) per
+    second of the three stages' CUDA-event time, against the FP32 peak."""
+    lv = level_cells(hog, W0, H0)
+    cells = sum(c for c, _, _ in lv)
+    wins = sum(wn for _, wn, _ in lv)
+    px = sum(p for _, _, p in lv)
+    ms = sum(stats[k][0] for k in ("hist", "feat", "corr") if stats[k][1] > 0)
+    if ms <= 0:
+        return None
+    flop = (CORR_FLOP_PER_UNIT * wins * NF + HIST_FLOP_PER_PX * px + FEAT_FLOP_PER_CELL * cells) * nfr * steps
+    achieved = flop / (ms / 1e3) / 1e12
+    return {"achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "flop_per_frame": flop / (nfr * steps),
+            "stages": "hist + feat + corr CUDA-event time",
+            "peak_note": "derived FP32 peak; the correlation runs on tensor cores, so the "
+                         "fraction can exceed what FP32 lanes alone could reach"}
 
 
 def stage_table(hog, stats, nfr, steps, engine, peaks):
@@ -726,8 +812,17 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    roofline = corr_roofline(hog, stats, mode, engine, nfr, args.steps, peaks)
     stages = stage_table(hog, stats, nfr, args.steps, engine, peaks)
+    roofline_corr = corr_roofline(hog, stats, mode, engine, nfr, args.steps, peaks)
+    headline = None
+    if mode == 0:
+        dominant = max((k for k in ("pyramid", "hist", "feat", "corr", "nms") if stats[k][1] > 0),
+                       key=lambda k: stats[k][0])
+        roofline = roofline_corr if dominant == "corr" else \
+            kernel_roofline(hog, dominant, stats, stages, nfr, args.steps, peaks)
+        headline = headline_roofline(hog, stats, nfr, args.steps)
+    else:
+        dominant, roofline = "fused", roofline_corr
     stage_ms = {k: v[0] / args.steps for k, v in stats.items() if v[1] > 0}
     nchunks = (nfr + args.batch - 1) // args.batch
     gpu_launches = int(sum(v[1] for v in stats.values())) + nchunks * args.steps   # + pack
@@ -837,6 +932,9 @@ def main():
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roofline,
+            "roofline_dominant_stage": dominant,
+            "roofline_corr": roofline_corr,
+            "roofline_headline": headline,
             "hbm": {"algorithmic_gbs": hbm_bytes / (step_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
                     "frac": hbm_bytes / (step_ms / 1e3) / 1e9 / hbm_peak},
             "stage_ms_per_step": stage_ms,

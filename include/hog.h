@@ -55,6 +55,10 @@ extern "C" {
 #define HOG_WIN         10   /* 10x10-cell (80x80-pixel) window               */
 #define HOG_MAX_FILTERS 8    /* filters per context (the paper uses 5)        */
 #define HOG_MAX_LEVELS  32   /* pyramid levels per frame                      */
+/* Largest |weight| the tensor-core correlation engines accept: they store
+ * 64 w in fp16, whose largest finite value is 65504.  Filters with a larger
+ * weight run on the FP32 CUDA-core engine (see hog_set_corr_engine).      */
+#define HOG_TC_MAX_WEIGHT 1023.5f
 
 typedef struct hog_ctx hog_ctx;   /* opaque, owned by the library */
 
@@ -127,12 +131,21 @@ int hog_level_geometry(const hog_params *p, int32_t w, int32_t h, hog_level *lev
 /* Create a context: validates *p, copies n_filters filters from host memory
  * (layout [f][row a][col b][channel c], 10 x 10 x 31 floats each; the five
  * rotation filters of Section 4.1.1) to the device and allocates the device
- * arenas for max_batch frames of max_w x max_h.  *out is NULL on failure. */
+ * arenas for max_batch frames of max_w x max_h.  *out is NULL on failure.
+ * The weights of a trained linear filter may have any scale: every finite
+ * value is accepted (HOG_EINVAL for a NaN or infinite weight).  The context
+ * starts on tensor-core engine 1 when every |w| <= HOG_TC_MAX_WEIGHT, else
+ * on the FP32 CUDA-core engine 0 (hog_get_corr_engine tells which;
+ * hog_last_error gives the reason). */
 int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters,
                hog_ctx **out);
 
 /* Replace the filters (same layout; 1 <= n_filters <= HOG_MAX_FILTERS).
- * Stream-ordered on the legacy default stream; synchronises the device. */
+ * Stream-ordered on the legacy default stream; synchronises the device.
+ * HOG_EINVAL (filters unchanged) for a weight that is not finite.  If a
+ * tensor engine is selected and a new weight exceeds HOG_TC_MAX_WEIGHT, the
+ * context switches to engine 0 and returns HOG_OK, with the reason in
+ * hog_last_error. */
 int hog_set_filters(hog_ctx *ctx, const float *filters_host, int32_t n_filters);
 
 /* Release everything the context owns.  NULL-safe. */
@@ -207,7 +220,8 @@ int hog_set_batched_mode(hog_ctx *ctx, int32_t mode);
  * features and the same correlation kernel follows it, so both batched
  * modes stay bit-identical to hog_detect.  Engines 1 and 2 hold 128 bytes
  * per feature cell per batch slot, engine 2 another 40 F bytes; switching
- * drops cached plans.  HOG_EINVAL for other values. */
+ * drops cached plans.  HOG_EINVAL for other values, and for engines 1 and 2
+ * while a filter weight exceeds HOG_TC_MAX_WEIGHT (their fp16 range). */
 int hog_set_corr_engine(hog_ctx *ctx, int32_t engine);
 int hog_get_corr_engine(const hog_ctx *ctx, int32_t *engine);
 
@@ -239,6 +253,19 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
 
 /* Current tuning: batched mode (0/1) and correlation shape policy (0..3). */
 int hog_get_tuning(const hog_ctx *ctx, int32_t *batched_mode, int32_t *corr_policy);
+
+/* Failure-path control of the bounded device waits of the persistent fused
+ * launch (hog_detect_batched in mode 1; no counterpart in the paper).  A
+ * work item polls the completion counter it depends on at most `polls`
+ * times (0 restores the default, 2^24 polls of about 64 ns each) before the
+ * launch gives up and the call returns HOG_ETIMEOUT with invalid outputs.
+ * withhold = 1 makes the first dependency wait of every plan built from now
+ * on expect one completion more than its producers give, so that wait runs
+ * out after `polls` polls: host-side fault injection for testing the error
+ * path; no GPU fault or hang is involved, and the context stays usable.
+ * withhold = 0 switches it off.  Drops cached plans and graphs.  HOG_EINVAL
+ * for polls < 0 or withhold not 0 or 1. */
+int hog_debug_waits(hog_ctx *ctx, int64_t polls, int32_t withhold);
 
 /* Region of interest of one frame (Section 6.6, future work: near the
  * previous frame's face, scan only some scales and locations).  Window (u, v)
@@ -338,10 +365,13 @@ int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog
  * fixed fields are still checked; direct_first must be 0: this entry point
  * computes the plain 5/6 pyramid).  frame (device) must be at most 640 x 480,
  * else HOG_EINVAL with a message in err.  feat_out (device), levels (host)
- * and the capacities behave as in hog_features.  err (host, may be NULL)
- * receives a message on failure.  All calls on a device share the array:
- * calls whose GPU work overlaps race.  The first call on each device looks up
- * the array's address; make it before any stream capture. */
+ * and the capacities behave as in hog_features; frame and feat_out must be
+ * memory of the current device, where the work runs.  err (host, may be
+ * NULL) receives a message on failure.  All calls on a device share the
+ * array: calls whose GPU work overlaps race.  The first call on each device
+ * looks up the array's address; make it before any stream capture.  The
+ * address is kept for the process, so a cudaDeviceReset of that device is
+ * not supported afterwards. */
 int hog_features_static(const hog_params *p, const hog_frame *frame, float *feat_out,
                         size_t cap_floats, hog_level *levels, int32_t cap_levels,
                         int32_t *n_levels, char *err, size_t err_cap, void *stream);
@@ -365,6 +395,33 @@ int hog_features_static(const hog_params *p, const hog_frame *frame, float *feat
 int hog_backward(hog_ctx *ctx, const float *images, int32_t n, int32_t w, int32_t h,
                  const float *labels, const float *weights, float *dW, float *dI, float *loss,
                  int32_t recompute, void *stream);
+
+/* hog_backward plus the discrete forward state its adjoint holds fixed, for
+ * checking the adjoint element by element against an independent
+ * implementation: where a reference computed in another precision takes
+ * one of these decisions the other way, the two gradients differ by design,
+ * and the state says where.  Arguments and results as hog_backward; each
+ * state output may be NULL:
+ *   best_out  (host int32 [n][4]): per crop the best window's level, u, v
+ *             and 1 if its hinge term is active (1 - y s > 0), else 0;
+ *   bins_out  (device uint8 [n][104][104]): for active crops, the
+ *             orientation bin (0..17) of every pixel of the region the
+ *             window's gradient reaches at its level -- 12 x 12 cells
+ *             starting at cell (u - 1, v - 1), i.e. pixels from
+ *             (8 (v - 1) - 4, 8 (u - 1) - 4) -- 255 where the pixel casts
+ *             no vote (zero gradient, outside the level or the voting
+ *             range); inactive crops are not written;
+ *   trunc_out (device uint8 [n][100][4][27]): for active crops, per window
+ *             cell (a, b) and block k, 1 where the truncation test
+ *             x N_k < tau holds (the gradient passes) for x = h_o
+ *             (o < 18) and x = h_o + h_{o+9} (o < 9); inactive crops are
+ *             not written.
+ * With bins_out or trunc_out the window adjoint runs even when dI is NULL.
+ * Synchronises the stream when best_out or loss is not NULL. */
+int hog_backward_state(hog_ctx *ctx, const float *images, int32_t n, int32_t w, int32_t h,
+                       const float *labels, const float *weights, float *dW, float *dI, float *loss,
+                       int32_t recompute, int32_t *best_out, uint8_t *bins_out, uint8_t *trunc_out,
+                       void *stream);
 
 /* ---- stage timing (tracing; no counterpart in the paper, which reads its
  * kernel times from a profiler, Section 5.1) ------------------------------ */

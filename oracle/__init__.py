@@ -93,6 +93,8 @@ def lib():
             "hgo_hinge_loss": (d, [dp, i, i, i, dp, i, d, d, dp, dp, i32p]),
             "hgo_hinge_backward": (d, [dp, i, i, i, dp, i, d, d, dp, dp, dp]),
             "hgo_forward_signature": (C.c_uint64, [dp, i, i, i, d, d, dp]),
+            "hgo_forward_state": (None, [dp, i, i, i, d, d, dp, i32p, i32p, i32p,
+                                         P(C.c_int8), u8p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -385,3 +387,21 @@ def forward_signature(img, filt, min_size=80, eps=EPS, tau=TAU):
     h, w = img.shape
     return lib().hgo_forward_signature(_p(img, C.c_double), w, h, min_size, eps, tau,
                                        _p(filt, C.c_double))
+
+
+def forward_state(img, filt, min_size=80, eps=EPS, tau=TAU):
+    """Discrete state of the float-mode forward of one crop that the adjoint
+    holds fixed: ((level, u, v) of the best window, bins [lh, lw] int8 of
+    that level (-1: no vote), trunc [100, 4, 27] uint8 (1: x N_k < tau))."""
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    filt = np.ascontiguousarray(filt, dtype=np.float64).reshape(10, 10, 31)
+    h, w = img.shape
+    best = np.zeros(3, np.int32)
+    lw, lh = C.c_int32(0), C.c_int32(0)
+    bins = np.full(w * h, -1, np.int8)
+    trunc = np.zeros((WIN * WIN, 4, NBIN + 9), np.uint8)
+    lib().hgo_forward_state(_p(img, C.c_double), w, h, min_size, eps, tau, _p(filt, C.c_double),
+                            _p(best, C.c_int32), C.byref(lw), C.byref(lh),
+                            bins.ctypes.data_as(C.POINTER(C.c_int8)), _p(trunc, C.c_uint8))
+    return (tuple(int(x) for x in best), bins[:lw.value * lh.value].reshape(lh.value, lw.value),
+            trunc)

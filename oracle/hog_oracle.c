@@ -970,3 +970,63 @@ uint64_t hgo_forward_signature(const double *img, int w, int h, int min_size, do
     free(P.pyr);
     return hsh;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The discrete state of the float-mode forward of one crop that the adjoint
+ * holds fixed -- the quantities hgo_forward_signature hashes, as arrays, so
+ * that a test can find where an adjoint computed in another precision took
+ * a decision the other way: best window (level, u, v) of the filter (-1 if
+ * none); the orientation bin of every pixel of that level (bins [lh][lw],
+ * -1 for a zero gradient and on the one-pixel border; room for w*h
+ * entries); and, per window cell (a, b) and block k, the 27 truncation
+ * tests x N_k < tau for x = h_o (o < 18) and h_o + h_{o+9} (o < 9) (trunc
+ * [100][4][27]).  *lw, *lh receive the level's size (0 without a window).  */
+
+void hgo_forward_state(const double *img, int w, int h, int min_size, double eps, double tau,
+                       const double *filt, int32_t *best3, int32_t *lw_out, int32_t *lh_out,
+                       int8_t *bins, uint8_t *trunc)
+{
+    hgo_fpyr P;
+    fpyr_build(img, w, h, min_size, &P);
+    int l, u0, v0;
+    best_window(&P, eps, tau, filt, &l, &u0, &v0);
+    best3[0] = l; best3[1] = u0; best3[2] = v0;
+    *lw_out = *lh_out = 0;
+    if (l >= 0) {
+        int lw = P.ws[l], lh = P.hs[l], cx = lw / CELL, cy = lh / CELL;
+        *lw_out = lw; *lh_out = lh;
+        const double *img2 = P.pyr + P.off[l];
+        for (int y = 0; y < lh; y++)
+            for (int x = 0; x < lw; x++) {
+                int b = -1;
+                if (y >= 1 && y < lh - 1 && x >= 1 && x < lw - 1)
+                    b = hgo_orientation_bin(img2[y * lw + x + 1] - img2[y * lw + x - 1],
+                                            img2[(y + 1) * lw + x] - img2[(y - 1) * lw + x]);
+                bins[(size_t)y * lw + x] = (int8_t)b;
+            }
+        double *hist = (double *)malloc(sizeof(double) * ((size_t)cx * cy * NBIN + 1));
+        hgo_cell_hist(img2, lw, lh, hist);
+        double *E = (double *)calloc((size_t)cx * cy + 1, sizeof(double));
+        for (int c = 0; c < cx * cy; c++)
+            for (int o = 0; o < 9; o++) E[c] += (hist[c * NBIN + o] + hist[c * NBIN + o + 9]) *
+                                                (hist[c * NBIN + o] + hist[c * NBIN + o + 9]);
+        static const int bdx[4] = {-1, +1, -1, +1};
+        static const int bdy[4] = {-1, -1, +1, +1};
+        for (int a = 0; a < WIN; a++)
+            for (int b = 0; b < WIN; b++) {
+                int ci = u0 + a, cj = v0 + b;
+                const double *hc = hist + ((size_t)ci * cx + cj) * NBIN;
+                for (int k = 0; k < 4; k++) {
+                    double S = energy_at(E, cx, cy, ci, cj) + energy_at(E, cx, cy, ci, cj + bdx[k])
+                             + energy_at(E, cx, cy, ci + bdy[k], cj)
+                             + energy_at(E, cx, cy, ci + bdy[k], cj + bdx[k]);
+                    double N = 1.0 / sqrt(S + eps);
+                    uint8_t *t = trunc + ((size_t)(a * WIN + b) * 4 + k) * (NBIN + 9);
+                    for (int o = 0; o < NBIN; o++) t[o] = hc[o] * N < tau;
+                    for (int o = 0; o < 9; o++) t[NBIN + o] = (hc[o] + hc[o + 9]) * N < tau;
+                }
+            }
+        free(hist); free(E);
+    }
+    free(P.pyr);
+}

@@ -165,10 +165,13 @@ struct hog_ctx {
     int batched_mode = MODE_FUSED;  // chosen by the autotuner
     int corr_policy = 0;            // 0: least padding; 1 + s: prefer warp-tile shape s
     int nms_cluster = 0;            // 0: automatic; 1: one CTA per frame; 2..16: cluster size
+    long long wait_polls = FUSED_DEFAULT_POLLS;   // fused launch: polls before a wait gives up
+    int wait_withhold = 0;          // 1: each new fused plan withholds one completion (tests)
     // correlation engine: 0 FP32 CUDA cores (k_corr.cu); tensor cores
     // (k_corr_tc.cu): 1 GEMM and reduction fused, 2 two passes through G
     int corr_engine = 0;
     std::vector<float> w_host;      // the filters as given, [F][10][10][31]
+    float w_absmax = 0.0f;          // largest |w| of the filters
     float *d_wuser = nullptr;       // device copy of w_host
     uint16_t *d_wtc = nullptr;      // tensor-core B planes (hi, lo)
     uint16_t *d_fh = nullptr;       // per slot: fp16 feature planes hi, lo [cells][32]
@@ -230,6 +233,15 @@ int check_params(const hog_params *p, std::string &why) {
 int upload_filters(hog_ctx *ctx, const float *filters, int n) {
     if (!filters || n < 1 || n > HOG_MAX_FILTERS)
         return fail(ctx, HOG_EINVAL, "need 1..%d filters", HOG_MAX_FILTERS);
+    // the weights of a linear filter may have any finite scale; the tensor
+    // engines store 64 w as fp16, finite only while |w| <= HOG_TC_MAX_WEIGHT
+    float amax = 0.0f;
+    for (size_t k = 0; k < (size_t)n * WIN * WIN * NFEAT; k++) {
+        if (!std::isfinite(filters[k]))
+            return fail(ctx, HOG_EINVAL, "filter %d weight %zu is not finite", (int)(k / (WIN * WIN * NFEAT)),
+                        k % (WIN * WIN * NFEAT));
+        amax = std::max(amax, std::fabs(filters[k]));
+    }
     const int nfk = n == 1 ? 1 : (n <= 5 ? 5 : 8);
     if (ctx->d_w && nfk != ctx->nfk) {
         cudaFree(ctx->d_w);
@@ -249,12 +261,20 @@ int upload_filters(hog_ctx *ctx, const float *filters, int n) {
     ctx->nf = n;
     ctx->nfk = nfk;
     ctx->w_host.assign(filters, filters + (size_t)n * WIN * WIN * NFEAT);
+    ctx->w_absmax = amax;
     return HOG_OK;
 }
+
+// Whether the tensor engines can represent the current filters.
+bool tc_range_ok(const hog_ctx *ctx) { return ctx->w_absmax <= HOG_TC_MAX_WEIGHT; }
 
 // Arenas and B planes of the tensor-core correlation (allocated when the
 // engine is first selected; rebuilt after a filter change).
 int prepare_tc(hog_ctx *ctx, bool need_g) {
+    if (!tc_range_ok(ctx))
+        return fail(ctx, HOG_EINVAL,
+                    "filter weight |w| = %g exceeds %g, the tensor engines' fp16 range (64 |w| <= 65504); "
+                    "use the CUDA-core engine 0", (double)ctx->w_absmax, (double)HOG_TC_MAX_WEIGHT);
     auto F = [](void *p) { if (p) cudaFree(p); };
     F(ctx->d_wuser); F(ctx->d_wtc); F(ctx->d_gm);
     ctx->d_wuser = nullptr; ctx->d_wtc = nullptr; ctx->d_gm = nullptr;
@@ -972,6 +992,9 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
         add_frame(ctx, pb, *g, f, i, frame_base + i, o);
     }
     build_fused_items(pb);
+    if (ctx->wait_withhold)   // failure-path test: one wait expects a completion nothing gives
+        for (FusedItem &it : pb.items)
+            if (it.wait >= 0) { it.target += 1; break; }
     build_tc_bands(pb, ctx->num_sms);
     PlanInfo info;
     layout_plan(pb, ctx->nf, info);
@@ -1027,6 +1050,7 @@ int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStr
     a.head = head;
     a.abort = abort_flag;
     a.flags = ctx->d_flags;
+    a.spin_limit = ctx->wait_polls;
     int rc = collect_profile(ctx);
     if (rc) return rc;
     auto mark = [&](int i) -> cudaError_t {
@@ -1319,12 +1343,13 @@ int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters
         }
     }
     // tensor-core correlation by default; the CUDA-core engine if its
-    // buffers cannot be had
+    // buffers cannot be had or the filters exceed its fp16 range (the
+    // message stays in hog_last_error)
     if (prepare_tc(ctx, false) == HOG_OK) {
         ctx->corr_engine = 1;
     } else {
         cudaGetLastError();
-        ctx->err.clear();
+        if (tc_range_ok(ctx)) ctx->err.clear();
     }
     *out = ctx;
     return HOG_OK;
@@ -1336,6 +1361,14 @@ int hog_set_filters(hog_ctx *ctx, const float *filters_host, int32_t n_filters) 
     const int nfk0 = ctx->nfk;
     int rc = upload_filters(ctx, filters_host, n_filters);
     if (rc == HOG_OK && ctx->corr_engine >= 1) {
+        if (!tc_range_ok(ctx)) {
+            // outside the tensor engines' fp16 range: the CUDA-core engine
+            // takes over (hog_get_corr_engine reports 0, hog_last_error why)
+            clear_plans(ctx);
+            ctx->corr_engine = 0;
+            prepare_tc(ctx, false);   // records the reason, allocates nothing
+            return HOG_OK;
+        }
         if (ctx->nfk != nfk0) clear_plans(ctx);   // row-shift matrices change size
         rc = prepare_tc(ctx, ctx->corr_engine == 2);
     }
@@ -1719,7 +1752,7 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
                 if (b != std::string::npos) pol = std::atoi(txt.c_str() + b + 15);
                 if (c != std::string::npos) eng = std::atoi(txt.c_str() + c + 15);
                 if ((mode == MODE_STAGED || mode == MODE_FUSED) && pol >= 0 && pol <= CORR_NSHAPE &&
-                    eng >= 0 && eng <= 2) {
+                    eng >= 0 && eng <= 2 && (eng == 0 || tc_range_ok(ctx))) {
                     if (pol != ctx->corr_policy) { ctx->corr_policy = pol; clear_plans(ctx); }
                     const int rc = hog_set_corr_engine(ctx, eng);
                     if (rc) return rc;
@@ -1827,6 +1860,16 @@ int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const 
     return HOG_OK;
 }
 
+int hog_debug_waits(hog_ctx *ctx, int64_t polls, int32_t withhold) {
+    if (!ctx) return HOG_EINVAL;
+    if (polls < 0 || (withhold != 0 && withhold != 1))
+        return fail(ctx, HOG_EINVAL, "polls must be >= 0 and withhold 0 or 1");
+    clear_plans(ctx);   // plans carry the wait targets; graphs carry the budget
+    ctx->wait_polls = polls == 0 ? FUSED_DEFAULT_POLLS : (long long)polls;
+    ctx->wait_withhold = withhold;
+    return HOG_OK;
+}
+
 int hog_get_tuning(const hog_ctx *ctx, int32_t *batched_mode, int32_t *corr_policy) {
     if (!ctx) return HOG_EINVAL;
     if (batched_mode) *batched_mode = ctx->batched_mode;
@@ -1837,6 +1880,14 @@ int hog_get_tuning(const hog_ctx *ctx, int32_t *batched_mode, int32_t *corr_poli
 int hog_backward(hog_ctx *ctx, const float *images, int32_t n, int32_t w, int32_t h,
                  const float *labels, const float *weights, float *dW, float *dI, float *loss,
                  int32_t recompute, void *stream_) {
+    return hog_backward_state(ctx, images, n, w, h, labels, weights, dW, dI, loss, recompute,
+                              nullptr, nullptr, nullptr, stream_);
+}
+
+int hog_backward_state(hog_ctx *ctx, const float *images, int32_t n, int32_t w, int32_t h,
+                       const float *labels, const float *weights, float *dW, float *dI, float *loss,
+                       int32_t recompute, int32_t *best_out, uint8_t *bins_out, uint8_t *trunc_out,
+                       void *stream_) {
     if (!ctx) return HOG_EINVAL;
     if (n < 1 || !images || !labels || !weights || !dW)
         return fail(ctx, HOG_EINVAL, "hog_backward: NULL argument or n < 1");
@@ -1942,15 +1993,30 @@ int hog_backward(hog_ctx *ctx, const float *images, int32_t n, int32_t w, int32_
     CUDA_TRY(ctx, launch_argmax(d_sc, s_sc, lv, labels, d_best, d_marg, n, stream));
     // adjoint
     CUDA_TRY(ctx, launch_dw(d_fu, s_featu, lv, d_best, d_marg, labels, n, dW, stream));
-    if (dI) {
+    if (dI || bins_out || trunc_out) {
         CUDA_TRY(ctx, cudaMemsetAsync(d_dp, 0, sizeof(float) * N * s_pyr, stream));
         CUDA_TRY(ctx, launch_window_adjoint(d_pyr, s_pyr, d_hist, s_hist, lv, d_best, d_marg, labels, n,
                                             weights, ctx->p.eps, ctx->p.trunc, recompute ? 1 : 0,
-                                            d_dp, stream));
+                                            d_dp, bins_out, trunc_out, stream));
+    }
+    if (dI) {
         for (int q = g.nlev - 2; q >= 0; q--)
             CUDA_TRY(ctx, launch_fpyr_adjoint(d_dp, s_pyr, lv, q, d_best, d_marg, n, stream));
         CUDA_TRY(ctx, cudaMemcpy2DAsync(dI, (size_t)w * h * 4, d_dp, s_pyr * 4, (size_t)w * h * 4, N,
                                         cudaMemcpyDeviceToDevice, stream));
+    }
+    if (best_out) {
+        std::vector<int4> b(n);
+        std::vector<float> m(n);
+        CUDA_TRY(ctx, cudaMemcpyAsync(b.data(), d_best, sizeof(int4) * n, cudaMemcpyDeviceToHost, stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(m.data(), d_marg, sizeof(float) * n, cudaMemcpyDeviceToHost, stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        for (int i = 0; i < n; i++) {
+            best_out[4 * i] = b[i].x;
+            best_out[4 * i + 1] = b[i].y;
+            best_out[4 * i + 2] = b[i].z;
+            best_out[4 * i + 3] = m[i] > 0.0f;
+        }
     }
     if (loss) {
         std::vector<float> m(n);

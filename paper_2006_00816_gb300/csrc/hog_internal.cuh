@@ -2,13 +2,44 @@
 // translation units of libhog.  Not part of the public ABI.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "hog.h"
 
 namespace hogk {
+
+// One-time set-up per device.  A kernel's attributes (the opt-in dynamic
+// shared-memory limit) belong to the function on each device, so a process
+// that launches on a second GPU must set them there too.  once(f) runs f()
+// the first time it is called with a given device current, and again after
+// a failure; callers on several host threads (a server's worker and its
+// callers) are serialised by the lock, and a finished device costs one
+// atomic load.
+class PerDevice {
+  public:
+    template <class F>
+    cudaError_t once(F &&f) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= kMaxDevices) return f();   // untracked: every call
+        if (done_[dev].load(std::memory_order_acquire)) return cudaSuccess;
+        std::lock_guard<std::mutex> lock(mu_);
+        if (done_[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+        e = f();
+        if (e == cudaSuccess) done_[dev].store(1, std::memory_order_release);
+        return e;
+    }
+
+  private:
+    static constexpr int kMaxDevices = 64;
+    std::atomic<unsigned char> done_[kMaxDevices] = {};
+    std::mutex mu_;
+};
 
 constexpr int CELL = 8;
 constexpr int NBIN = 18;
@@ -180,7 +211,9 @@ struct FusedArgs {
     int *head;                     // ticket counter (zeroed before the launch)
     int *abort;                    // set when a bounded wait gave up (zeroed before)
     int *flags;                    // flags[2] |= 1 on a timeout
+    long long spin_limit;          // polls of one dependency wait before it gives up
 };
+constexpr long long FUSED_DEFAULT_POLLS = 1ll << 24;
 
 cudaError_t launch_fused(const FusedArgs &a, int nf_kernel, int grid, cudaStream_t stream);
 int fused_max_ctas_per_sm(int nf_kernel);
@@ -207,7 +240,10 @@ cudaError_t launch_window_adjoint(const float *pyr, size_t pyr_stride, const flo
                                   size_t hist_stride, const TrainLevels &lv, const int4 *best,
                                   const float *margin, const float *labels, int n,
                                   const float *wuser, float eps, float tau, int recompute,
-                                  float *dP, cudaStream_t s);
+                                  float *dP, uint8_t *st_bins, uint8_t *st_trunc, cudaStream_t s);
+// region of the window adjoint: pixels per side of the best window's
+// region (12 x 12 cells), whose bins hog_backward_state reports
+constexpr int TRAIN_RP = (WIN + 2) * CELL + CELL;
 cudaError_t launch_fpyr_adjoint(float *dP, size_t pyr_stride, const TrainLevels &lv, int q,
                                 const int4 *best, const float *margin, int n, cudaStream_t s);
 cudaError_t launch_filter_chunks(const float *wuser, float *wch, cudaStream_t s);

@@ -19,7 +19,12 @@
 // whose work overlaps on the GPU (on different streams, or from different
 // threads) race on the array.  The first call on each device resolves the
 // array's device address (cudaGetSymbolAddress); make that first call before
-// any stream capture.
+// any stream capture.  The address is kept for the life of the process, so
+// a cudaDeviceReset of that device is not supported afterwards.
+//
+// The launch tables (level descriptors and job lists) are written into the
+// array by a small kernel that receives them by value as its parameter, so
+// no host memory is read after the call returns.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -37,6 +42,32 @@ constexpr int STATIC_MAX_JOBS = 2048;
 constexpr int STATIC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+// Levels of a frame of at most 640 x 480 with min_size >= 80: 480 (5/6)^9 <
+// 80, so at most 10; the table holds a few more.
+constexpr int STATIC_MAX_LEVELS = 12;
+constexpr int STATIC_MAX_SEGS = 3 * STATIC_MAX_LEVELS;
+
+// Everything the launch tables hold, passed by value: the level descriptors
+// and the job list as segments of consecutive tiles of one level.
+struct StaticTables {
+    LevelDesc descs[STATIC_MAX_LEVELS];
+    int32_t nlev, nseg, njobs;
+    int32_t seg_first[STATIC_MAX_SEGS];   // first job of the segment
+    int32_t seg_level[STATIC_MAX_SEGS];   // its level (descriptor index)
+    LevelDesc *d_descs;
+    Job *d_jobs;
+};
+static_assert(sizeof(StaticTables) <= 4096, "kernel parameter block");
+
+__global__ void static_tables_kernel(const StaticTables t) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < t.nlev) t.d_descs[k] = t.descs[k];
+    if (k >= t.njobs) return;
+    int s = 0;
+    while (s + 1 < t.nseg && t.seg_first[s + 1] <= k) s++;
+    t.d_jobs[k] = Job{t.seg_level[s], k - t.seg_first[s]};
+}
 
 std::mutex g_static_mu;
 unsigned char *g_static_addr[STATIC_MAX_DEVICES];
@@ -92,10 +123,10 @@ extern "C" int hog_features_static(const hog_params *p, const hog_frame *frame, 
         return put_error(err, err_cap, HOG_EINVAL, "hog_features_static: bad frame data or pitch");
 
     // level geometry: w' = floor(5w/6), h' = floor(5h/6), while min(w, h) >= min_size
-    int lw[MAX_LEVELS], lh[MAX_LEVELS], L = 0;
+    int lw[STATIC_MAX_LEVELS], lh[STATIC_MAX_LEVELS], L = 0;
     for (int w = frame->w, h = frame->h; w >= p->min_size && h >= p->min_size;
          w = 5 * w / 6, h = 5 * h / 6) {
-        if (L >= MAX_LEVELS) return put_error(err, err_cap, HOG_EINVAL, "too many levels");
+        if (L >= STATIC_MAX_LEVELS) return put_error(err, err_cap, HOG_EINVAL, "too many levels");
         lw[L] = w;
         lh[L] = h;
         L++;
@@ -112,15 +143,11 @@ extern "C" int hog_features_static(const hog_params *p, const hog_frame *frame, 
     if (!feat_out || uoff > cap_floats)
         return put_error(err, err_cap, HOG_EINVAL, "hog_features_static: output capacity too small");
 
-    unsigned char *base = nullptr;
-    int rc = scratch_address(&base, err, err_cap);
-    if (rc) return rc;
-
     // scratch layout: [descs][jobs][pyramid][hist][feat]
     const size_t off_desc = 0;
-    const size_t off_jobs = up(sizeof(LevelDesc) * MAX_LEVELS, 256);
+    const size_t off_jobs = up(sizeof(LevelDesc) * STATIC_MAX_LEVELS, 256);
     size_t off = up(off_jobs + sizeof(Job) * STATIC_MAX_JOBS, 256);
-    size_t pyr_off[MAX_LEVELS], hist_off[MAX_LEVELS], feat_off[MAX_LEVELS];
+    size_t pyr_off[STATIC_MAX_LEVELS], hist_off[STATIC_MAX_LEVELS], feat_off[STATIC_MAX_LEVELS];
     for (int l = 1; l < L; l++) {
         pyr_off[l] = off;
         off = up(off + up((size_t)lw[l], 16) * lh[l], 256);
@@ -136,12 +163,36 @@ extern "C" int hog_features_static(const hog_params *p, const hog_frame *frame, 
     if (off > STATIC_SCRATCH_BYTES)
         return put_error(err, err_cap, HOG_EINVAL, "hog_features_static: scratch too small");
 
-    LevelDesc descs[MAX_LEVELS];
-    Job jobs[STATIC_MAX_JOBS];
-    int nj = 0, pyr_beg[MAX_LEVELS], pyr_n[MAX_LEVELS];
-    std::memset(descs, 0, sizeof descs);
+    // job segments: pyramid levels 1..L-1, then histogram and feature tiles of every level
+    StaticTables t;
+    std::memset(&t, 0, sizeof t);
+    int nj = 0, pyr_beg[STATIC_MAX_LEVELS], pyr_n[STATIC_MAX_LEVELS];
+    auto segment = [&](int l, int ntiles) {
+        t.seg_first[t.nseg] = nj;
+        t.seg_level[t.nseg] = l;
+        t.nseg++;
+        nj += ntiles;
+    };
+    for (int l = 1; l < L; l++) {
+        pyr_beg[l] = nj;
+        pyr_n[l] = ((lw[l] + PYR_TX - 1) / PYR_TX) * ((lh[l] + PYR_TY - 1) / PYR_TY);
+        segment(l, pyr_n[l]);
+    }
+    const int hist_beg = nj;
+    for (int l = 0; l < L; l++)
+        segment(l, hist_ntiles(lw[l] / CELL, lh[l] / CELL, hist_tile_bw(lw[l] / CELL, lh[l] / CELL, lh[l])));
+    const int feat_beg = nj;
+    for (int l = 0; l < L; l++)
+        segment(l, ((lw[l] / CELL + FEAT_TX - 1) / FEAT_TX) * ((lh[l] / CELL + FEAT_TY - 1) / FEAT_TY));
+    if (nj > STATIC_MAX_JOBS)
+        return put_error(err, err_cap, HOG_EINVAL, "hog_features_static: job table too small");
+
+    unsigned char *base = nullptr;
+    int rc = scratch_address(&base, err, err_cap);
+    if (rc) return rc;
+
     for (int l = 0; l < L; l++) {
-        LevelDesc &d = descs[l];
+        LevelDesc &d = t.descs[l];
         d.w = lw[l];
         d.h = lh[l];
         d.cx = lw[l] / CELL;
@@ -155,43 +206,24 @@ extern "C" int hog_features_static(const hog_params *p, const hog_frame *frame, 
             d.dst = base + pyr_off[l];
             d.img = d.dst;
             d.pitch = (int)up((size_t)lw[l], 16);
-            d.src = descs[l - 1].img;
-            d.sw = descs[l - 1].w;
-            d.sh = descs[l - 1].h;
-            d.spitch = descs[l - 1].pitch;
+            d.src = t.descs[l - 1].img;
+            d.sw = t.descs[l - 1].w;
+            d.sh = t.descs[l - 1].h;
+            d.spitch = t.descs[l - 1].pitch;
         }
         d.hist = reinterpret_cast<float *>(base + hist_off[l]);
         d.feat = reinterpret_cast<float *>(base + feat_off[l]);
         d.feat_user = feat_out + levels[l].offset;
     }
-    for (int l = 1; l < L; l++) {
-        pyr_beg[l] = nj;
-        const int nt = ((lw[l] + PYR_TX - 1) / PYR_TX) * ((lh[l] + PYR_TY - 1) / PYR_TY);
-        for (int k = 0; k < nt && nj < STATIC_MAX_JOBS; k++) jobs[nj++] = Job{l, k};
-        pyr_n[l] = nj - pyr_beg[l];
-    }
-    const int hist_beg = nj;
-    for (int l = 0; l < L; l++) {
-        const int nt = hist_ntiles(descs[l].cx, descs[l].cy, descs[l].hist_bw);
-        for (int k = 0; k < nt && nj < STATIC_MAX_JOBS; k++) jobs[nj++] = Job{l, k};
-    }
-    const int feat_beg = nj;
-    for (int l = 0; l < L; l++) {
-        const int nt = ((descs[l].cx + FEAT_TX - 1) / FEAT_TX) * ((descs[l].cy + FEAT_TY - 1) / FEAT_TY);
-        for (int k = 0; k < nt && nj < STATIC_MAX_JOBS; k++) jobs[nj++] = Job{l, k};
-    }
-    if (nj >= STATIC_MAX_JOBS)
-        return put_error(err, err_cap, HOG_EINVAL, "hog_features_static: job table too small");
-
-    // The tables live in the scratch array; the source buffers are on the
-    // host stack (pageable), so these copies finish reading them before
-    // returning.
     LevelDesc *d_descs = reinterpret_cast<LevelDesc *>(base + off_desc);
     Job *d_jobs = reinterpret_cast<Job *>(base + off_jobs);
-    cudaError_t e = cudaMemcpyAsync(d_descs, descs, sizeof(LevelDesc) * L, cudaMemcpyHostToDevice,
-                                    stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_jobs, jobs, sizeof(Job) * nj, cudaMemcpyHostToDevice, stream);
+    t.nlev = L;
+    t.njobs = nj;
+    t.d_descs = d_descs;
+    t.d_jobs = d_jobs;
+
+    static_tables_kernel<<<(nj + 255) / 256, 256, 0, stream>>>(t);
+    cudaError_t e = cudaGetLastError();
     for (int l = 1; l < L && e == cudaSuccess; l++)
         e = launch_pyramid(d_descs, d_jobs + pyr_beg[l], pyr_n[l], stream);
     if (e == cudaSuccess) e = launch_hist(d_descs, d_jobs + hist_beg, feat_beg - hist_beg, stream);

@@ -31,14 +31,14 @@ template <int NF>
 static cudaError_t launch_corr_t(const LevelDesc *descs, const Job *jobs, int njobs,
                                  const float *wchunks, int nf_real, float threshold,
                                  cudaStream_t stream) {
-    static bool configured = false;
-    if (!configured) {
+    static PerDevice attr;
+    cudaError_t e_attr = attr.once([&]() {
         cudaError_t e = cudaFuncSetAttribute(corr_kernel<NF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)SMEM);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+        return e;
+    });
+    if (e_attr != cudaSuccess) return e_attr;
     if (njobs <= 0) return cudaSuccess;
     const int grid = (njobs + CORR_WARPS - 1) / CORR_WARPS;
     corr_kernel<NF><<<grid, NT, SMEM, stream>>>(descs, jobs, njobs, wchunks, nf_real, threshold);

@@ -657,13 +657,13 @@ template <int NF>
 cudaError_t launch_tcf_t(const LevelDesc *descs, const TcBand *bands, const int32_t *cta_first, int grid,
                          const uint16_t *wb, int nf_real, float threshold, int *flags,
                          cudaStream_t stream) {
-    static bool configured = false;
-    if (!configured) {
+    static PerDevice attr;
+    cudaError_t e_attr = attr.once([&]() {
         cudaError_t e = cudaFuncSetAttribute(corr_tcf_kernel<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)tf_smem(NF));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+        return e;
+    });
+    if (e_attr != cudaSuccess) return e_attr;
     if (grid > 0)
         corr_tcf_kernel<NF><<<grid, TF_NT, tf_smem(NF), stream>>>(descs, bands, cta_first, wb, nf_real,
                                                                   threshold, flags);
@@ -687,14 +687,14 @@ template <int NF>
 cudaError_t launch_tc_t(const LevelDesc *descs, const Job *jobs, int njobs, const Job *rjobs,
                         int nrjobs, const uint16_t *wb, int nf_real, float threshold, int *flags,
                         int grid, cudaStream_t stream) {
-    static bool configured = false;
-    if (!configured) {
+    static PerDevice attr;
+    cudaError_t e_attr = attr.once([&]() {
         cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel<NF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)tc_smem(NF));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+        return e;
+    });
+    if (e_attr != cudaSuccess) return e_attr;
     if (njobs > 0) {
         corr_tc_kernel<NF><<<grid < njobs ? grid : njobs, TC_NT, tc_smem(NF), stream>>>(
             descs, jobs, njobs, wb, flags);

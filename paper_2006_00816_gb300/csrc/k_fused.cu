@@ -15,10 +15,12 @@
 // running CTA, which never waits on anything later: the schedule cannot
 // deadlock, even when not every CTA is resident.
 //
-// Waits are bounded: after FUSED_SPIN_LIMIT polls the kernel raises a
-// global abort flag and every CTA stops taking items, so a fault in the
-// schedule ends the launch with an error status (read by the host as
-// HOG_ETIMEOUT) instead of a hang.
+// Waits are bounded: after spin_limit polls (2^24 by default, set by
+// hog_debug_waits) the kernel raises a global abort flag and every CTA stops
+// taking items, so a fault in the schedule ends the launch with an error
+// status (read by the host as HOG_ETIMEOUT) instead of a hang.  A wait is
+// taken before the item's work starts, so a CTA that stops has no copy in
+// flight.
 //
 // Completion uses release/acquire at GPU scope (__threadfence then
 // atomicAdd; ld.acquire.gpu polls), and every stage reads data produced in
@@ -37,7 +39,6 @@ static_assert((8 + WIN - 1) * (16 + WIN - 1) <= FUSED_BUF4, "fused staging holds
 constexpr size_t FUSED_SMEM_CORR = sizeof(float4) * FUSED_BUF4 * 2 * FUSED_CORR_WARPS;
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t FUSED_SMEM = cmax(cmax(FUSED_SMEM_CORR, hist_cfg::SMEM), feat_cfg::SMEM);
-constexpr long long FUSED_SPIN_LIMIT = 1ll << 24;
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(FUSED_NT, fused_minb(NF)) fused_kernel(FusedAr
                 long long spins = 0;
                 while (ld_acquire(a.ctr + item.wait) < item.target) {
                     if (*((volatile int *)a.abort)) { ok = 0; break; }
-                    if (++spins > FUSED_SPIN_LIMIT) {
+                    if (++spins > a.spin_limit) {
                         atomicExch(a.abort, 1);
                         atomicOr(a.flags + 2, 1);
                         ok = 0;
@@ -111,14 +112,14 @@ __global__ void __launch_bounds__(FUSED_NT, fused_minb(NF)) fused_kernel(FusedAr
 
 template <int NF>
 static cudaError_t launch_fused_t(const FusedArgs &a, int grid, cudaStream_t stream) {
-    static bool configured = false;
-    if (!configured) {
+    static PerDevice attr;
+    cudaError_t e_attr = attr.once([&]() {
         cudaError_t e = cudaFuncSetAttribute(fused_kernel<NF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)FUSED_SMEM);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+        return e;
+    });
+    if (e_attr != cudaSuccess) return e_attr;
     fused_kernel<NF><<<grid, FUSED_NT, FUSED_SMEM, stream>>>(a);
     return cudaGetLastError();
 }

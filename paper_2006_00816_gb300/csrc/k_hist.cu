@@ -14,13 +14,13 @@ __global__ void __launch_bounds__(hist_cfg::NT, 2) hist_kernel(const LevelDesc *
 
 cudaError_t launch_hist(const LevelDesc *descs, const Job *jobs, int njobs,
                         cudaStream_t stream) {
-    static bool configured = false;
-    if (!configured) {
+    static PerDevice attr;
+    cudaError_t e_attr = attr.once([&]() {
         cudaError_t e = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)hist_cfg::SMEM);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+        return e;
+    });
+    if (e_attr != cudaSuccess) return e_attr;
     if (njobs <= 0) return cudaSuccess;
     hist_kernel<<<njobs, hist_cfg::NT, hist_cfg::SMEM, stream>>>(descs, jobs);
     return cudaGetLastError();

@@ -490,16 +490,16 @@ int nms_cluster_size(int nframes, int max_npos, int request) {
 cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *flags,
                        cudaStream_t stream, int cluster_request) {
     if (nframes <= 0) return cudaSuccess;
-    static bool configured = false;
-    if (!configured) {
+    static PerDevice attr;
+    cudaError_t e_attr = attr.once([&]() {
         cudaError_t e = cudaFuncSetAttribute(nms_kernel<true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, NMS_SMEM_MAX);
         if (e == cudaSuccess)   // all of the unified L1 as shared memory: three frames per SM
             e = cudaFuncSetAttribute(nms_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+        return e;
+    });
+    if (e_attr != cudaSuccess) return e_attr;
     const int c = nms_cluster_size(nframes, max_npos, cluster_request);
     if (c >= 2) {
         cudaLaunchConfig_t cfg = {};

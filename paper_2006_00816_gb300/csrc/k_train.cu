@@ -173,13 +173,20 @@ namespace bw {
 constexpr int RC = WIN + 2;             // 12 region cells per side
 constexpr int RP = RC * CELL + CELL;    // 104 region pixels per side
 constexpr int NT = 256;
+static_assert(RP == TRAIN_RP, "region size of hog_backward_state");
 }  // namespace bw
 
+// With st_bins / st_trunc (may be NULL) the kernel also records the discrete
+// state it holds fixed: the bin of every region pixel ([RP][RP] per crop,
+// 255 where the pixel does not vote) and, per window cell and block k, the
+// 27 truncation tests x N_k < tau of its 18 signed and 9 unsigned values
+// ([100][4][27] per crop, 1 = below tau: the gradient passes).
 __global__ void __launch_bounds__(bw::NT) window_adjoint_kernel(
     const float *__restrict__ pyr, size_t pyr_stride, const float *__restrict__ hist,
     size_t hist_stride, TrainLevels lv, const int4 *__restrict__ best,
     const float *__restrict__ margin, const float *__restrict__ labels, int n,
-    const float *__restrict__ wuser, float eps, float tau, int recompute, float *__restrict__ dP) {
+    const float *__restrict__ wuser, float eps, float tau, int recompute, float *__restrict__ dP,
+    uint8_t *__restrict__ st_bins, uint8_t *__restrict__ st_trunc) {
     using namespace bw;
     extern __shared__ float sm[];
     float *H = sm;                           // [RC*RC][18] region histograms
@@ -234,6 +241,14 @@ __global__ void __launch_bounds__(bw::NT) window_adjoint_kernel(
                    E[(r + bdy[k]) * RC + c + bdx[k]];
             N[k] = 1.0f / sqrtf(S[k] + eps);
         }
+        if (st_trunc) {
+            uint8_t *st = st_trunc + ((size_t)i * WIN * WIN + t) * 4 * (NBIN + 9);
+            for (int k = 0; k < 4; k++) {
+                for (int o = 0; o < NBIN; o++) st[k * (NBIN + 9) + o] = hc[o] * N[k] < tau;
+                for (int o = 0; o < 9; o++)
+                    st[k * (NBIN + 9) + NBIN + o] = (hc[o] + hc[o + 9]) * N[k] < tau;
+            }
+        }
         for (int o = 0; o < NBIN; o++)
             for (int k = 0; k < 4; k++)
                 if (hc[o] * N[k] < tau) {
@@ -287,11 +302,13 @@ __global__ void __launch_bounds__(bw::NT) window_adjoint_kernel(
         const int ry = k / RP, rx = k % RP;
         const int X = X0 + rx, Y = Y0 + ry;
         float gx = 0.0f, gy = 0.0f;
+        int bin_state = 255;
         if (X >= 1 && X <= xmax && Y >= 1 && Y <= ymax) {
             const float dx = img[Y * w + X + 1] - img[Y * w + X - 1];
             const float dy = img[(Y + 1) * w + X] - img[(Y - 1) * w + X];
             const int b = fbin(dx, dy);
             if (b >= 0) {
+                bin_state = b;
                 const float mag = sqrtf(dx * dx + dy * dy);
                 // the pixel's two cells per axis, tent weights (offset t = footprint position)
                 const int ix = (X + 4) / CELL - 1, iy = (Y + 4) / CELL - 1;  // lower cell
@@ -310,6 +327,7 @@ __global__ void __launch_bounds__(bw::NT) window_adjoint_kernel(
         }
         GX[k] = gx;
         GY[k] = gy;
+        if (st_bins) st_bins[(size_t)i * RP * RP + k] = (uint8_t)bin_state;
     }
     __syncthreads();
 
@@ -405,18 +423,19 @@ cudaError_t launch_window_adjoint(const float *pyr, size_t pyr_stride, const flo
                                   size_t hist_stride, const TrainLevels &lv, const int4 *best,
                                   const float *margin, const float *labels, int n,
                                   const float *wuser, float eps, float tau, int recompute,
-                                  float *dP, cudaStream_t s) {
+                                  float *dP, uint8_t *st_bins, uint8_t *st_trunc, cudaStream_t s) {
     using namespace bw;
     const size_t smem = sizeof(float) * (2 * RC * RC * NBIN + RC * RC + WIN * WIN * 4 + 2 * RP * RP);
-    static bool configured = false;
-    if (!configured) {
+    static PerDevice attr;
+    cudaError_t e_attr = attr.once([&]() {
         cudaError_t e = cudaFuncSetAttribute(window_adjoint_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+        return e;
+    });
+    if (e_attr != cudaSuccess) return e_attr;
     window_adjoint_kernel<<<n, NT, smem, s>>>(pyr, pyr_stride, hist, hist_stride, lv, best, margin,
-                                              labels, n, wuser, eps, tau, recompute, dP);
+                                              labels, n, wuser, eps, tau, recompute, dP, st_bins,
+                                              st_trunc);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@ HOG_OK, HOG_EINVAL, HOG_ENOMEM, HOG_ECUDA, HOG_ECAPACITY, HOG_ETIMEOUT, HOG_EINT
     0, -1, -2, -3, -4, -5, -6)
 HOG_EBUSY = -7
 NFEAT, NBIN, CELL, WIN = 31, 18, 8, 10
+TRAIN_RP = (WIN + 2) * CELL + CELL   # pixels per side of a crop's adjoint region (hog_backward_state)
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libhog.so not built (run __graft_entry__.build()): %s" % LIB_PATH)
@@ -137,10 +138,13 @@ _SIGS = {
     "hog_nms_cluster_size": (C.c_int, [_vp, _i32, _i32, _i32, _P(_i32)]),
     "hog_autotune": (C.c_int, [_vp, _P(Frame), _i32, C.c_char_p, _vp]),
     "hog_get_tuning": (C.c_int, [_vp, _P(_i32), _P(_i32)]),
+    "hog_debug_waits": (C.c_int, [_vp, C.c_int64, _i32]),
     "hog_features_static": (C.c_int, [_P(Params), _P(Frame), _vp, C.c_size_t, _P(Level), _i32,
                                       _P(_i32), C.c_char_p, C.c_size_t, _vp]),
     "hog_backward": (C.c_int, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _P(C.c_float),
                                _i32, _vp]),
+    "hog_backward_state": (C.c_int, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp,
+                                     _P(C.c_float), _i32, _vp, _vp, _vp, _vp]),
     "hog_set_profiling": (C.c_int, [_vp, _i32]),
     "hog_stage_stats": (C.c_int, [_vp, _vp, _i32, _i32]),
     "hog_default_server_config": (None, [_P(ServerConfig)]),
@@ -191,16 +195,20 @@ def features_static(frame, params: Params | None = None, stream=None):
     device allocation by the library; the output tensor is allocated here by
     the caller side (torch).  Returns (list of [cy, cx, 31] tensors, rc, msg)."""
     import torch
+    if not (isinstance(frame, torch.Tensor) and frame.is_cuda):
+        raise ValueError("hog_features_static wants a CUDA uint8 tensor [h, w]")
     p = params or default_params()
     fr = _frame_of(frame)
     geo = level_geometry(fr.w, fr.h, p) if fr.w <= 16384 and fr.h <= 16384 else []
     total = sum(g[2] * g[3] * NFEAT for g in geo)
-    out = torch.empty(max(total, 1), dtype=torch.float32, device=frame.device)
-    lv = (Level * 64)()
-    n = _i32(0)
-    err = C.create_string_buffer(256)
-    rc = _lib.hog_features_static(C.byref(p), C.byref(fr), C.c_void_p(out.data_ptr()),
-                                  out.numel(), lv, 64, C.byref(n), err, 256, _stream_ptr(stream))
+    # the C side works on the current device: make it the frame's
+    with torch.cuda.device(frame.device):
+        out = torch.empty(max(total, 1), dtype=torch.float32, device=frame.device)
+        lv = (Level * 64)()
+        n = _i32(0)
+        err = C.create_string_buffer(256)
+        rc = _lib.hog_features_static(C.byref(p), C.byref(fr), C.c_void_p(out.data_ptr()),
+                                      out.numel(), lv, 64, C.byref(n), err, 256, _stream_ptr(stream))
     res = []
     if rc == 0:
         for i in range(n.value):
@@ -348,6 +356,29 @@ class Detector:
                                       C.byref(loss), int(bool(recompute)), _stream_ptr(stream)))
         return loss.value, dW, dI
 
+    def backward_state(self, images, labels, weights, recompute=False, stream=None):
+        """hog_backward_state: (loss, dW, dI, best [n, 4] (level, u, v,
+        active), bins [n, 104, 104] uint8, trunc [n, 100, 4, 27] uint8) --
+        the gradients and the discrete state the adjoint held fixed."""
+        import torch
+        assert images.is_cuda and images.dtype == torch.float32 and images.is_contiguous()
+        n, h, w = images.shape
+        labels = labels.contiguous()
+        weights = weights.contiguous()
+        dev = images.device
+        dW = torch.empty((10, 10, NFEAT), dtype=torch.float32, device=dev)
+        dI = torch.empty_like(images)
+        best = np.zeros((n, 4), np.int32)
+        bins = torch.full((n, TRAIN_RP, TRAIN_RP), 255, dtype=torch.uint8, device=dev)
+        trunc = torch.zeros((n, WIN * WIN, 4, NBIN + 9), dtype=torch.uint8, device=dev)
+        loss = C.c_float(0.0)
+        self._check(_lib.hog_backward_state(
+            self._h, C.c_void_p(images.data_ptr()), n, w, h, C.c_void_p(labels.data_ptr()),
+            C.c_void_p(weights.data_ptr()), C.c_void_p(dW.data_ptr()), C.c_void_p(dI.data_ptr()),
+            C.byref(loss), int(bool(recompute)), best.ctypes.data_as(_vp),
+            C.c_void_p(bins.data_ptr()), C.c_void_p(trunc.data_ptr()), _stream_ptr(stream)))
+        return loss.value, dW, dI, best, bins, trunc
+
     def set_batched_mode(self, mode):
         """1: persistent fused launch, 0: one launch per stage."""
         self._check(_lib.hog_set_batched_mode(self._h, int(mode)))
@@ -384,6 +415,15 @@ class Detector:
         m, p = _i32(0), _i32(0)
         self._check(_lib.hog_get_tuning(self._h, C.byref(m), C.byref(p)))
         return m.value, p.value
+
+    def debug_waits(self, polls=0, withhold=False):
+        """hog_debug_waits: poll budget of the fused launch's dependency
+        waits (0 = default) and, with withhold, a wait that is bound to run
+        out (the error path's test)."""
+        self._check(_lib.hog_debug_waits(self._h, int(polls), int(bool(withhold))))
+
+    def last_error(self):
+        return _lib.hog_last_error(self._h).decode()
 
     def set_filters(self, filters):
         w = np.ascontiguousarray(np.asarray(filters, dtype=np.float32))

@@ -4,10 +4,16 @@ planted ellipse, labels +1/-1).
 
 Bars: loss and best scores against the FP64 oracle; dW and dI against the
 oracle's FP64 adjoint to 1e-3 relative (floor 1e-6 of the largest
-magnitude); dI against FP64 central finite differences of the oracle's
-forward (eps 1e-3, 1e-3 relative), skipping perturbations that change a
-discrete state (bins, best window, truncation set); recompute modes and
-repeated calls bit-identical; torch autograd equal to the raw call."""
+magnitude) at every element, except where the GPU's FP32 forward took a
+discrete decision (best window, hinge activity, an orientation bin of the
+window's region, a truncation test of its cells) the other way from the
+oracle's FP64 forward -- there the two are gradients of different pieces of
+the piecewise-smooth loss.  The excluded elements are exactly those such a
+decision can reach (rule in _excluded_pixels) and are counted; dI against
+FP64 central finite differences of the oracle's forward (eps 1e-3, 1e-3
+relative), skipping perturbations that change a discrete state; recompute
+modes and repeated calls bit-identical; torch autograd equal to the raw
+call."""
 import numpy as np
 import pytest
 
@@ -42,21 +48,105 @@ def _close(g, o, rtol=1e-3):
     return np.abs(g - o) <= rtol * np.abs(o) + 1e-6 * scale
 
 
+RP = 104   # pixels per side of a window's adjoint region (12 x 12 cells + 4-pixel margins)
+
+
+def _excluded_pixels(oracle, img, W, gbest, gbins, gtrunc):
+    """Level-0 pixels of one crop whose dI may legitimately differ between
+    the GPU and the oracle, and whether the whole crop differs.
+
+    The adjoint holds a discrete state fixed (reading R10): the best window
+    and hinge activity, the orientation bin of every pixel voting into the
+    window's 12 x 12-cell region, and the window cells' truncation tests.
+    Where the two forwards took one of these decisions differently:
+      - best window or activity: the whole crop;
+      - a bin at level pixel r: the histograms of r's (up to) four cells
+        change, which changes dH of every cell within two cells of them (a
+        cell's dH reads the normalisers of the blocks around it, whose
+        energy gradients read the blocks' cells);
+      - a truncation test of window cell c: dH of c and of the cells of its
+        blocks (within one cell).
+    A level pixel is affected if it votes into such a cell; its dI, and the
+    central-difference neighbours it feeds, may differ (a 3x3 dilation);
+    the pyramid adjoint then carries each affected level pixel to the 2 x 2
+    source pixels of every level below.  Returns (mask [h, w], whole_crop)."""
+    (l, u, v), obins, otrunc = oracle.forward_state(img, W)
+    h, w = img.shape
+    if (l, u, v) != tuple(int(x) for x in gbest[:3]):
+        return np.ones((h, w), bool), True
+    lh, lw = obins.shape
+    cy, cx = lh // 8, lw // 8
+    xmax, ymax = min(lw - 2, 8 * cx - 1), min(lh - 2, 8 * cy - 1)
+    X0, Y0 = 8 * (v - 1) - 4, 8 * (u - 1) - 4
+    Y, X = np.mgrid[Y0:Y0 + RP, X0:X0 + RP]
+    inside = (X >= 1) & (X <= xmax) & (Y >= 1) & (Y <= ymax)
+    ob = np.full((RP, RP), 255, np.int32)
+    ob[inside] = obins[Y[inside], X[inside]]
+    ob[ob < 0] = 255
+    bad_cells = np.zeros((cy + 8, cx + 8), bool)     # cell (i, j) at [i + 4, j + 4]
+    for ry, rx in np.argwhere(ob != gbins.astype(np.int32)):
+        iy, ix = (Y[ry, rx] + 4) // 8 - 1, (X[ry, rx] + 4) // 8 - 1
+        bad_cells[iy - 2 + 4:iy + 4 + 4, ix - 2 + 4:ix + 4 + 4] = True
+    for cell in np.argwhere((otrunc != gtrunc).any(axis=(1, 2))).ravel():
+        ci, cj = u + cell // 10, v + cell % 10
+        bad_cells[ci - 1 + 4:ci + 2 + 4, cj - 1 + 4:cj + 2 + 4] = True
+    yy, xx = np.mgrid[0:lh, 0:lw]
+    iy, ix = (yy + 4) // 8 - 1 + 4, (xx + 4) // 8 - 1 + 4
+    m = bad_cells[iy, ix] | bad_cells[iy + 1, ix] | bad_cells[iy, ix + 1] | bad_cells[iy + 1, ix + 1]
+    d = np.zeros((lh + 2, lw + 2), bool)
+    for oy in range(3):
+        for ox in range(3):
+            d[oy:oy + lh, ox:ox + lw] |= m
+    m = d[1:-1, 1:-1]
+    sizes = oracle.level_sizes(w, h)
+    for q in range(l - 1, -1, -1):       # pyramid adjoint: level q + 1 -> q
+        qw, qh = sizes[q]
+        mq = np.zeros((qh, qw), bool)
+        for y1, x1 in np.argwhere(m):
+            y0, x0 = (12 * y1 + 1) // 10, (12 * x1 + 1) // 10
+            mq[y0:y0 + 2, x0:x0 + 2] = True
+        m = mq
+    return m, False
+
+
 def test_backward_matches_oracle_adjoint(H, oracle, data):
     imgs, labels, W = data
+    n = len(imgs)
     det = H.Detector(W[None], max_w=128, max_h=128, max_batch=1)
     ti, tl, tw = (torch.from_numpy(x).cuda() for x in (imgs, labels, W))
-    loss, dW, dI = det.backward(ti, tl, tw)
+    loss, dW, dI, gbest, gbins, gtrunc = det.backward_state(ti, tl, tw)
+    l2, dW2, dI2 = det.backward(ti, tl, tw)
+    assert l2 == loss and torch.equal(dW, dW2) and torch.equal(dI, dI2)   # same call
     oloss, osc, owin = oracle.hinge_loss(imgs, labels, W)
     assert loss == pytest.approx(oloss, rel=1e-5, abs=1e-6)
     assert (owin[:, 0] >= 1).any() and (owin[:, 0] == 0).any()
     ol, odW, odI = oracle.hinge_backward(imgs, labels, W)
-    g = dW.cpu().numpy().astype(np.float64)
-    assert _close(g, odW).all(), np.abs(g - odW).max()
+    gbins, gtrunc = gbins.cpu().numpy(), gtrunc.cpu().numpy()
+    oactive = (1.0 - labels.astype(np.float64) * osc) > 0
+    excl = np.zeros(imgs.shape, bool)
+    whole = []
+    for i in range(n):
+        if bool(gbest[i, 3]) != bool(oactive[i]):
+            excl[i], _ = True, whole.append(i)
+        elif oactive[i]:
+            excl[i], all_of_it = _excluded_pixels(oracle, imgs[i], W, gbest[i], gbins[i], gtrunc[i])
+            if all_of_it:
+                whole.append(i)
     gi = dI.cpu().numpy().astype(np.float64)
     ok = _close(gi, odI)
-    assert ok.mean() > 0.9999, (1 - ok.mean(), np.abs(gi - odI).max(), np.abs(odI).max())
-    assert np.linalg.norm(gi - odI) <= 1e-3 * np.linalg.norm(odI)
+    bad = ~ok & ~excl
+    print("adjoint: %d of %d crops differ as a whole, %d of %d pixels excluded, %d outside the bar"
+          % (len(whole), n, int(excl.sum()), excl.size, int((~ok).sum())))
+    assert not bad.any(), (np.argwhere(bad)[:10].tolist(), np.abs(gi - odI)[bad].max())
+    assert len(whole) <= 2 and excl.mean() < 0.02      # the rule excludes little
+    # dW: every crop whose best window and activity agree
+    keep = [i for i in range(n) if i not in whole]
+    if whole:
+        sub = np.array(keep)
+        _, odW, _ = oracle.hinge_backward(imgs[sub], labels[sub], W, with_image=False)
+        _, dW, _ = det.backward(ti[sub].contiguous(), tl[sub].contiguous(), tw, with_image=False)
+    g = dW.cpu().numpy().astype(np.float64)
+    assert _close(g, odW).all(), np.abs(g - odW).max()
 
 
 def test_backward_matches_finite_differences(H, oracle, data):

@@ -162,3 +162,76 @@ def test_autotune_records_engine(H, S, tmp_path):
     det2.set_corr_engine((rec["corr_engine"] + 1) % 3)
     det2.autotune(frames, cache_path=path)     # loaded from the file, not measured
     assert det2.corr_engine() == rec["corr_engine"]
+
+
+# Filter weights are trained SVM weights (Section 4.1.1, linear
+# classification), so their scale is not fixed.  A score is a dot product of
+# 3100 weights with features in [0, 0.85]; its rounding error grows with the
+# filter's l1 norm, so the score bar is 1e-4 at the scale of the N(0, 0.01)
+# workload filters (l1 norm 3100 x 0.01 x sqrt(2/pi) = 24.7) and scales with
+# the l1 norm above it.
+L1_REF = 3100 * 0.01 * np.sqrt(2 / np.pi)
+
+
+def _score_bar(W):
+    return SCORE_ATOL * np.maximum(1.0, np.abs(W).reshape(len(W), -1).sum(1) / L1_REF)
+
+
+@pytest.mark.parametrize("std", [1e-3, 1.0, 100.0])
+def test_filter_scales_every_engine(H, S, oracle, std):
+    f = S.eyeblink_frame(6)
+    W = S.filters(5, config=31, std=std)
+    assert np.abs(W).max() <= 1023.5                 # inside the tensor engines' fp16 range
+    det = H.Detector(W, max_w=640, max_h=480, max_batch=1)
+    assert det.corr_engine() == 1
+    ref = oracle.frame_scores(f, W)
+    bar = _score_bar(W)[:, None, None]
+    for e in (1, 2, 0):
+        det.set_corr_engine(e)
+        got = det.scores(dev(f))
+        for a, b in zip(got, ref):
+            err = np.abs(a.cpu().numpy().astype(np.float64) - b)
+            assert np.isfinite(a.cpu().numpy()).all()
+            assert (err <= bar).all(), (std, e, float(err.max()), bar.ravel().tolist())
+
+
+def test_filters_beyond_fp16_range_run_on_cuda_cores(H, S, oracle):
+    """A weight above HOG_TC_MAX_WEIGHT (64 w would overflow fp16) puts the
+    context on the FP32 CUDA-core engine, whose scores stay finite and
+    within the scaled bar; the tensor engines refuse those filters; a
+    non-finite weight is refused outright."""
+    f = S.eyeblink_frame(6)
+    W = S.filters(5, config=32, std=1.0)
+    W[2, 4, 4, 7] = 2000.0
+    W[0, 0, 0, 0] = -1500.0
+    det = H.Detector(W, max_w=640, max_h=480, max_batch=2)
+    assert det.corr_engine() == 0
+    assert "fp16" in det.last_error()
+    for e in (1, 2):
+        with pytest.raises(H.HogError) as ei:
+            det.set_corr_engine(e)
+        assert ei.value.code == H.HOG_EINVAL
+    assert det.corr_engine() == 0
+    bar = _score_bar(W)[:, None, None]
+    for a, b in zip(det.scores(dev(f)), oracle.frame_scores(f, W)):
+        a = a.cpu().numpy()
+        assert np.isfinite(a).all() and (np.abs(a.astype(np.float64) - b) <= bar).all()
+    dets, counts = det.detect([dev(f)])
+    assert counts[0] == len(dets) > 0 and np.isfinite(dets["score"]).all()
+    # back to in-range filters: the tensor engine can be selected again
+    W_ok = S.filters(5, config=33)
+    det.set_filters(W_ok)
+    det.set_corr_engine(1)
+    assert det.corr_engine() == 1
+    # a context on a tensor engine given out-of-range filters moves to engine 0
+    det.set_filters(W)
+    assert det.corr_engine() == 0
+    for bad in (np.nan, np.inf, -np.inf):
+        Wb = W_ok.copy()
+        Wb[1, 2, 3, 4] = bad
+        with pytest.raises(H.HogError) as ei:
+            det.set_filters(Wb)
+        assert ei.value.code == H.HOG_EINVAL
+        with pytest.raises(H.HogError):
+            H.Detector(Wb, max_w=640, max_h=480, max_batch=1)
+    assert det.corr_engine() == 0                    # the rejected call changed nothing

@@ -94,3 +94,57 @@ def test_inactive_crop_has_zero_gradient(oracle, batch):
     # labels scaled so that every margin y*s >= 2 > 1 -> inactive -> zero gradients
     loss, dW, dI = oracle.hinge_backward(imgs, np.sign(s) * np.maximum(1.0, 2.0 / np.abs(s)), W)
     assert loss == 0.0 and not dW.any() and not dI.any()
+
+
+def _fnv(values):
+    """The 64-bit FNV-style mix the oracle's forward signature applies to
+    each value in turn (x as int64, reinterpreted as uint64)."""
+    h = 1469598103934665603
+    for x in values:
+        h ^= int(x) & 0xFFFFFFFFFFFFFFFF
+        h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _atan2_bin(dx, dy):
+    """Nearest of the 18 signed centres 20 b degrees by atan2 (reading R4;
+    dx == 0 ties: 4 for dy > 0, 13 for dy < 0; -1 for a zero gradient)."""
+    if dx == 0 and dy == 0:
+        return -1
+    if dx == 0:
+        return 4 if dy > 0 else 13
+    ang = np.degrees(np.arctan2(dy, dx)) % 360.0
+    return int(np.floor(ang / 20.0 + 0.5)) % 18
+
+
+def test_forward_state_is_the_signature_state(oracle, batch):
+    """forward_state returns, as arrays, exactly what forward_signature
+    hashes (best window, every bin of its level, the window's truncation
+    tests); its bins follow the atan2 rule on the FP64 float pyramid, and the
+    truncation tests match a direct evaluation of the normalisers."""
+    imgs, labels, W = batch
+    for i in range(len(imgs)):
+        (l, u, v), bins, trunc = oracle.forward_state(imgs[i], W)
+        _, _, win = oracle.hinge_loss(imgs[i:i + 1], labels[i:i + 1], W)
+        assert (l, u, v) == tuple(win[0])
+        want = _fnv([l, u, v] + bins[1:-1, 1:-1].ravel().tolist() + trunc.ravel().tolist())
+        assert want == oracle.forward_signature(imgs[i], W)
+        lvl = oracle.pyramid_f64(imgs[i])[l]
+        rng = np.random.default_rng(i)
+        for y, x in zip(rng.integers(1, lvl.shape[0] - 1, 300), rng.integers(1, lvl.shape[1] - 1, 300)):
+            dx = lvl[y, x + 1] - lvl[y, x - 1]
+            dy = lvl[y + 1, x] - lvl[y - 1, x]
+            assert bins[y, x] == _atan2_bin(dx, dy)
+        hist = oracle.cell_hist(lvl)
+        cy, cx = hist.shape[:2]
+        E = ((hist[..., :9] + hist[..., 9:]) ** 2).sum(-1)
+        Ep = np.pad(E, 1)
+        for a, b, k in [(0, 0, 0), (4, 7, 3), (9, 9, 1), (5, 2, 2)]:
+            ci, cj = u + a, v + b
+            ddx, ddy = [(-1, -1), (1, -1), (-1, 1), (1, 1)][k]
+            S = Ep[ci + 1, cj + 1] + Ep[ci + 1, cj + 1 + ddx] + Ep[ci + 1 + ddy, cj + 1] + \
+                Ep[ci + 1 + ddy, cj + 1 + ddx]
+            N = 1.0 / np.sqrt(S + oracle.EPS)
+            hc = hist[ci, cj]
+            direct = np.concatenate([hc * N < oracle.TAU, (hc[:9] + hc[9:]) * N < oracle.TAU])
+            assert np.array_equal(trunc[a * 10 + b, k], direct.astype(np.uint8))

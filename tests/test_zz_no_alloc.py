@@ -32,7 +32,9 @@ def H():
 def test_static_features_match_context_features(H):
     from paper_2006_00816_gb300 import synth
     det = H.Detector(synth.filters(1), max_w=640, max_h=480, max_batch=1)
+    # an exact 640x480 frame (the largest legal size), then a ragged one
     frames = [synth.eyeblink_frame(4), synth.single_frame(333, 211, config=13)]
+    assert frames[0].shape == (480, 640)
     for f in frames:                       # two calls in a row, different sizes
         ft = torch.from_numpy(f).cuda()
         got, rc, msg = H.features_static(ft)
@@ -52,3 +54,19 @@ def test_static_features_reject_oversize(H):
     _, rc, msg = H.features_static(big)
     assert rc == H.HOG_EINVAL
     assert "exceeds the static limit 640x480" in msg
+
+
+def test_static_every_legal_size_fits(H):
+    """The scratch layout and the job table hold every frame up to the limit:
+    a sweep over widths and heights (the exact 640x480 limit included, the
+    largest legal frame) returns HOG_OK for each, never the scratch-too-small
+    or job-table-too-small error."""
+    sizes = [(w, h) for w in range(80, 641, 7) for h in (80, 241, 479, 480)]
+    sizes += [(w, h) for h in range(80, 481, 7) for w in (639, 640)]
+    sizes += [(640, 480), (640, 479), (639, 480), (80, 80), (81, 80)]
+    buf = torch.randint(0, 256, (480, 640), dtype=torch.uint8, device="cuda")
+    for w, h in sizes:
+        got, rc, msg = H.features_static(buf[:h, :w])
+        assert rc == 0, (w, h, msg)
+        assert len(got) >= 1
+    torch.cuda.synchronize()
