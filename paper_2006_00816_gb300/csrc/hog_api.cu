@@ -136,7 +136,8 @@ struct hog_ctx {
     uint8_t *d_pyr = nullptr;
     float *d_hist = nullptr, *d_feat = nullptr;
     uint64_t *d_keys = nullptr;
-    uint32_t *d_nmsws = nullptr;    // suppression workspace, 14 bytes (4 words) per position
+    uint32_t *d_nmsws = nullptr;    // suppression workspace, HOG_NMS_WS_WORDS per position
+    uint8_t *d_nmscand = nullptr;   // suppression: candidate flag per position
     hog_det *d_dets = nullptr;
     int32_t *d_counts = nullptr;
     int *d_flags = nullptr;
@@ -298,7 +299,7 @@ void free_ctx(hog_ctx *ctx) {
     auto F = [](void *p) { if (p) cudaFree(p); };
     auto FH = [](void *p) { if (p) cudaFreeHost(p); };
     F(ctx->d_w); F(ctx->d_pyr); F(ctx->d_hist); F(ctx->d_feat); F(ctx->d_keys);
-    F(ctx->d_nmsws); F(ctx->d_dets); F(ctx->d_counts); F(ctx->d_flags); F(ctx->d_plan);
+    F(ctx->d_nmsws); F(ctx->d_nmscand); F(ctx->d_dets); F(ctx->d_counts); F(ctx->d_flags); F(ctx->d_plan);
     F(ctx->d_stage);
     FH(ctx->h_plan); FH(ctx->h_dets); FH(ctx->h_counts); FH(ctx->h_flags); FH(ctx->h_stage);
     if (ctx->plan_done) cudaEventDestroy(ctx->plan_done);
@@ -669,7 +670,8 @@ void add_frame(hog_ctx *ctx, PlanBuilder &pb, const Geometry &g, const hog_frame
         }
         fd.lev_pos[g.nlev] = g.npos;
         fd.keys = keys;
-        fd.ws = ctx->d_nmsws + (size_t)slot * ctx->pos_slot * 4;
+        fd.ws = ctx->d_nmsws + (size_t)slot * ctx->pos_slot * HOG_NMS_WS_WORDS;
+        fd.cand = ctx->d_nmscand + (size_t)slot * ctx->pos_slot;
         fd.nbr = g.d_nbr;
         fd.nbr_t = g.d_nbr_t;
         fd.nbr_cnt = g.d_cnt;
@@ -1308,7 +1310,8 @@ int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters
     M((void **)&ctx->d_hist, B * ctx->hist_slot * sizeof(float));
     M((void **)&ctx->d_feat, B * ctx->feat_slot * sizeof(float));
     M((void **)&ctx->d_keys, B * ctx->pos_slot * sizeof(uint64_t));
-    M((void **)&ctx->d_nmsws, B * ctx->pos_slot * 4 * sizeof(uint32_t));
+    M((void **)&ctx->d_nmsws, B * ctx->pos_slot * HOG_NMS_WS_WORDS * sizeof(uint32_t));
+    M((void **)&ctx->d_nmscand, B * ctx->pos_slot);
     M((void **)&ctx->d_dets, B * D * sizeof(hog_det));
     M((void **)&ctx->d_counts, B * sizeof(int32_t));
     M((void **)&ctx->d_flags, sizeof(int) * 4);

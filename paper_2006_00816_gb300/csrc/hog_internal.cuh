@@ -49,6 +49,10 @@ constexpr int CHUNK = 8;            // channels per chunk of the internal featur
 constexpr int NCHUNK = 4;           // 4 x 8 = 32 channels (31 + one zero pad)
 constexpr int MAX_LEVELS = HOG_MAX_LEVELS;
 constexpr int MAXN = 192;           // suppression neighbours per window position (<= 150 seen at IoU 0.45)
+// 32-bit words of suppression workspace per window position and frame slot
+// (cluster form: above-mask, list length and overflow slot, 48 listed
+// neighbours; the one-CTA global-memory form uses 9 bytes of it)
+#define HOG_NMS_WS_WORDS 32
 
 // Tile shapes of the plain kernels.
 constexpr int PYR_TX = 160, PYR_TY = 32;         // output pixels per CTA (256 threads x 20)
@@ -162,10 +166,13 @@ struct FrameDesc {
     int32_t lev_pos[MAX_LEVELS + 1];
     double lev_rx[MAX_LEVELS], lev_ry[MAX_LEVELS];   // W/Wl, H/Hl (FP64, host-divided)
     const uint64_t *keys;             // [npos]
-    uint32_t *ws;                     // suppression workspace (global mode), 9 B per position
+    uint32_t *ws;                     // one-CTA global-memory form: workspace, 9 B per position;
+                                      // cluster form: masks and lists, HOG_NMS_WS_WORDS per position
     const int32_t *nbr;               // [MAXN][npos] neighbour lists, slot-major
     const int32_t *nbr_t;             // [npos][MAXN] the same lists, position-major
     const uint8_t *nbr_cnt;           // [npos]
+    uint8_t *cand;                    // [npos] 1 = scanned candidate (written by the cluster
+                                      // form's pre-pass; room for the position slot)
     hog_det *out;                     // [out_cap]
     int32_t out_cap;
     int32_t *count;                   // kept count (exact)

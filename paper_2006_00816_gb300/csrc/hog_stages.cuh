@@ -299,7 +299,8 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
     // bytes that exist but vote with weight 0 (their column's tent weights
     // are zeroed); zero gradients vote 0 as well (adding +0 leaves the
     // non-negative partials unchanged).  Magnitude sqrt(s) of the exact
-    // integer s = dx^2 + dy^2 as s * rsqrt(s).
+    // integer s = dx^2 + dy^2 by the hardware square root (sqrt.approx, a
+    // few ulp).
     const int by = t / bw, bx = t - by * bw;
     const int X0 = CELL * (j0 + bx) - 4, Y0 = CELL * (i0 + by) - 4;
     const bool active = t < bw * bh && i0 + by <= d.cy && j0 + bx <= d.cx;
@@ -332,7 +333,8 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         auto vote = [&](float dxf, float dyf, int ox) {
             const uint32_t boff = orientation_bin_f<NT * sizeof(float2)>(dxf, dyf);   // bytes
             const float sf = fmaf(dxf, dxf, dyf * dyf);       // dx^2 + dy^2, exact
-            const float m = sf * rsqrtf(sf + 1e-30f);         // sqrt(sf); 0 for sf = 0
+            float m;                                          // sqrt(sf); 0 for sf = 0
+            asm("sqrt.approx.f32 %0, %1;" : "=f"(m) : "f"(sf));
             const float m0 = m * wy0, m1 = m * wy1;
             float2 *pb = reinterpret_cast<float2 *>(reinterpret_cast<char *>(p0) + boff);
             float2 a = pb[0], c = pb[PB * NT];

@@ -21,6 +21,8 @@
 // IoU > nms_iou, computed in FP64 with explicitly rounded operations (no
 // fused multiply-add), so the test matches a host evaluation of the same
 // formula bit for bit.
+#include <algorithm>
+
 #include "hog_stages.cuh"
 
 namespace hogk {
@@ -202,6 +204,11 @@ __device__ __forceinline__ void cl_or_u32(uint32_t addr, uint32_t v) {
 __device__ __forceinline__ void cl_st_u32(uint32_t addr, uint32_t v) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
+__device__ __forceinline__ void cl_st_v4(uint32_t addr, uint4 v) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
 __device__ __forceinline__ void cl_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
                  "barrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -209,14 +216,94 @@ __device__ __forceinline__ void cl_sync() {
 }  // namespace
 
 constexpr int NMS_MAX_CLUSTER = 16;
-// per CTA: key high words, two lists (4 B each), the suppression bits, and
-// state and resume slot (1 B each) of its owned positions
-__host__ __device__ constexpr size_t nms_cluster_ws_bytes(int npos, int c) {
-    return (size_t)((npos + c - 1) / c) * 14 + 4 * (size_t)(((npos + c - 1) / c + 31) / 32) + 64;
+constexpr int NMS_MASK_WORDS = MAXN / 32;   // 192 neighbour slots: six 32-bit words
+// Higher-ranked neighbours a CTA caches per owned candidate (cluster form,
+// mode 2); a candidate with more keeps the rest in its global above-mask.
+constexpr int NMS_LIST = 48;
+constexpr int NMS_WS_WORDS = 8 + NMS_LIST / 2;   // global workspace per position (cluster form)
+static_assert(NMS_WS_WORDS == HOG_NMS_WS_WORDS, "workspace stride");
+// Cluster-form modes: 0 scans every neighbour slot through L2 and compares
+// keys; 1 scans only the above-mask's slots (mask in shared memory); 2 checks
+// a cached list of the higher-ranked neighbours' positions each round.
+// Per CTA: key high words, two lists (4 B each), the suppression bits, and
+// state and resume slot (1 B each) of its owned positions; mode 1 adds each
+// owned position's above-mask (24 B), mode 2 its cached list (96 B), its
+// length and its overflow slot (1 B each).
+__host__ __device__ constexpr size_t nms_cluster_ws_bytes(int npos, int c, int mode) {
+    return (size_t)((npos + c - 1) / c) * (14 + (mode == 1 ? 4 * NMS_MASK_WORDS : 0)) +
+           4 * (size_t)(((npos + c - 1) / c + 31) / 32) + 64 + (mode ? 16 : 0);
+}
+// Replicated-state cluster form: the owned slice of P positions (a multiple
+// of 32), the state of every position of the frame (C P bytes), resume
+// entry, list length and overflow slot (1 B each, then 3 B of padding to
+// keep the lists 16-byte aligned) and the cached list (48 entries in a
+// 112-byte row) per owned position, a changed flag per 16 positions and a
+// suppression bit per owned position.
+__host__ __device__ constexpr int nms_rep_slice(int npos, int c) {
+    return ((npos + c - 1) / c + 31) / 32 * 32;
+}
+// Shared-memory list stride (halves): 112 bytes, so that the 16-byte loads
+// of eight consecutive positions' lists fall on distinct banks.
+constexpr int NMS_LIST_STRIDE = 56;
+__host__ __device__ constexpr size_t nms_rep_ws_bytes(int npos, int c) {
+    return (size_t)nms_rep_slice(npos, c) * (c + 6 + 2 * NMS_LIST_STRIDE) + nms_rep_slice(npos, c) / 16 +
+           nms_rep_slice(npos, c) / 8 + 64;
 }
 
+// Above-masks and lists for the cluster form.  For every window position p
+// of every frame, bit s of the mask is set iff neighbour slot s of p holds a
+// scanned candidate ranked above p (full key smaller: score, then level,
+// filter, u, v), and the list holds the positions of the first NMS_LIST such
+// neighbours in slot order.  One warp per position, a lane per slot; the
+// whole GPU takes part, so a frame's pairwise rank tests cost one short
+// launch, and the rounds that follow only look at the neighbours a mask or
+// list names.  Written to the frame's workspace fd.ws, NMS_WS_WORDS words per
+// position: words 0-5 the mask, word 6 the list's length, word 7 the slot
+// where the mask goes on past the list (255: nowhere), words 8-31 the list
+// as 16-bit positions (positions below 65536; longer frames keep the mask
+// only).  Non-candidates get an empty mask and list.  fd.cand[p] records
+// whether p is a candidate.
+__global__ void __launch_bounds__(256) nms_above_kernel(const FrameDesc *__restrict__ frames) {
+    const FrameDesc &fd = frames[blockIdx.y];
+    const int p = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (p >= fd.npos) return;
+    uint32_t *ws = fd.ws + (size_t)p * NMS_WS_WORDS;
+    uint16_t *list = reinterpret_cast<uint16_t *>(ws + 8);
+    const uint64_t kp = nms_scanned(fd, p) ? __ldg(fd.keys + p) : KEY_NONE;
+    if (lane == 0) fd.cand[p] = kp != KEY_NONE;
+    if (kp == KEY_NONE) {
+        if (lane < 8) ws[lane] = lane == 7 ? 255u : 0u;
+        return;
+    }
+    const int32_t *row = fd.nbr_t + (size_t)p * MAXN;
+    uint32_t mine = 0u;   // lane w < 6 ends up holding word w
+    bool ended = false;
+    int k = 0, ovf = 255;
+    for (int w = 0; w < NMS_MASK_WORDS; w++) {
+        unsigned above = 0u;
+        if (!ended) {
+            const int q = __ldg(row + w * 32 + lane);
+            const bool a = q >= 0 && nms_scanned(fd, q) && __ldg(fd.keys + q) < kp;
+            above = __ballot_sync(0xffffffffu, a);
+            ended = __ballot_sync(0xffffffffu, q < 0) != 0u;   // -1 past the list's end
+            const int idx = k + __popc(above & ((1u << lane) - 1u));
+            if (a && idx < NMS_LIST) list[idx] = (uint16_t)q;
+            if (a && idx == NMS_LIST) ovf = w * 32 + lane;     // first slot past the list
+            k += __popc(above);
+        }
+        if (lane == w) mine = above;
+    }
+    const unsigned has_ovf = __ballot_sync(0xffffffffu, ovf != 255);
+    if (has_ovf) ovf = __shfl_sync(0xffffffffu, ovf, __ffs(has_ovf) - 1);
+    if (lane < NMS_MASK_WORDS) ws[lane] = mine;
+    if (lane == 6) ws[6] = (uint32_t)(k < NMS_LIST ? k : NMS_LIST);
+    if (lane == 7) ws[7] = (uint32_t)ovf;
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc *__restrict__ frames,
                                                                 int *flags) {
+    constexpr bool MASK = MODE == 1;
     extern __shared__ __align__(16) unsigned char nsm[];
     __shared__ int sh[NMS_NT / 32 + 4];
     __shared__ int s_cnt[2][NMS_MAX_CLUSTER];     // read in CTA 0: undecided per CTA
@@ -236,6 +323,9 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
     volatile uint32_t *supp = reinterpret_cast<volatile uint32_t *>(nsm + (size_t)P * 12);   // bits [P]
     volatile uint8_t *state = nsm + (size_t)P * 12 + 4 * (size_t)PW;                        // [P]
     uint8_t *resume = nsm + (size_t)P * 13 + 4 * (size_t)PW;                                 // [P]
+    // mode 1: each owned position's above-mask (nms_above_kernel), [P][6]
+    uint32_t *amask = reinterpret_cast<uint32_t *>(
+        (reinterpret_cast<uintptr_t>(nsm + (size_t)P * 14 + 4 * (size_t)PW) + 15) & ~(uintptr_t)15);
     const uint64_t *gkeys = fd.keys;
     const int32_t *__restrict__ nbr = fd.nbr;
     const int32_t *__restrict__ nbr_t = fd.nbr_t;
@@ -280,7 +370,12 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
         }
         append(h != NMS_NOKEY, i, 0);
     }
-    cl_sync();   // every CTA's keys, states and bits are initialised
+    if (MASK)
+        for (int k = t; k < nmine * NMS_MASK_WORDS; k += NMS_NT) {
+            const int i = k / NMS_MASK_WORDS;
+            amask[k] = __ldg(fd.ws + (size_t)(lo + i) * NMS_WS_WORDS + (k - i * NMS_MASK_WORDS));
+        }
+    cl_sync();   // every CTA's keys, states, bits and masks are initialised
 
     int cur = 0, round = 0;
     for (; round <= npos; round++) {
@@ -292,11 +387,50 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
             if (i < n_cur) {
                 li = list[cur][i];
                 p = lo + li;
-                const uint32_t hp = khi[li];
-                const int n = __ldg(nbr_cnt + p);
                 bool dead = (supp[li >> 5] >> (li & 31)) & 1u, wait = false;
                 const int r0 = resume[li];
                 int settled = r0;
+                if (MASK) {
+                    // only the higher-ranked candidates among p's neighbours (the
+                    // set bits of its mask, from the resume slot on), up to four
+                    // in flight: one kept -> suppressed, one undecided -> wait
+                    const uint32_t *mk = amask + (size_t)li * NMS_MASK_WORDS;
+                    int w = settled >> 5;
+                    uint32_t bits = w < NMS_MASK_WORDS ? mk[w] & (~0u << (settled & 31)) : 0u;
+                    while (!dead && !wait) {
+                        int sl[4], ns = 0;
+                        while (ns < 4) {
+                            while (!bits && ++w < NMS_MASK_WORDS) bits = mk[w];
+                            if (!bits) break;
+                            sl[ns++] = w * 32 + __ffs(bits) - 1;
+                            bits &= bits - 1;
+                        }
+                        if (ns == 0) break;   // every higher-ranked neighbour is suppressed
+                        int q[4];
+                        uint32_t sq[4];
+#pragma unroll
+                        for (int k = 0; k < 4; k++)
+                            q[k] = k < ns ? __ldg(nbr_t + (size_t)p * MAXN + sl[k]) : 0;
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            sq[k] = NMS_DEAD;
+                            if (k < ns) {
+                                const int o = owner(q[k]);
+                                sq[k] = cl_ld_u8(s_rstate[o] + (uint32_t)(q[k] - o * P));
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            if (k >= ns || dead || wait) continue;
+                            if (sq[k] == NMS_KEPT) dead = true;
+                            else if (sq[k] == NMS_ALIVE) { wait = true; settled = sl[k]; }
+                            else settled = sl[k] + 1;
+                        }
+                        if (ns < 4) break;
+                    }
+                }
+                const uint32_t hp = khi[li];
+                const int n = MODE ? 0 : __ldg(nbr_cnt + p);
                 for (int s0 = r0; s0 < n && !dead && !wait; s0 += 4) {
                     int q[4];
 #pragma unroll
@@ -424,23 +558,282 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
     cl_sync();   // no CTA leaves while another may still read its shared memory
 }
 
-namespace {
-int g_nsm = 0;             // SM count of the device
-int g_cluster_max = -1;    // largest cluster size the device can run (1 = none)
 
-int nms_cluster_max() {
-    if (g_cluster_max >= 0) return g_cluster_max;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
-    g_cluster_max = 1;
-    if (cudaFuncSetAttribute(nms_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             NMS_SMEM_MAX) != cudaSuccess ||
-        cudaFuncSetAttribute(nms_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-            cudaSuccess) {
-        cudaGetLastError();
-        return g_cluster_max;
+// ---- replicated-state cluster form ------------------------------------------
+// For frames of at most 65535 positions whose per-position lists fit: every
+// CTA of the cluster keeps the state of EVERY position of the frame (one
+// byte each: 9.5 KB for a 640x480 frame), so a candidate's checks read only
+// local shared memory.  CTA r decides its own slice of P positions; each of
+// its candidates checks, each round, all its higher-ranked neighbours from
+// the list the pre-pass wrote (nms_above_kernel): one kept -> suppressed;
+// one undecided -> wait; all suppressed -> the rest of its above-mask, if
+// any (through L2), then kept.  At the end of a round every CTA copies its
+// slice of states, as 32-bit words, into the other CTAs' copies, and a
+// cluster barrier (release/acquire) closes the round.  A copy may receive a
+// newer slice while its CTA still reads it: states only move from undecided
+// to decided, so a newer value is as good as the old one.  The rounds reach
+// the same fixed point as the one-CTA form.
+__global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_rep_kernel(const FrameDesc *__restrict__ frames,
+                                                                    int *flags) {
+    extern __shared__ __align__(16) unsigned char nsm[];
+    __shared__ int sh[NMS_NT / 32 + 4];
+    __shared__ int s_cnt[2][NMS_MAX_CLUSTER];
+    __shared__ int s_kept[NMS_MAX_CLUSTER];
+    __shared__ uint32_t s_rst[NMS_MAX_CLUSTER], s_rsupp[NMS_MAX_CLUSTER];
+    __shared__ int s_total;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int C = (int)cl_size(), rank = (int)cl_rank();
+    const FrameDesc &fd = frames[cl_id()];
+    const int npos = fd.npos;
+    const int P = nms_rep_slice(npos, C);
+    const int lo = min(rank * P, npos), nmine = min(lo + P, npos) - lo;
+    uint8_t *st = nsm;                                                          // [C P] all states
+    uint8_t *resume = nsm + (size_t)C * P;                                      // [P]
+    uint8_t *lcnt = resume + P, *lovf = lcnt + P;                               // [P], [P]
+    uint16_t *alist = reinterpret_cast<uint16_t *>(lovf + P + 3 * (size_t)P);   // [P][56], 16-B aligned
+    // suppression bits of the owned positions, set (remote atomic OR) by a
+    // kept neighbour in any CTA: such a position is suppressed without a check
+    volatile uint32_t *supp = reinterpret_cast<volatile uint32_t *>(alist + (size_t)P * NMS_LIST_STRIDE);  // [P / 32]
+    uint8_t *dirty = reinterpret_cast<uint8_t *>(const_cast<uint32_t *>(supp) + P / 32);              // [P / 16]
+    const int32_t *__restrict__ nbr_t = fd.nbr_t;
+    const int base = rank * P;      // owned slice of the copy, 16-byte aligned (lo: clamped to npos)
+    const int nch = P / 16;
+
+    if (t < C) {
+        s_rst[t] = cl_map(st, t);
+        s_rsupp[t] = cl_map((const void *)supp, t);
     }
+    for (int c = t; c < nch; c += NMS_NT) dirty[c] = 0;
+    for (int c = t; c < P / 32; c += NMS_NT) supp[c] = 0u;
+    const uint32_t *__restrict__ ws = fd.ws;
+    // every position's initial state from the pre-pass's candidate flags, 16
+    // positions per load (flags are 0 or 1: ALIVE = 1, DEAD = 0; positions
+    // past npos: suppressed; the flag array has room for whole 16-byte
+    // chunks up to the position slot)
+    static_assert(NMS_ALIVE == 1 && NMS_DEAD == 0, "states as candidate flags");
+    for (int c0 = t; c0 < C * P / 16; c0 += NMS_NT) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (16 * c0 < npos) v = __ldg(reinterpret_cast<const uint4 *>(fd.cand) + c0);
+        if (16 * c0 + 16 > npos) {   // the chunk holding npos: clear bytes past it
+            uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int b = 0; b < 16; b++)
+                if (16 * c0 + b >= npos) w[b >> 2] &= ~(0xffu << (8 * (b & 3)));
+            v = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        reinterpret_cast<uint4 *>(st)[c0] = v;
+    }
+    // the owned candidates' lists, as the pre-pass wrote them (eight loads
+    // in flight per thread)
+    constexpr int LW = NMS_LIST / 2;
+    for (int k0 = t; k0 < nmine * LW; k0 += 8 * NMS_NT) {
+        uint32_t v[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int k = k0 + j * NMS_NT, i = k / LW;
+            v[j] = k < nmine * LW ? __ldg(ws + (size_t)(lo + i) * NMS_WS_WORDS + 8 + (k - i * LW)) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int k = k0 + j * NMS_NT, i = k / LW;
+            if (k < nmine * LW) reinterpret_cast<uint32_t *>(alist)[i * (NMS_LIST_STRIDE / 2) + (k - i * LW)] = v[j];
+        }
+    }
+    for (int i = t; i < nmine; i += NMS_NT) {
+        const uint32_t c = __ldg(ws + (size_t)(lo + i) * NMS_WS_WORDS + 6);
+        const uint32_t o = __ldg(ws + (size_t)(lo + i) * NMS_WS_WORDS + 7);
+        lcnt[i] = (uint8_t)c;
+        lovf[i] = (uint8_t)o;
+        resume[i] = 0;
+    }
+    cl_sync();   // no CTA writes into another's copy before that one is initialised
+
+    // Each thread owns the positions t, t + NT, ... of the slice and decides
+    // its undecided ones; __syncthreads_count gives the CTA's undecided count.
+    int round = 0;
+    for (; round <= npos; round++) {
+        bool any = false;
+        int kept0 = -1, kept1 = -1;   // positions this thread keeps this round (P <= 2 NT)
+        for (int li = t; li < nmine; li += NMS_NT) {
+            const int p = lo + li;
+            if (st[p] != NMS_ALIVE) continue;
+            const int n2 = lcnt[li];
+            const uint16_t *al = alist + (size_t)li * NMS_LIST_STRIDE;   // 16-byte aligned
+            bool dead = (supp[li >> 5] >> (li & 31)) & 1u, wait = false, prefix = true;
+            const int r0 = resume[li];
+            int settled = r0;
+            // eight listed neighbours per 16-byte load, their states in flight
+            // together; the check ends at a kept one (suppressed) or at the
+            // eight-entry group holding the first undecided one (wait: a
+            // candidate that waits looks again next round, from its first
+            // undecided neighbour on)
+            for (int k0 = r0 & ~7; k0 < n2 && !dead && !wait; k0 += 8) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(al + k0);
+                const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+                uint8_t sq[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int k = k0 + j;
+                    sq[j] = (k >= r0 && k < n2) ? st[(w4[j >> 1] >> (16 * (j & 1))) & 0xffffu] : NMS_DEAD;
+                }
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int k = k0 + j;
+                    if (k < r0 || k >= n2) continue;
+                    if (sq[j] == NMS_KEPT) dead = true;
+                    else if (sq[j] == NMS_ALIVE) { wait = true; prefix = false; }
+                    else if (prefix) settled = k + 1;
+                }
+            }
+            int ov = lovf[li];
+            if (!dead && !wait && ov != 255) {
+                // the rest of the above-mask, from slot ov, through L2
+                const uint32_t *mk = ws + (size_t)p * NMS_WS_WORDS;
+                int w = ov >> 5;
+                uint32_t bits = __ldg(mk + w) & (~0u << (ov & 31));
+                for (;;) {
+                    while (!bits && ++w < NMS_MASK_WORDS) bits = __ldg(mk + w);
+                    if (!bits) { ov = 255; break; }
+                    const int sl = w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const uint8_t sq = st[__ldg(nbr_t + (size_t)p * MAXN + sl)];
+                    if (sq == NMS_KEPT) { dead = true; break; }
+                    if (sq == NMS_ALIVE) { wait = true; ov = sl; break; }
+                }
+                lovf[li] = (uint8_t)ov;
+            }
+            if (dead || !wait) {
+                st[p] = dead ? NMS_DEAD : NMS_KEPT;
+                dirty[(p - base) >> 4] = 1;
+                if (!dead) (li < NMS_NT ? kept0 : kept1) = p;
+            } else {
+                any = true;
+                resume[li] = (uint8_t)settled;
+            }
+        }
+        // each kept candidate marks its still-undecided neighbours in their
+        // owners' suppression bits, the warp's lanes splitting the slots
+#pragma unroll
+        for (int m = 0; m < 2; m++) {
+            const int kp = m ? kept1 : kept0;
+            for (unsigned km = __ballot_sync(0xffffffffu, kp >= 0); km; km &= km - 1) {
+                const int pk = __shfl_sync(0xffffffffu, kp, __ffs(km) - 1);
+                int q[MAXN / 32];   // all six 32-slot chunks in flight (-1 past the list's end)
+#pragma unroll
+                for (int j = 0; j < MAXN / 32; j++) q[j] = __ldg(nbr_t + (size_t)pk * MAXN + 32 * j + lane);
+#pragma unroll
+                for (int j = 0; j < MAXN / 32; j++) {
+                    if (q[j] >= 0 && st[q[j]] == NMS_ALIVE) {
+                        const int o = q[j] / P, lq = q[j] - o * P;
+                        cl_or_u32(s_rsupp[o] + 4u * (uint32_t)(lq >> 5), 1u << (lq & 31));
+                    }
+                }
+            }
+        }
+        const int n_und = __syncthreads_count(any);
+        // the 16-byte chunks of this CTA's slice that changed this round,
+        // into every other CTA's copy (bytes [base, base + P): aligned and
+        // inside the C P-byte copy), and this CTA's undecided count into
+        // every CTA's count table (slot by round parity: slot r & 1 is
+        // rewritten two rounds later, after every CTA has read it)
+        for (int k = t; k < nch * (C - 1); k += NMS_NT) {
+            const int r = k / nch, c = k - r * nch;
+            if (!dirty[c]) continue;
+            const int dst = r < rank ? r : r + 1;
+            cl_st_v4(s_rst[dst] + (uint32_t)(base + 16 * c), *reinterpret_cast<const uint4 *>(st + base + 16 * c));
+        }
+        if (t < C) cl_st_u32(cl_map(&s_cnt[round & 1][rank], t), (uint32_t)n_und);
+        cl_sync();
+        for (int c = t; c < nch; c += NMS_NT) dirty[c] = 0;
+        if (wid == 0) {
+            int c = lane < C ? s_cnt[round & 1][lane] : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0) s_total = c;
+        }
+        __syncthreads();
+        if (s_total == 0) break;
+    }
+
+    // kept positions in position order: CTA r's before CTA r+1's
+    int *s_warp = sh;
+    const int per = (nmine + NMS_NT - 1) / NMS_NT;
+    const int beg = min(t * per, nmine), end = min(beg + per, nmine);
+    int mine_kept = 0;
+    for (int i = beg; i < end; i++) mine_kept += st[lo + i] == NMS_KEPT;
+    int incl = mine_kept;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int k = 0; k < NMS_NT / 32; k++) {
+            const int x = s_warp[k];
+            s_warp[k] = run;
+            run += x;
+        }
+        cl_st_u32(cl_map(&s_kept[rank], 0), (uint32_t)run);
+    }
+    cl_sync();
+    if (wid == 0) {
+        const int c = lane < C ? (int)cl_ld_u32(cl_map(&s_kept[lane], 0)) : 0;
+        int before = lane < rank ? c : 0, all = c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            before += __shfl_xor_sync(0xffffffffu, before, o);
+            all += __shfl_xor_sync(0xffffffffu, all, o);
+        }
+        if (lane == 0) { sh[NMS_NT / 32] = before; s_total = all; }
+    }
+    __syncthreads();
+    const int total = s_total;
+    int pos = sh[NMS_NT / 32] + s_warp[wid] + incl - mine_kept;
+    for (int i = beg; i < end; i++) {
+        if (st[lo + i] != NMS_KEPT) continue;
+        if (pos < fd.out_cap) {
+            const uint64_t k = __ldg(fd.keys + lo + i);
+            const int l = key_level(k);
+            const int u = key_u(k), v = key_v(k);
+            const WinBox b = window_box(fd.lev_rx[l], fd.lev_ry[l], u, v);
+            hog_det det;
+            det.frame = fd.frame;
+            det.level = l;
+            det.filter = key_filter(k);
+            det.u = u;
+            det.v = v;
+            det.score = key_score(k);
+            det.x = b.x; det.y = b.y; det.w = b.w; det.h = b.h;
+            fd.out[pos] = det;
+        }
+        pos++;
+    }
+    if (rank == 0 && t == 0) {
+        *fd.count = total;
+        if (total > fd.out_cap) atomicOr(flags, 1);
+        atomicMax(flags + 1, round + 1);
+    }
+    cl_sync();   // no CTA leaves while another may still write into its copy
+}
+
+namespace {
+constexpr int NMS_MAX_DEVICES = 64;
+int g_nsm[NMS_MAX_DEVICES];           // SM count of each device
+int g_cluster_max[NMS_MAX_DEVICES];   // largest cluster size each device can run (1 = none)
+PerDevice g_cluster_setup;
+
+template <class K>
+bool cluster_attrs(K kern) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, NMS_SMEM_MAX) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+}
+
+template <class K>
+int largest_cluster(K kern) {
     for (int c = NMS_MAX_CLUSTER; c >= 2; c >>= 1) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
@@ -454,13 +847,39 @@ int nms_cluster_max() {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, nms_cluster_kernel, &cfg) == cudaSuccess && n > 0) {
-            g_cluster_max = c;
-            break;
-        }
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0) return c;
         cudaGetLastError();
     }
-    return g_cluster_max;
+    return 1;
+}
+
+// The cluster kernels' attributes are set once per device; returns the
+// largest cluster size both can run there and the device's SM count.
+int nms_cluster_max(int *nsm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NMS_MAX_DEVICES) {
+        cudaGetLastError();
+        *nsm = 1;
+        return 1;
+    }
+    g_cluster_setup.once([&]() -> cudaError_t {
+        int n = 1;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        g_nsm[dev] = n > 0 ? n : 1;
+        g_cluster_max[dev] = 1;
+        if (!cluster_attrs(nms_cluster_kernel<0>) || !cluster_attrs(nms_cluster_kernel<1>) ||
+            !cluster_attrs(nms_cluster_rep_kernel)) {
+            cudaGetLastError();
+            return cudaSuccess;
+        }
+        int m = largest_cluster(nms_cluster_kernel<0>);
+        m = std::min(m, largest_cluster(nms_cluster_kernel<1>));
+        m = std::min(m, largest_cluster(nms_cluster_rep_kernel));
+        g_cluster_max[dev] = m;
+        return cudaSuccess;
+    });
+    *nsm = g_nsm[dev];
+    return g_cluster_max[dev];
 }
 }  // namespace
 
@@ -469,21 +888,22 @@ int nms_cluster_max() {
 // power of two), and at least the size whose per-CTA state fits in shared
 // memory.  Returns 1 for the one-CTA form.
 int nms_cluster_size(int nframes, int max_npos, int request) {
-    const int cmax = nms_cluster_max();
+    int nsm = 1;
+    const int cmax = nms_cluster_max(&nsm);
     if (cmax < 2 || request == 1 || nframes <= 0) return 1;
     int c;
     if (request >= 2) {
         c = request > cmax ? cmax : request;
     } else {
-        const int want = g_nsm / nframes;
+        const int want = nsm / nframes;
         c = 1;
         while (c * 2 <= want && c * 2 <= cmax) c *= 2;
         if ((nms_ws_bytes(max_npos, true) > (size_t)NMS_SMEM_MAX || max_npos > NMS_SMEM_MAX_NPOS) &&
             c < 2)
             c = 2;
     }
-    while (c < cmax && nms_cluster_ws_bytes(max_npos, c) > (size_t)NMS_SMEM_MAX) c *= 2;
-    if (c >= 2 && nms_cluster_ws_bytes(max_npos, c) > (size_t)NMS_SMEM_MAX) return 1;
+    while (c < cmax && nms_cluster_ws_bytes(max_npos, c, 0) > (size_t)NMS_SMEM_MAX) c *= 2;
+    if (c >= 2 && nms_cluster_ws_bytes(max_npos, c, 0) > (size_t)NMS_SMEM_MAX) return 1;
     return c;
 }
 
@@ -510,11 +930,25 @@ cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *
         at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(nframes * c);
         cfg.blockDim = dim3(NMS_NT);
-        cfg.dynamicSmemBytes = nms_cluster_ws_bytes(max_npos, c);
         cfg.stream = stream;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, nms_cluster_kernel, frames, flags);
+        // with the above-masks and cached lists (16-bit positions) when they
+        // fit in the CTAs' shared memory, else with the masks alone
+        const size_t ws2 = nms_rep_ws_bytes(max_npos, c), ws1 = nms_cluster_ws_bytes(max_npos, c, 1);
+        if (ws1 <= (size_t)NMS_SMEM_MAX || ws2 <= (size_t)NMS_SMEM_MAX) {
+            nms_above_kernel<<<dim3((max_npos + 7) / 8, nframes), 256, 0, stream>>>(frames);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            if (ws2 <= (size_t)NMS_SMEM_MAX && max_npos <= 65535 && nms_rep_slice(max_npos, c) <= 2 * NMS_NT) {
+                cfg.dynamicSmemBytes = ws2;
+                return cudaLaunchKernelEx(&cfg, nms_cluster_rep_kernel, frames, flags);
+            }
+            cfg.dynamicSmemBytes = ws1;
+            return cudaLaunchKernelEx(&cfg, nms_cluster_kernel<1>, frames, flags);
+        }
+        cfg.dynamicSmemBytes = nms_cluster_ws_bytes(max_npos, c, 0);
+        return cudaLaunchKernelEx(&cfg, nms_cluster_kernel<0>, frames, flags);
     }
     const size_t ws = nms_ws_bytes(max_npos, true);
     if (ws <= (size_t)NMS_SMEM_MAX && max_npos <= NMS_SMEM_MAX_NPOS)
