@@ -117,7 +117,9 @@ struct PlanInfo {
 enum { MODE_STAGED = 0, MODE_FUSED = 1 };
 
 struct CachedPlan {
-    std::vector<uint64_t> sig;
+    std::vector<uint64_t> sig;              // batch shape: sizes, pitches, pointer alignment, regions
+    std::vector<const uint8_t *> fptr;      // the frames' data pointers the plan holds
+    std::vector<LevelDesc> hdescs;          // host copy of its level descriptors (rebasing)
     PlanInfo info;
     char *d = nullptr;
     size_t cap = 0;
@@ -953,15 +955,47 @@ int run_plan(hog_ctx *ctx, PlanBuilder &pb, cudaStream_t stream) {
 // Device-resident plans of recent detection batches, keyed by the batch's
 // frames (pointer, size, pitch) and frame numbering: a repeated batch (a
 // ring of camera buffers, a benchmark loop) skips plan building and upload.
+// Point a cached plan at other frames of the same shape: level 0 reads the
+// frame (img), and the first 5/6 step or a direct-to-size level resamples it
+// (src).  The patched descriptors go to the device on the stream, after the
+// plan's earlier uses; its graphs read them from there and stay valid.
+int rebase_plan(hog_ctx *ctx, CachedPlan &cp, const std::vector<const uint8_t *> &ptrs,
+                int frame_base, cudaStream_t stream) {
+    for (LevelDesc &d : cp.hdescs) {
+        const int i = d.frame - frame_base;
+        if (i < 0 || i >= (int)ptrs.size()) continue;
+        if (d.img == cp.fptr[i]) d.img = ptrs[i];
+        if (d.src == cp.fptr[i]) d.src = ptrs[i];
+    }
+    const size_t bytes = cp.hdescs.size() * sizeof(LevelDesc);
+    if (bytes) {
+        int rc = ensure_plan_capacity(ctx, cp.info.L.descs + bytes);
+        if (rc) return rc;
+        CUDA_TRY(ctx, cudaEventSynchronize(ctx->plan_done));   // the staging buffer is free
+        std::memcpy(ctx->h_plan + cp.info.L.descs, cp.hdescs.data(), bytes);
+        CUDA_TRY(ctx, cudaMemcpyAsync(cp.d + cp.info.L.descs, ctx->h_plan + cp.info.L.descs, bytes,
+                                      cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(ctx, cudaEventRecord(ctx->plan_done, stream));
+    }
+    cp.fptr = ptrs;
+    return HOG_OK;
+}
+
 int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, cudaStream_t stream,
                 const char **d_out, const PlanInfo **info_out, CachedPlan **entry = nullptr,
                 const hog_roi *rois = nullptr) {
+    // Signature of the batch's shape (frame sizes, pitches, the data
+    // pointers' alignment mod 16, regions); the pointers themselves are
+    // compared apart.  A plan of the same shape and other frames is rebased:
+    // only the level descriptors that point at a frame change.
     std::vector<uint64_t> sig;
+    std::vector<const uint8_t *> ptrs((size_t)nb);
     sig.reserve(2 + 2 * (size_t)nb + (rois ? 5 * (size_t)nb : 0));
     sig.push_back((uint64_t)nb | (rois ? (1ull << 63) : 0ull));
     sig.push_back((uint64_t)(uint32_t)frame_base);
     for (int i = 0; i < nb; i++) {
-        sig.push_back((uint64_t)(uintptr_t)frames[i].data);
+        ptrs[i] = frames[i].data;
+        sig.push_back((uint64_t)(uintptr_t)frames[i].data & 15u);
         sig.push_back(((uint64_t)(uint32_t)frames[i].w << 40) ^ ((uint64_t)(uint32_t)frames[i].h << 20) ^
                       (uint64_t)(uint32_t)frames[i].pitch);
         if (rois) {
@@ -974,13 +1008,28 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
     }
     ctx->plan_clock++;
     for (auto &cp : ctx->plans)
-        if (cp.d && cp.sig == sig) {
+        if (cp.d && cp.sig == sig && cp.fptr == ptrs) {
             cp.used = ctx->plan_clock;
             *d_out = cp.d;
             *info_out = &cp.info;
             if (entry) *entry = &cp;
             return HOG_OK;
         }
+    // no free cache entry: rebase the least recently used plan of this shape
+    if ((int)ctx->plans.size() >= ctx->plan_cache_max) {
+        CachedPlan *rb = nullptr;
+        for (auto &cp : ctx->plans)
+            if (cp.d && cp.sig == sig && (!rb || cp.used < rb->used)) rb = &cp;
+        if (rb) {
+            int rc = rebase_plan(ctx, *rb, ptrs, frame_base, stream);
+            if (rc) return rc;
+            rb->used = ctx->plan_clock;
+            *d_out = rb->d;
+            *info_out = &rb->info;
+            if (entry) *entry = rb;
+            return HOG_OK;
+        }
+    }
     PlanBuilder pb;
     for (int i = 0; i < nb; i++) {
         const hog_frame &f = frames[i];
@@ -1023,6 +1072,8 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
     int rc = upload_plan(ctx, pb, info, victim->d, stream);
     if (rc) { victim->sig.clear(); return rc; }
     victim->sig = std::move(sig);
+    victim->fptr = std::move(ptrs);
+    victim->hdescs = pb.descs;
     victim->info = info;
     victim->used = ctx->plan_clock;
     *d_out = victim->d;
@@ -1516,7 +1567,7 @@ int hog_detect(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det 
         if (rc) return rc;
     }
     return detect_device(ctx, frames, n_frames, 0, dets, det_cap, nullptr, counts,
-                         (cudaStream_t)stream_);
+                         (cudaStream_t)stream_, MODE_STAGED, true);
 }
 
 int hog_detect_batched(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
