@@ -225,8 +225,12 @@ def run_serving(hog, synth, W, seconds, warm, mode, lanes=4, max_batch=16, camer
     pool = {i: [synth.camera_frame(c, k) for k in range(8)] for i, c in enumerate(ids)}
     arr = synth.arrivals(n_cameras=8, seconds=seconds + warm)
     arr = [arr[c] for c in ids]
+    # lanes sized for the camera mix: half for 640x480 frames, half for
+    # 1280x1024 (each size is admitted to a lane of the smallest class that
+    # holds it)
     cfg = hog.default_server_config(max_batch=max_batch, max_lanes=lanes, queue_cap=256,
-                                    batched_mode=mode)
+                                    batched_mode=mode,
+                                    classes=[(640, 480, lanes // 2), (1280, 1024, lanes - lanes // 2)])
     srv = hog.Server(W, cfg, max_w=1280, max_h=1024)
     dropped = [0] * nc
     accepted = [0] * nc
@@ -283,6 +287,9 @@ def run_serving(hog, synth, W, seconds, warm, mode, lanes=4, max_batch=16, camer
         "queue_p50_ms": pct(queue_ms, 50), "queue_p99_ms": pct(queue_ms, 99),
         "device_p50_ms": pct(dev_ms, 50), "device_p99_ms": pct(dev_ms, 99),
         "lanes": st["lanes"], "lane_mb": st["lane_bytes"] / 2**20,
+        "lane_classes": [{"frame": "%dx%d" % wh, "lanes": st["class_lanes"][k],
+                          "lane_mb": st["class_bytes"][k] / 2**20, "frames": st["class_frames"][k]}
+                         for k, wh in enumerate([(640, 480), (1280, 1024)])],
         "mean_batch": st["batched_frames"] / max(st["batches"], 1),
         "max_inflight": st["max_inflight"], "batches": st["batches"],
         "mode": "fused" if mode == 1 else "per-stage",

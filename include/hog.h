@@ -450,6 +450,8 @@ int hog_stage_stats(hog_ctx *ctx, hog_stage_stat *out, int32_t cap, int32_t rese
  * per camera) ----------------------------------------------------------- */
 typedef struct hog_server hog_server;   /* opaque, owned by the library */
 
+#define HOG_SERVER_CLASSES 4   /* lane size classes of a server */
+
 /* Server configuration.  hog_default_server_config() fills the defaults. */
 typedef struct {
     int32_t max_batch;    /* frames per device batch, 1..1024 (default 8)     */
@@ -461,6 +463,18 @@ typedef struct {
     int64_t mem_reserve;  /* lanes after the first are created only while
                              free device memory stays above this many bytes
                              (default 1 GiB)                                 */
+    /* Lane size classes (the lanes' arenas are sized for the camera mix
+     * instead of all for max_w x max_h): class k holds frames up to
+     * class_w[k] x class_h[k] and gets up to class_lanes[k] lanes.  All
+     * class_lanes zero (default): one class of max_w x max_h with max_lanes
+     * lanes.  Otherwise some class must hold max_w x max_h, the lanes of all
+     * classes number at most 16, and max_lanes is not used.  A waiting frame
+     * is admitted to a free lane of the smallest class that holds it; a lane
+     * of a larger class takes it only while no waiting frame needs that
+     * class, so small frames keep flowing while large ones wait. */
+    int32_t class_w[HOG_SERVER_CLASSES];
+    int32_t class_h[HOG_SERVER_CLASSES];
+    int32_t class_lanes[HOG_SERVER_CLASSES];
 } hog_server_config;
 
 /* One finished request, returned by hog_server_poll. */
@@ -470,7 +484,7 @@ typedef struct {
     int32_t  status;      /* HOG_OK or the HOG_E* code of its batch           */
     int32_t  count;       /* kept detections (exact)                          */
     int32_t  stored;      /* of which copied into the poll's dets buffer      */
-    int32_t  pad;
+    int32_t  lane_class;  /* size class of the lane that ran it              */
     double   latency_ms;  /* submit -> result ready (host clock)              */
     double   queue_ms;    /* submit -> dispatched to a lane                   */
     double   device_ms;   /* its batch on the lane's stream: copy-in ..
@@ -487,14 +501,21 @@ typedef struct {
     int64_t lanes;          /* lanes created (admission by free memory)       */
     int64_t lane_bytes;     /* device bytes the first lane took               */
     int64_t pending;        /* frames waiting for a lane right now            */
+    int64_t class_lanes[HOG_SERVER_CLASSES];   /* lanes created per class      */
+    int64_t class_bytes[HOG_SERVER_CLASSES];   /* device bytes of one lane of
+                                                  each class (0: none made)    */
+    int64_t class_frames[HOG_SERVER_CLASSES];  /* frames each class served    */
 } hog_server_stats;
 
 void hog_default_server_config(hog_server_config *c);
 
 /* Create a server for frames up to p->max_w x p->max_h (p->max_batch is
  * replaced by c->max_batch) with F filters (host float [F][10][10][31]).
- * Starts one worker thread.  HOG_EINVAL for a bad configuration (message in
- * hog_server_last_error(NULL)), HOG_ENOMEM if not even one lane fits. */
+ * Lanes are made class by class, smallest first; each lane after the very
+ * first only while free device memory minus the measured size of a lane of
+ * its class stays above c->mem_reserve.  Starts one worker thread.
+ * HOG_EINVAL for a bad configuration (message in hog_server_last_error
+ * (NULL)), HOG_ENOMEM if a class that must serve some frames gets no lane. */
 int hog_server_create(const hog_params *p, const float *filters_host, int32_t n_filters,
                       const hog_server_config *c, hog_server **out);
 

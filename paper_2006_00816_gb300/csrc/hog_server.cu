@@ -15,9 +15,13 @@
 //   - completion is signalled by a host callback on the lane's stream; the
 //     worker moves the lane's results to the completed queue, frees the
 //     slots, and the lane takes the next batch;
-//   - lanes are created at start-up only while free device memory stays
-//     above mem_reserve bytes (admission by memory): the number of frames
-//     in flight is what the device can hold.
+//   - lanes belong to size classes (arenas sized for the camera mix, not
+//     all for the largest frame) and are created at start-up only while
+//     free device memory stays above mem_reserve bytes (admission by
+//     memory): the number of frames in flight is what the device can hold;
+//   - a waiting frame is admitted to a free lane of the smallest class that
+//     holds it; a lane of a larger class takes it only while no waiting frame
+//     needs that class, so small frames are admitted while large ones wait.
 // Each result is bit-identical to hog_detect on the same frame alone: the
 // kernels are deterministic and frames of a batch never interact.
 #include <algorithm>
@@ -60,6 +64,7 @@ struct Lane {
     uint8_t *d_frames = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int index = 0;
+    int cls = 0, cw = 0, ch = 0;   // size class and the largest frame it holds
     std::vector<Request> batch;
     bool busy = false;
     volatile bool completed = false;
@@ -85,6 +90,8 @@ struct hog_server {
     hog_server_stats st = {};
     std::string err;
     int mode = 0;
+    int ncls = 1;
+    int cls_w[HOG_SERVER_CLASSES] = {}, cls_h[HOG_SERVER_CLASSES] = {};   // by increasing area
 };
 
 namespace {
@@ -128,6 +135,7 @@ void harvest(hog_server *s, Lane *ln) {
         r.r.device_ms = dev_ms;
         r.r.batch = (int32_t)ln->batch.size();
         r.r.lane = ln->index;
+        r.r.lane_class = ln->cls;
         if (stored > 0) {
             r.dets.assign(dets + off, dets + off + stored);
             for (auto &d : r.dets) d.frame = 0;
@@ -157,7 +165,7 @@ void dispatch(hog_server *s, Lane *ln, std::vector<Request> &&batch) {
     for (int k = 0; k < nb; k++) {
         Request &q = batch[k];
         q.t_dispatch = t;
-        uint8_t *dst = ln->d_frames + (size_t)k * s->fbytes;
+        uint8_t *dst = ln->d_frames + (size_t)k * ln->cw * ln->ch;
         const uint8_t *src = s->h_slots + (size_t)q.slot * s->fbytes;
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(dst, src, (size_t)q.w * q.h, cudaMemcpyHostToDevice, ln->stream);
@@ -196,6 +204,14 @@ void dispatch(hog_server *s, Lane *ln, std::vector<Request> &&batch) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->st.batches++;
     s->st.batched_frames += nb;
+    s->st.class_frames[ln->cls] += nb;
+}
+
+// Smallest class that holds a w x h frame (ncls if none).
+int class_of(const hog_server *s, int w, int h) {
+    for (int k = 0; k < s->ncls; k++)
+        if (w <= s->cls_w[k] && h <= s->cls_h[k]) return k;
+    return s->ncls;
 }
 
 void worker_loop(hog_server *s) {
@@ -208,17 +224,37 @@ void worker_loop(hog_server *s) {
                 harvest(s, ln);
                 lk.lock();
             }
-        // a free lane takes what is waiting
+        // admission: the waiting frame sizes in order of their oldest
+        // request; the first size with a free lane it may use forms a batch.
+        // A size uses the smallest free lane class that holds it, and a
+        // larger class only while no waiting frame needs that class.
         Lane *free_lane = nullptr;
-        for (Lane *ln : s->lanes)
-            if (!ln->busy) { free_lane = ln; break; }
-        if (free_lane && !s->pending.empty()) {
-            // the oldest request and the waiting requests of its frame size,
-            // in arrival order: one size per batch, so a lane's cached plans
-            // and graphs stay few (size x count) and small frames never wait
-            // for a large frame's suppression in the same batch
+        int bw = 0, bh = 0;
+        if (!s->pending.empty()) {
+            bool wanted[HOG_SERVER_CLASSES + 1] = {};
+            for (const Request &q : s->pending) wanted[class_of(s, q.w, q.h)] = true;
+            std::vector<std::pair<int, int>> sizes;
+            for (const Request &q : s->pending) {
+                bool seen = false;
+                for (auto &z : sizes) seen |= z.first == q.w && z.second == q.h;
+                if (!seen) sizes.push_back({q.w, q.h});
+            }
+            for (auto &z : sizes) {
+                const int c0 = class_of(s, z.first, z.second);
+                for (int c = c0; c < s->ncls && !free_lane; c++) {
+                    if (c > c0 && wanted[c]) break;   // that class is needed by its own frames
+                    for (Lane *ln : s->lanes)
+                        if (!ln->busy && ln->cls == c) { free_lane = ln; break; }
+                }
+                if (free_lane) { bw = z.first; bh = z.second; break; }
+            }
+        }
+        if (free_lane) {
+            // the waiting requests of that frame size, in arrival order: one
+            // size per batch, so a lane's cached plans and graphs stay few
+            // (size x count) and small frames never wait for a large frame's
+            // suppression in the same batch
             std::vector<Request> batch;
-            const int bw = s->pending.front().w, bh = s->pending.front().h;
             for (auto it = s->pending.begin();
                  it != s->pending.end() && (int)batch.size() < s->cfg.max_batch;) {
                 if (it->w == bw && it->h == bh) {
@@ -246,7 +282,17 @@ void worker_loop(hog_server *s) {
 int validate(const hog_server_config *c, std::string &why) {
     if (!c) { why = "config is NULL"; return HOG_EINVAL; }
     if (c->max_batch < 1 || c->max_batch > 1024) { why = "max_batch out of 1..1024"; return HOG_EINVAL; }
-    if (c->max_lanes < 1 || c->max_lanes > 16) { why = "max_lanes out of 1..16"; return HOG_EINVAL; }
+    int classed = 0;
+    for (int k = 0; k < HOG_SERVER_CLASSES; k++) {
+        if (c->class_lanes[k] < 0) { why = "class_lanes < 0"; return HOG_EINVAL; }
+        classed += c->class_lanes[k];
+        if (c->class_lanes[k] > 0 && (c->class_w[k] < 1 || c->class_h[k] < 1)) {
+            why = "a lane class needs a frame size";
+            return HOG_EINVAL;
+        }
+    }
+    if (classed > 16) { why = "more than 16 lanes over the classes"; return HOG_EINVAL; }
+    if (!classed && (c->max_lanes < 1 || c->max_lanes > 16)) { why = "max_lanes out of 1..16"; return HOG_EINVAL; }
     if (c->queue_cap < c->max_batch) { why = "queue_cap < max_batch"; return HOG_EINVAL; }
     if (c->batched_mode < -1 || c->batched_mode > 1) { why = "batched_mode out of -1..1"; return HOG_EINVAL; }
     if (c->mem_reserve < 0) { why = "mem_reserve < 0"; return HOG_EINVAL; }
@@ -287,6 +333,7 @@ void hog_default_server_config(hog_server_config *c) {
     c->queue_cap = 64;
     c->batched_mode = -1;
     c->mem_reserve = (int64_t)1 << 30;
+    for (int k = 0; k < HOG_SERVER_CLASSES; k++) c->class_w[k] = c->class_h[k] = c->class_lanes[k] = 0;
 }
 
 int hog_server_create(const hog_params *p, const float *filters_host, int32_t n_filters,
@@ -301,40 +348,83 @@ int hog_server_create(const hog_params *p, const float *filters_host, int32_t n_
     s->p = *p;
     s->p.max_batch = cfg->max_batch;
     s->fbytes = (size_t)p->max_w * p->max_h;
-    for (int l = 0; l < cfg->max_lanes; l++) {
-        size_t free0 = 0, total = 0;
-        cudaMemGetInfo(&free0, &total);
-        if (l > 0 && (int64_t)free0 - (int64_t)s->st.lane_bytes < cfg->mem_reserve) break;
-        Lane *ln = new Lane();
-        ln->srv = s;
-        int rc = hog_create(&s->p, filters_host, n_filters, &ln->ctx);
-        if (rc) {
-            g_server_error = hog_last_error(nullptr);
-            delete ln;
-            if (l == 0) { destroy_server(s); return rc; }
-            break;
+    // lane classes by increasing area (one class of the largest frame when
+    // none is configured); some class must hold p->max_w x p->max_h
+    struct Cls { int w, h, lanes; };
+    std::vector<Cls> cls;
+    for (int k = 0; k < HOG_SERVER_CLASSES; k++)
+        if (cfg->class_lanes[k] > 0)
+            cls.push_back({std::min(cfg->class_w[k], p->max_w), std::min(cfg->class_h[k], p->max_h),
+                           cfg->class_lanes[k]});
+    if (cls.empty()) cls.push_back({p->max_w, p->max_h, cfg->max_lanes});
+    std::stable_sort(cls.begin(), cls.end(),
+                     [](const Cls &a, const Cls &b) { return (int64_t)a.w * a.h < (int64_t)b.w * b.h; });
+    bool covers = false;
+    for (const Cls &c : cls) covers |= c.w >= p->max_w && c.h >= p->max_h;
+    if (!covers) {
+        g_server_error = "no lane class holds max_w x max_h";
+        delete s;
+        return HOG_EINVAL;
+    }
+    s->ncls = (int)cls.size();
+    for (int k = 0; k < s->ncls; k++) { s->cls_w[k] = cls[k].w; s->cls_h[k] = cls[k].h; }
+    int index = 0;
+    for (int k = 0; k < s->ncls; k++) {
+        for (int j = 0; j < cls[k].lanes; j++) {
+            size_t free0 = 0, total = 0;
+            cudaMemGetInfo(&free0, &total);
+            // each lane after the very first: only while free memory minus the
+            // measured size of a lane of its class stays above the reserve
+            // (a class's first lane is estimated by the largest class measured)
+            int64_t est = s->st.class_bytes[k];
+            for (int m = 0; m < k && !est; m++) est = std::max(est, s->st.class_bytes[m]);
+            if (index > 0 && (int64_t)free0 - est < cfg->mem_reserve) break;
+            Lane *ln = new Lane();
+            ln->srv = s;
+            hog_params lp = s->p;
+            lp.max_w = cls[k].w;
+            lp.max_h = cls[k].h;
+            int rc = hog_create(&lp, filters_host, n_filters, &ln->ctx);
+            if (rc) {
+                g_server_error = hog_last_error(nullptr);
+                delete ln;
+                if (index == 0) { destroy_server(s); return rc; }
+                break;
+            }
+            ctx_set_plan_cache(ln->ctx, 64);
+            if (cfg->batched_mode >= 0) hog_set_batched_mode(ln->ctx, cfg->batched_mode);
+            ln->index = index;
+            ln->cls = k;
+            ln->cw = cls[k].w;
+            ln->ch = cls[k].h;
+            const size_t fb = (size_t)cls[k].w * cls[k].h;
+            if (cudaStreamCreateWithFlags(&ln->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreate(&ln->ev0) != cudaSuccess || cudaEventCreate(&ln->ev1) != cudaSuccess ||
+                cudaMalloc(&ln->d_frames, fb * cfg->max_batch) != cudaSuccess) {
+                cudaGetLastError();
+                hog_destroy(ln->ctx);
+                if (ln->stream) cudaStreamDestroy(ln->stream);
+                if (ln->ev0) cudaEventDestroy(ln->ev0);
+                if (ln->ev1) cudaEventDestroy(ln->ev1);
+                delete ln;
+                if (index == 0) { g_server_error = "lane allocation failed"; destroy_server(s); return HOG_ENOMEM; }
+                break;
+            }
+            s->lanes.push_back(ln);
+            index++;
+            s->st.class_lanes[k]++;
+            if (!s->st.class_bytes[k]) {
+                size_t free1 = 0;
+                cudaMemGetInfo(&free1, &total);
+                s->st.class_bytes[k] = free0 > free1 ? (int64_t)(free0 - free1) : 0;
+                if (index == 1) s->st.lane_bytes = s->st.class_bytes[k];
+            }
         }
-        ctx_set_plan_cache(ln->ctx, 64);
-        if (cfg->batched_mode >= 0) hog_set_batched_mode(ln->ctx, cfg->batched_mode);
-        ln->index = l;
-        if (cudaStreamCreateWithFlags(&ln->stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreate(&ln->ev0) != cudaSuccess || cudaEventCreate(&ln->ev1) != cudaSuccess ||
-            cudaMalloc(&ln->d_frames, s->fbytes * cfg->max_batch) != cudaSuccess) {
-            cudaGetLastError();
-            hog_destroy(ln->ctx);
-            if (ln->stream) cudaStreamDestroy(ln->stream);
-            if (ln->ev0) cudaEventDestroy(ln->ev0);
-            if (ln->ev1) cudaEventDestroy(ln->ev1);
-            delete ln;
-            if (l == 0) { g_server_error = "lane allocation failed"; destroy_server(s); return HOG_ENOMEM; }
-            break;
-        }
-        s->lanes.push_back(ln);
-        if (l == 0) {
-            size_t free1 = 0;
-            cudaMemGetInfo(&free1, &total);
-            s->st.lane_bytes = free0 > free1 ? (int64_t)(free0 - free1) : 0;
-        }
+    }
+    if (!s->st.class_lanes[s->ncls - 1]) {
+        g_server_error = "no lane of the largest class fits in device memory";
+        destroy_server(s);
+        return HOG_ENOMEM;
     }
     s->st.lanes = (int64_t)s->lanes.size();
     s->mode = ctx_batched_mode(s->lanes[0]->ctx);

@@ -86,14 +86,19 @@ class Level(C.Structure):
                 ("offset", C.c_int64)]
 
 
+SERVER_CLASSES = 4
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("max_batch", C.c_int32), ("max_lanes", C.c_int32), ("queue_cap", C.c_int32),
-                ("batched_mode", C.c_int32), ("mem_reserve", C.c_int64)]
+                ("batched_mode", C.c_int32), ("mem_reserve", C.c_int64),
+                ("class_w", C.c_int32 * SERVER_CLASSES), ("class_h", C.c_int32 * SERVER_CLASSES),
+                ("class_lanes", C.c_int32 * SERVER_CLASSES)]
 
 
 class Result(C.Structure):
     _fields_ = [("id", C.c_uint64), ("tag", C.c_int64), ("status", C.c_int32),
-                ("count", C.c_int32), ("stored", C.c_int32), ("pad", C.c_int32),
+                ("count", C.c_int32), ("stored", C.c_int32), ("lane_class", C.c_int32),
                 ("latency_ms", C.c_double), ("queue_ms", C.c_double),
                 ("device_ms", C.c_double), ("batch", C.c_int32), ("lane", C.c_int32)]
 
@@ -101,7 +106,8 @@ class Result(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("submitted", "completed", "failed", "rejected", "batches",
                                          "batched_frames", "max_inflight", "lanes", "lane_bytes",
-                                         "pending")]
+                                         "pending")] + [
+        (k, C.c_int64 * SERVER_CLASSES) for k in ("class_lanes", "class_bytes", "class_frames")]
 
 
 DET_DTYPE = np.dtype([("frame", "<i4"), ("level", "<i4"), ("filter", "<i4"), ("u", "<i4"),
@@ -541,13 +547,17 @@ class Detector:
             n, det_cap, allow_capacity, out)
 
 
-def default_server_config(**kw) -> ServerConfig:
+def default_server_config(classes=None, **kw) -> ServerConfig:
+    """hog_server_config with the defaults, fields set from kw; classes: a
+    list of (w, h, lanes) lane size classes (at most SERVER_CLASSES)."""
     c = ServerConfig()
     _lib.hog_default_server_config(C.byref(c))
     for k, v in kw.items():
         if not hasattr(c, k):
             raise AttributeError(k)
         setattr(c, k, v)
+    for k, (w, h, n) in enumerate(classes or []):
+        c.class_w[k], c.class_h[k], c.class_lanes[k] = int(w), int(h), int(n)
     return c
 
 
@@ -674,14 +684,18 @@ class Server:
             out.append(dict(id=r.id, tag=r.tag, status=r.status, count=r.count,
                             latency_ms=r.latency_ms, queue_ms=r.queue_ms,
                             device_ms=r.device_ms, batch=r.batch, lane=r.lane,
-                            dets=dets[off:off + r.stored].copy()))
+                            lane_class=r.lane_class, dets=dets[off:off + r.stored].copy()))
             off += r.stored
         return out
 
     def stats(self):
         st = ServerStats()
         _lib.hog_server_get_stats(self._h, C.byref(st))
-        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+        out = {}
+        for k, _ in ServerStats._fields_:
+            v = getattr(st, k)
+            out[k] = list(v) if k.startswith("class_") else v
+        return out
 
 
 def hinge_loss(detector, images, labels, weights, recompute=False):

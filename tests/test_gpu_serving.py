@@ -127,3 +127,51 @@ def test_poll_splits_boxes_by_capacity(H, S, streams, alone):
         assert r["count"] == len(ref[r["tag"]])
         n = min(3, r["count"])
         assert len(r["dets"]) == n and r["dets"].tobytes() == ref[r["tag"]][:n].tobytes()
+
+
+def test_lane_classes_admit_small_frames_while_large_ones_wait(H, S, alone, streams):
+    """Lanes sized for the camera mix: two lanes for frames up to 640x480
+    and one for 1280x1024.  A burst of large frames queues for the one large
+    lane while small frames submitted after them are admitted to the small
+    lanes and finish first; no large frame runs on a small lane, the small
+    lanes hold less device memory than the large one, and every result is
+    the frame's hog_detect result alone."""
+    cfg = H.default_server_config(max_batch=1, queue_cap=64, mem_reserve=0,
+                                  classes=[(640, 480, 2), (1280, 1024, 1)])
+    big = [(c, k) for c in (4, 5, 6, 7) for k in range(3)]      # 1280x1024 cameras
+    small = [(c, k) for c in (1, 2, 3) for k in range(4)]       # 640x480 cameras
+    with H.Server(S.filters(5), config=cfg, max_w=1280, max_h=1024) as srv:
+        st = srv.stats()
+        assert st["class_lanes"][:2] == [2, 1] and st["lanes"] == 3
+        assert 0 < st["class_bytes"][0] < st["class_bytes"][1]
+        order = []
+        for c, k in big + small:                 # all large frames first
+            assert srv.submit(streams[c][k], tag=_tag(c, k)) is not None
+        got = {}
+        t0 = time.time()
+        while len(got) < len(big) + len(small) and time.time() - t0 < 60:
+            for r in srv.poll(cap=16, wait_us=20000):
+                got[r["tag"]] = r
+                order.append(r["tag"])
+        assert len(got) == len(big) + len(small)
+        for c, k in big + small:
+            r = got[_tag(c, k)]
+            assert r["status"] == 0
+            assert r["lane_class"] == (1 if (c, k) in big else 0)
+            want = alone[(c, k)]
+            assert r["count"] == len(want) and r["dets"].tobytes() == want.tobytes()
+        # small frames were admitted while large ones waited for their lane
+        last_big = max(order.index(_tag(c, k)) for c, k in big)
+        first_small = min(order.index(_tag(c, k)) for c, k in small)
+        assert first_small < last_big
+        st = srv.stats()
+        assert st["class_frames"][:2] == [len(small), len(big)]
+
+
+def test_lane_classes_validation(H, S):
+    bad = H.default_server_config(classes=[(640, 480, 2)])     # nothing holds 1280x1024
+    with pytest.raises(H.HogError):
+        H.Server(S.filters(5), config=bad, max_w=1280, max_h=1024)
+    bad = H.default_server_config(classes=[(640, 480, 9), (1280, 1024, 9)])   # 18 lanes
+    with pytest.raises(H.HogError):
+        H.Server(S.filters(5), config=bad, max_w=1280, max_h=1024)
