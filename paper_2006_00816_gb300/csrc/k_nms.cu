@@ -123,20 +123,25 @@ __global__ void __launch_bounds__(256) pack_kernel(const hog_det *__restrict__ d
     __syncthreads();
     const int off = off_s;
     const int n = min(counts[i], per_frame);
-    // copy as 8-byte words (hog_det is 56 bytes = 7 words)
+    // copy as 8-byte words (hog_det is 56 bytes = 7 words); the gridDim.y
+    // CTAs of a frame split its words (the output may be host memory, where
+    // one CTA's stores alone would be latency-bound)
     const unsigned long long *src =
         reinterpret_cast<const unsigned long long *>(dets + (size_t)i * per_frame);
     unsigned long long *dst = reinterpret_cast<unsigned long long *>(out + off);
     const int nw = max(0, min(n, out_cap - off)) * 7;
-    for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = src[k];
-    if (threadIdx.x == 0) counts_out[i] = counts[i];
+    const int per = (nw + gridDim.y - 1) / gridDim.y;
+    const int k0 = blockIdx.y * per, k1 = min(nw, k0 + per);
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) dst[k] = src[k];
+    if (threadIdx.x == 0 && blockIdx.y == 0) counts_out[i] = counts[i];
 }
 
 cudaError_t launch_pack(const hog_det *dets, int per_frame, const int32_t *counts, int nframes,
                         hog_det *out, int out_cap, int32_t *counts_out, cudaStream_t stream) {
     if (nframes <= 0) return cudaSuccess;
-    pack_kernel<<<nframes, 256, 0, stream>>>(dets, per_frame, counts, nframes, out, out_cap,
-                                             counts_out);
+    const int split = std::max(1, std::min(16, 64 / nframes));   // CTAs per frame for small batches
+    pack_kernel<<<dim3(nframes, split), 256, 0, stream>>>(dets, per_frame, counts, nframes, out, out_cap,
+                                                          counts_out);
     return cudaGetLastError();
 }
 
@@ -242,11 +247,12 @@ __host__ __device__ constexpr size_t nms_cluster_ws_bytes(int npos, int c, int m
 __host__ __device__ constexpr int nms_rep_slice(int npos, int c) {
     return ((npos + c - 1) / c + 31) / 32 * 32;
 }
-// Shared-memory list stride (halves): 112 bytes, so that the 16-byte loads
-// of eight consecutive positions' lists fall on distinct banks.
-constexpr int NMS_LIST_STRIDE = 56;
-__host__ __device__ constexpr size_t nms_rep_ws_bytes(int npos, int c) {
-    return (size_t)nms_rep_slice(npos, c) * (c + 6 + 2 * NMS_LIST_STRIDE) + nms_rep_slice(npos, c) / 16 +
+// Cached list lengths of the replicated form: 48 neighbours in a 112-byte
+// row (the 16-byte loads of eight consecutive positions' lists fall on
+// distinct banks), or 16 in a 32-byte row for frames with more positions.
+__host__ __device__ constexpr int nms_rep_stride(int list) { return list == 48 ? 56 : list; }
+__host__ __device__ constexpr size_t nms_rep_ws_bytes(int npos, int c, int list) {
+    return (size_t)nms_rep_slice(npos, c) * (c + 6 + 2 * nms_rep_stride(list)) + nms_rep_slice(npos, c) / 16 +
            nms_rep_slice(npos, c) / 8 + 64;
 }
 
@@ -573,8 +579,27 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_kernel(const FrameDesc 
 // newer slice while its CTA still reads it: states only move from undecided
 // to decided, so a newer value is as good as the old one.  The rounds reach
 // the same fixed point as the one-CTA form.
+// Slot of set bit n (0-based) of a 192-bit above-mask, 255 if there are n or fewer.
+__device__ __forceinline__ int nth_set_slot(const uint32_t *mk, int n) {
+    for (int w = 0; w < NMS_MASK_WORDS; w++) {
+        uint32_t b = __ldg(mk + w);
+        const int c = __popc(b);
+        if (n < c) {
+            for (int j = 0; j < n; j++) b &= b - 1;
+            return w * 32 + __ffs(b) - 1;
+        }
+        n -= c;
+    }
+    return 255;
+}
+
+// LIST: cached higher-ranked neighbours per position (48 or 16); PPT: owned
+// positions per thread (the slice holds at most PPT x NT positions).
+template <int LIST, int PPT>
 __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_rep_kernel(const FrameDesc *__restrict__ frames,
                                                                     int *flags) {
+    static_assert(LIST == 48 || LIST == 16, "list length");
+    constexpr int LSTR = nms_rep_stride(LIST);
     extern __shared__ __align__(16) unsigned char nsm[];
     __shared__ int sh[NMS_NT / 32 + 4];
     __shared__ int s_cnt[2][NMS_MAX_CLUSTER];
@@ -590,10 +615,10 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_rep_kernel(const FrameD
     uint8_t *st = nsm;                                                          // [C P] all states
     uint8_t *resume = nsm + (size_t)C * P;                                      // [P]
     uint8_t *lcnt = resume + P, *lovf = lcnt + P;                               // [P], [P]
-    uint16_t *alist = reinterpret_cast<uint16_t *>(lovf + P + 3 * (size_t)P);   // [P][56], 16-B aligned
+    uint16_t *alist = reinterpret_cast<uint16_t *>(lovf + P + 3 * (size_t)P);   // [P][LSTR], 16-B aligned
     // suppression bits of the owned positions, set (remote atomic OR) by a
     // kept neighbour in any CTA: such a position is suppressed without a check
-    volatile uint32_t *supp = reinterpret_cast<volatile uint32_t *>(alist + (size_t)P * NMS_LIST_STRIDE);  // [P / 32]
+    volatile uint32_t *supp = reinterpret_cast<volatile uint32_t *>(alist + (size_t)P * LSTR);  // [P / 32]
     uint8_t *dirty = reinterpret_cast<uint8_t *>(const_cast<uint32_t *>(supp) + P / 32);              // [P / 16]
     const int32_t *__restrict__ nbr_t = fd.nbr_t;
     const int base = rank * P;      // owned slice of the copy, 16-byte aligned (lo: clamped to npos)
@@ -623,9 +648,9 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_rep_kernel(const FrameD
         }
         reinterpret_cast<uint4 *>(st)[c0] = v;
     }
-    // the owned candidates' lists, as the pre-pass wrote them (eight loads
-    // in flight per thread)
-    constexpr int LW = NMS_LIST / 2;
+    // the owned candidates' lists, as the pre-pass wrote them (its first
+    // LIST entries; eight loads in flight per thread)
+    constexpr int LW = LIST / 2;
     for (int k0 = t; k0 < nmine * LW; k0 += 8 * NMS_NT) {
         uint32_t v[8];
 #pragma unroll
@@ -636,13 +661,16 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_rep_kernel(const FrameD
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const int k = k0 + j * NMS_NT, i = k / LW;
-            if (k < nmine * LW) reinterpret_cast<uint32_t *>(alist)[i * (NMS_LIST_STRIDE / 2) + (k - i * LW)] = v[j];
+            if (k < nmine * LW) reinterpret_cast<uint32_t *>(alist)[i * (LSTR / 2) + (k - i * LW)] = v[j];
         }
     }
     for (int i = t; i < nmine; i += NMS_NT) {
         const uint32_t c = __ldg(ws + (size_t)(lo + i) * NMS_WS_WORDS + 6);
-        const uint32_t o = __ldg(ws + (size_t)(lo + i) * NMS_WS_WORDS + 7);
-        lcnt[i] = (uint8_t)c;
+        uint32_t o = __ldg(ws + (size_t)(lo + i) * NMS_WS_WORDS + 7);
+        // a shorter cached list: the rest of the mask starts after its last entry
+        if (LIST < NMS_LIST && (c > (uint32_t)LIST || o != 255u))
+            o = (uint32_t)nth_set_slot(ws + (size_t)(lo + i) * NMS_WS_WORDS, LIST);
+        lcnt[i] = (uint8_t)(c < (uint32_t)LIST ? c : (uint32_t)LIST);
         lovf[i] = (uint8_t)o;
         resume[i] = 0;
     }
@@ -653,12 +681,16 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_rep_kernel(const FrameD
     int round = 0;
     for (; round <= npos; round++) {
         bool any = false;
-        int kept0 = -1, kept1 = -1;   // positions this thread keeps this round (P <= 2 NT)
-        for (int li = t; li < nmine; li += NMS_NT) {
+        int kept[PPT];   // positions this thread keeps this round
+#pragma unroll
+        for (int m = 0; m < PPT; m++) {
+            kept[m] = -1;
+            const int li = t + m * NMS_NT;
+            if (li >= nmine) continue;
             const int p = lo + li;
             if (st[p] != NMS_ALIVE) continue;
             const int n2 = lcnt[li];
-            const uint16_t *al = alist + (size_t)li * NMS_LIST_STRIDE;   // 16-byte aligned
+            const uint16_t *al = alist + (size_t)li * LSTR;   // 16-byte aligned
             bool dead = (supp[li >> 5] >> (li & 31)) & 1u, wait = false, prefix = true;
             const int r0 = resume[li];
             int settled = r0;
@@ -705,7 +737,7 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_rep_kernel(const FrameD
             if (dead || !wait) {
                 st[p] = dead ? NMS_DEAD : NMS_KEPT;
                 dirty[(p - base) >> 4] = 1;
-                if (!dead) (li < NMS_NT ? kept0 : kept1) = p;
+                if (!dead) kept[m] = p;
             } else {
                 any = true;
                 resume[li] = (uint8_t)settled;
@@ -714,8 +746,8 @@ __global__ void __launch_bounds__(NMS_NT, 1) nms_cluster_rep_kernel(const FrameD
         // each kept candidate marks its still-undecided neighbours in their
         // owners' suppression bits, the warp's lanes splitting the slots
 #pragma unroll
-        for (int m = 0; m < 2; m++) {
-            const int kp = m ? kept1 : kept0;
+        for (int m = 0; m < PPT; m++) {
+            const int kp = kept[m];
             for (unsigned km = __ballot_sync(0xffffffffu, kp >= 0); km; km &= km - 1) {
                 const int pk = __shfl_sync(0xffffffffu, kp, __ffs(km) - 1);
                 int q[MAXN / 32];   // all six 32-slot chunks in flight (-1 past the list's end)
@@ -868,13 +900,14 @@ int nms_cluster_max(int *nsm) {
         g_nsm[dev] = n > 0 ? n : 1;
         g_cluster_max[dev] = 1;
         if (!cluster_attrs(nms_cluster_kernel<0>) || !cluster_attrs(nms_cluster_kernel<1>) ||
-            !cluster_attrs(nms_cluster_rep_kernel)) {
+            !cluster_attrs(nms_cluster_rep_kernel<48, 2>) || !cluster_attrs(nms_cluster_rep_kernel<16, 4>)) {
             cudaGetLastError();
             return cudaSuccess;
         }
         int m = largest_cluster(nms_cluster_kernel<0>);
         m = std::min(m, largest_cluster(nms_cluster_kernel<1>));
-        m = std::min(m, largest_cluster(nms_cluster_rep_kernel));
+        m = std::min(m, largest_cluster(nms_cluster_rep_kernel<48, 2>));
+        m = std::min(m, largest_cluster(nms_cluster_rep_kernel<16, 4>));
         g_cluster_max[dev] = m;
         return cudaSuccess;
     });
@@ -935,14 +968,22 @@ cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *
         cfg.numAttrs = 1;
         // with the above-masks and cached lists (16-bit positions) when they
         // fit in the CTAs' shared memory, else with the masks alone
-        const size_t ws2 = nms_rep_ws_bytes(max_npos, c), ws1 = nms_cluster_ws_bytes(max_npos, c, 1);
-        if (ws1 <= (size_t)NMS_SMEM_MAX || ws2 <= (size_t)NMS_SMEM_MAX) {
+        const size_t ws48 = nms_rep_ws_bytes(max_npos, c, 48), ws16 = nms_rep_ws_bytes(max_npos, c, 16);
+        const size_t ws1 = nms_cluster_ws_bytes(max_npos, c, 1);
+        const int P = nms_rep_slice(max_npos, c);
+        const bool rep48 = ws48 <= (size_t)NMS_SMEM_MAX && max_npos <= 65535 && P <= 2 * NMS_NT;
+        const bool rep16 = ws16 <= (size_t)NMS_SMEM_MAX && max_npos <= 65535 && P <= 4 * NMS_NT;
+        if (ws1 <= (size_t)NMS_SMEM_MAX || rep48 || rep16) {
             nms_above_kernel<<<dim3((max_npos + 7) / 8, nframes), 256, 0, stream>>>(frames);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
-            if (ws2 <= (size_t)NMS_SMEM_MAX && max_npos <= 65535 && nms_rep_slice(max_npos, c) <= 2 * NMS_NT) {
-                cfg.dynamicSmemBytes = ws2;
-                return cudaLaunchKernelEx(&cfg, nms_cluster_rep_kernel, frames, flags);
+            if (rep48) {
+                cfg.dynamicSmemBytes = ws48;
+                return cudaLaunchKernelEx(&cfg, nms_cluster_rep_kernel<48, 2>, frames, flags);
+            }
+            if (rep16) {
+                cfg.dynamicSmemBytes = ws16;
+                return cudaLaunchKernelEx(&cfg, nms_cluster_rep_kernel<16, 4>, frames, flags);
             }
             cfg.dynamicSmemBytes = ws1;
             return cudaLaunchKernelEx(&cfg, nms_cluster_kernel<1>, frames, flags);
