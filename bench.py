@@ -49,8 +49,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # correlation stage for one 250-frame 640x480 batch, per engine, from one ncu
 # capture (--set full, 250-frame batch); valid while k_corr_tc.cu is the
 # source captured (first 16 hex digits of its SHA-256); None: not captured
-CORR_TC_TRAFFIC_250 = {1: 479.547648e6 + 20.450816e6, 2: None}
-CORR_TC_SOURCE_SHA = "2b41c1116f1dad71"
+CORR_TC_TRAFFIC_250 = {1: 479.525888e6 + 20.467200e6, 2: None}
+CORR_TC_SOURCE_SHA = "f1485626afd8f16b"
 # Gradient + histogram work per pyramid pixel: central differences, the
 # magnitude, the orientation test and four bilinear votes, about 60 FLOP
 # (the paper's per-pixel steps counted as FP32 operations)
@@ -59,10 +59,11 @@ HIST_FLOP_PER_PX = 60
 # normalisers, 27 x 4 truncated products and their sums)
 FEAT_FLOP_PER_CELL = 300
 # DRAM bytes of hist_kernel per 250-frame 640x480 batch from one ncu capture
-# (--set full) of the source whose SHA-256 starts with HIST_SOURCE_SHA (the
-# stage code lives in hog_stages.cuh); None: not captured
-HIST_TRAFFIC_250 = 249.0e6 + 226.8e6
-HIST_SOURCE_SHA = None
+# (--set full) of the source whose SHA-256 starts with HIST_SOURCE_SHA: the
+# histogram stage's part of hog_stages.cuh (from its configuration to the
+# feature stage) and k_hist.cu; None: not captured
+HIST_TRAFFIC_250 = 248.913152e6 + 227.027712e6
+HIST_SOURCE_SHA = "fed70df76502fb6e"
 PAPER_CONTEXT = {"ms_per_frame": 0.333, "frames_per_s": 3003,
                  "hardware": "NVIDIA Titan X (Pascal), 16 frames/launch, incl. transfers"}
 
@@ -361,6 +362,19 @@ def _src_sha(*names):
     return h.hexdigest()[:16]
 
 
+def _hist_sha():
+    """Hash of the histogram stage's source: its part of hog_stages.cuh and
+    its launcher."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2006_00816_gb300", "csrc")
+    s = open(os.path.join(csrc, "hog_stages.cuh")).read()
+    seg = s[s.index("namespace hist_cfg {"):s.index("// Energy, block normalisation")]
+    h = hashlib.sha256()
+    h.update(seg.encode())
+    h.update(open(os.path.join(csrc, "k_hist.cu"), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_roofline(hog, stage, stats, stages, nfr, steps, peaks):
     """Roofline entry of one stage's kernel (per-stage mode): achieved =
     algorithmic work per launch / average launch time (CUDA events on the
@@ -380,7 +394,7 @@ def kernel_roofline(hog, stage, stats, stages, nfr, steps, peaks):
     if stage == "hist":
         flop = HIST_FLOP_PER_PX * px * frames_per_launch
         achieved = flop / (per_launch_ms / 1e3) / 1e12
-        same = HIST_SOURCE_SHA is not None and _src_sha("hog_stages.cuh", "k_hist.cu") == HIST_SOURCE_SHA
+        same = HIST_SOURCE_SHA is not None and _hist_sha() == HIST_SOURCE_SHA
         return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS,
                 "traffic": HIST_TRAFFIC_250 * frames_per_launch / 250 if same else None,
