@@ -278,17 +278,32 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
     // read.  xbase[r] = image column of staged byte 0 of staged row r.
     const int Xs = CELL * j0 - 5, Ys = CELL * i0 - 5;
     const int xa = max(Xs, 0), xb = min(Xs + CELL * bw + 2, d.w);
-    for (int idx = t; idx < py * nch; idx += NT) {
-        const int r = idx / nch, ci = idx - r * nch;
-        const int Y = Ys + r;
-        if (Y < 0 || Y >= d.h || xa >= xb) continue;
-        const uintptr_t rp = (uintptr_t)(d.img + (size_t)Y * d.pitch);
-        const uintptr_t c0 = (rp + (uintptr_t)xa) & ~(uintptr_t)15;
-        const uintptr_t a = c0 + 16 * (uintptr_t)ci;
-        if (ci == 0) xbase[r] = (int)((intptr_t)c0 - (intptr_t)rp);
-        if (a <= rp + (uintptr_t)(xb - 1)) cp_async16(srcS + r * srowb + 16 * ci, (const void *)a);
+    {
+        // idx = r nch + ci walks t, t + NT, ...: one division up front, then
+        // a carry from ci into r.  Every staged row gets its xbase (rows off
+        // the image take the alignment of the nearest image row and are
+        // never copied), so the row loop below may read any staged row.
+        const int q0 = NT / nch, rem0 = NT - q0 * nch;
+        int r = t / nch, ci = t - r * nch;
+        while (r < py) {
+            const int Y = Ys + r;
+            const int Yc = min(max(Y, 0), d.h - 1);
+            const uintptr_t rp = (uintptr_t)(d.img + (size_t)Yc * d.pitch);
+            const uintptr_t c0 = (rp + (uintptr_t)xa) & ~(uintptr_t)15;
+            const uintptr_t a = c0 + 16 * (uintptr_t)ci;
+            if (ci == 0) xbase[r] = (int)((intptr_t)c0 - (intptr_t)rp);
+            if (Y >= 0 && Y < d.h && xa < xb && a <= rp + (uintptr_t)(xb - 1))
+                cp_async16(srcS + r * srowb + 16 * ci, (const void *)a);
+            ci += rem0;
+            r += q0;
+            if (ci >= nch) {
+                ci -= nch;
+                r++;
+            }
+        }
     }
-    for (int k = t; k < PB * NT; k += NT) reinterpret_cast<float4 *>(part)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < PB; k++) reinterpret_cast<float4 *>(part)[k * NT + t] = make_float4(0.f, 0.f, 0.f, 0.f);
     cp_async_wait_all();
     __syncthreads();
 
@@ -300,7 +315,7 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
     // are zeroed); zero gradients vote 0 as well (adding +0 leaves the
     // non-negative partials unchanged).  Magnitude sqrt(s) of the exact
     // integer s = dx^2 + dy^2 by the hardware square root (sqrt.approx, a
-    // few ulp).
+    // few ulp; s is 0 or >= 1, so flushing subnormals changes nothing).
     const int by = t / bw, bx = t - by * bw;
     const int X0 = CELL * (j0 + bx) - 4, Y0 = CELL * (i0 + by) - 4;
     const bool active = t < bw * bh && i0 + by <= d.cy && j0 + bx <= d.cx;
@@ -312,58 +327,63 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         wx1v[ox] = ok ? tent16(ox) : 0.0f;
     }
     float2 *p0 = part + t;
-    // Word reads: where the level's rows are 8-byte aligned in memory (image
-    // base and pitch multiples of 8), byte X0 of every staged row lies at a
-    // shared address = 4 (mod 8).  A thread then reads its 10 middle-row
-    // bytes (X0-1 .. X0+8) inside two 8-byte words and its 8 upper and lower
-    // bytes as two 4-byte words each: 6 shared loads per pixel row instead
-    // of 26 byte loads, whose 8-byte lane stride put a warp's two block rows
-    // on the same banks.  Each byte becomes the float 2^23 + byte with one
-    // byte permute, so dx and dy are float subtractions (byte_f23).
+    // Row reads: each pixel row's three image rows are staged rows r-1, r,
+    // r+1, and each staged row is read once per block: as the floats
+    // 2^23 + byte of its 10 columns X0-1 .. X0+8 (one byte permute each,
+    // byte_f23), which serve as the lower row, the middle row and the upper
+    // row of three successive pixel rows.  dx and dy are then float
+    // subtractions.  Where the level's rows are 8-byte aligned in memory
+    // (image base and pitch multiples of 8), byte X0 of every staged row lies
+    // at a shared address = 4 (mod 8), so the 10 bytes come from two 8-byte
+    // loads; otherwise from 10 byte loads.
     const bool words = ((uintptr_t)d.img & 7) == 0 && (d.pitch & 7) == 0;
-#pragma unroll 1
-    for (int oy = 0; oy < 8; oy++) {
-        const int Y = Y0 + oy;
-        if (!active || Y < 1 || Y > ymax) continue;
-        const int r = Y - Ys;                       // staged row of Y
-        const uint8_t *up = srcS + (r - 1) * srowb - xbase[r - 1];
-        const uint8_t *mid = srcS + r * srowb - xbase[r];
-        const uint8_t *dn = srcS + (r + 1) * srowb - xbase[r + 1];
-        const float wy1 = tent16(oy), wy0 = tent16(oy + 8);   // to cell rows bi, bi-1
-        auto vote = [&](float dxf, float dyf, int ox) {
-            const uint32_t boff = orientation_bin_f<NT * sizeof(float2)>(dxf, dyf);   // bytes
-            const float sf = fmaf(dxf, dxf, dyf * dyf);       // dx^2 + dy^2, exact
-            float m;                                          // sqrt(sf); 0 for sf = 0
-            asm("sqrt.approx.f32 %0, %1;" : "=f"(m) : "f"(sf));
-            const float m0 = m * wy0, m1 = m * wy1;
-            float2 *pb = reinterpret_cast<float2 *>(reinterpret_cast<char *>(p0) + boff);
-            float2 a = pb[0], c = pb[PB * NT];
-            a.x = fmaf(m0, wx0v[ox], a.x);   // cell (bi-1, bj-1)
-            a.y = fmaf(m0, wx1v[ox], a.y);   // cell (bi-1, bj)
-            c.x = fmaf(m1, wx0v[ox], c.x);   // cell (bi,   bj-1)
-            c.y = fmaf(m1, wx1v[ox], c.y);   // cell (bi,   bj)
-            pb[0] = a;
-            pb[PB * NT] = c;
-        };
+    // Staged row r as the floats 2^23 + byte of columns X0-1 .. X0+8.
+    auto load_row = [&](int r, float (&f)[10]) {
+        const uint8_t *row = srcS + r * srowb - xbase[r];
         if (words) {
-            const uint2 ma = *reinterpret_cast<const uint2 *>(mid + X0 - 4);   // X0-4 .. X0+3
-            const uint2 mb = *reinterpret_cast<const uint2 *>(mid + X0 + 4);   // X0+4 .. X0+11
-            const uint32_t mw[4] = {ma.x, ma.y, mb.x, mb.y};
-            const uint32_t uw[2] = {*reinterpret_cast<const uint32_t *>(up + X0),
-                                    *reinterpret_cast<const uint32_t *>(up + X0 + 4)};
-            const uint32_t dw[2] = {*reinterpret_cast<const uint32_t *>(dn + X0),
-                                    *reinterpret_cast<const uint32_t *>(dn + X0 + 4)};
+            const uint2 lo = *reinterpret_cast<const uint2 *>(row + X0 - 4);   // X0-4 .. X0+3
+            const uint2 hi = *reinterpret_cast<const uint2 *>(row + X0 + 4);   // X0+4 .. X0+11
+            const uint32_t w4[4] = {lo.x, lo.y, hi.x, hi.y};
 #pragma unroll
-            for (int ox = 0; ox < 8; ox++) {
-                const int kr = ox + 5, kl = ox + 3;     // bytes X0+ox+1, X0+ox-1 of mw
-                vote(byte_f23(mw[kr >> 2], kr & 3) - byte_f23(mw[kl >> 2], kl & 3),
-                     byte_f23(dw[ox >> 2], ox & 3) - byte_f23(uw[ox >> 2], ox & 3), ox);
-            }
+            for (int k = 0; k < 10; k++) f[k] = byte_f23(w4[(k + 3) >> 2], (k + 3) & 3);
         } else {
 #pragma unroll
+            for (int k = 0; k < 10; k++) f[k] = __uint_as_float(0x4B000000u | row[X0 - 1 + k]);
+        }
+    };
+    if (active) {
+        // pixel row oy of the block is staged row r0 + oy; three rows of
+        // floats rotate through f (the loop is unrolled, so the rotation
+        // is register naming): up = f[oy % 3], mid, down the next two
+        const int r0 = CELL * by + 1;
+        float f[3][10];
+        load_row(r0 - 1, f[0]);
+        load_row(r0, f[1]);
+#pragma unroll
+        for (int oy = 0; oy < 8; oy++) {
+            float(&fu)[10] = f[oy % 3];
+            float(&fm)[10] = f[(oy + 1) % 3];
+            float(&fd)[10] = f[(oy + 2) % 3];
+            load_row(r0 + oy + 1, fd);
+            const int Y = Y0 + oy;
+            if (Y < 1 || Y > ymax) continue;
+            const float wy1 = tent16(oy), wy0 = tent16(oy + 8);   // to cell rows bi, bi-1
+#pragma unroll
             for (int ox = 0; ox < 8; ox++) {
-                const int X = X0 + ox;
-                vote((float)((int)mid[X + 1] - (int)mid[X - 1]), (float)((int)dn[X] - (int)up[X]), ox);
+                const float dxf = fm[ox + 2] - fm[ox], dyf = fd[ox + 1] - fu[ox + 1];
+                const uint32_t boff = orientation_bin_f<NT * sizeof(float2)>(dxf, dyf);   // bytes
+                const float sf = fmaf(dxf, dxf, dyf * dyf);       // dx^2 + dy^2, exact
+                float m;                                          // sqrt(sf); 0 for sf = 0
+                asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(m) : "f"(sf));
+                const float m0 = m * wy0, m1 = m * wy1;
+                float2 *pb = reinterpret_cast<float2 *>(reinterpret_cast<char *>(p0) + boff);
+                float2 a = pb[0], c = pb[PB * NT];
+                a.x = fmaf(m0, wx0v[ox], a.x);   // cell (bi-1, bj-1)
+                a.y = fmaf(m0, wx1v[ox], a.y);   // cell (bi-1, bj)
+                c.x = fmaf(m1, wx0v[ox], c.x);   // cell (bi,   bj-1)
+                c.y = fmaf(m1, wx1v[ox], c.y);   // cell (bi,   bj)
+                pb[0] = a;
+                pb[PB * NT] = c;
             }
         }
     }
@@ -391,13 +411,30 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
         }
     }
     __syncthreads();
-    const int ncol = min(tw, d.cx - j0);
-    for (int r = 0; r < th; r++) {
-        const int i = i0 + r;
-        if (i >= d.cy) break;
-        float *dst = d.hist + ((size_t)i * d.cx + j0) * NBIN;
-        const float *srcr = outS + r * tw * NBIN;
-        for (int k = t; k < ncol * NBIN; k += NT) dst[k] = srcr[k];
+    // the tile's cells, row by row, as float2 (a cell is 72 bytes and the
+    // level's cells start 8-byte aligned); k = r rowf2 + c walks t, t + NT, ...
+    const int nrow = min(th, d.cy - i0), ncol = min(tw, d.cx - j0);
+    if (nrow > 0 && ncol > 0 && ((uintptr_t)d.hist & 7) == 0) {
+        const int rowf2 = ncol * (NBIN / 2);
+        const int q0 = NT / rowf2, rem0 = NT - q0 * rowf2;
+        int r = t / rowf2, c = t - r * rowf2;
+        const float2 *src2 = reinterpret_cast<const float2 *>(outS);
+        while (r < nrow) {
+            float2 *dst = reinterpret_cast<float2 *>(d.hist + ((size_t)(i0 + r) * d.cx + j0) * NBIN);
+            dst[c] = src2[r * tw * (NBIN / 2) + c];
+            c += rem0;
+            r += q0;
+            if (c >= rowf2) {
+                c -= rowf2;
+                r++;
+            }
+        }
+    } else {
+        for (int r = 0; r < nrow; r++) {
+            float *dst = d.hist + ((size_t)(i0 + r) * d.cx + j0) * NBIN;
+            const float *srcr = outS + r * tw * NBIN;
+            for (int k = t; k < ncol * NBIN; k += NT) dst[k] = srcr[k];
+        }
     }
     __syncthreads();   // shared memory may be reused by the caller's next tile
 }
