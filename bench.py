@@ -62,8 +62,8 @@ FEAT_FLOP_PER_CELL = 300
 # (--set full) of the source whose SHA-256 starts with HIST_SOURCE_SHA: the
 # histogram stage's part of hog_stages.cuh (from its configuration to the
 # feature stage) and k_hist.cu; None: not captured
-HIST_TRAFFIC_250 = 248.913152e6 + 227.027712e6
-HIST_SOURCE_SHA = "fed70df76502fb6e"
+HIST_TRAFFIC_250 = 248.945920e6 + 226.867968e6
+HIST_SOURCE_SHA = "707dfffcdb6ed573"
 PAPER_CONTEXT = {"ms_per_frame": 0.333, "frames_per_s": 3003,
                  "hardware": "NVIDIA Titan X (Pascal), 16 frames/launch, incl. transfers"}
 

@@ -452,17 +452,43 @@ __device__ __forceinline__ void hist_tile(const LevelDesc &d, int tile, unsigned
 namespace feat_cfg {
 constexpr int HX = FEAT_TX + 2;   // 34 halo columns
 constexpr int HY = FEAT_TY + 2;   // 10 halo rows
-constexpr int CS = NBIN + 1;      // padded cell stride in shared memory
 constexpr int NT = FEAT_TX * FEAT_TY;
-constexpr size_t SMEM = sizeof(float) * (HY * HX * CS + HY * HX);   // 27,200
+// cells of 18 floats, read and written as 8-byte pairs: a warp's lanes at
+// the 72-byte cell stride hit distinct banks within each half-warp
+constexpr size_t SMEM = sizeof(float) * (HY * HX * NBIN + HY * HX);   // 25,840
 }  // namespace feat_cfg
+
+// (a.x * b.x, a.y * b.y) and (a.x + b.x, a.y + b.y), one packed FP32
+// instruction each (two IEEE operations, RN)
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "mul.rn.f32x2 pc, pa, pb;\n\t"
+        "mov.b64 {%0, %1}, pc;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pc, pa, pb;\n\t"
+        "mov.b64 {%0, %1}, pc;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
 
 template <bool COH>
 __device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float eps, float tau,
                                           unsigned char *smem) {
     using namespace feat_cfg;
-    float *hS = reinterpret_cast<float *>(smem);
-    float *eS = hS + HY * HX * CS;
+    float2 *hS = reinterpret_cast<float2 *>(smem);                  // [HY*HX][9]
+    float *eS = reinterpret_cast<float *>(smem) + HY * HX * NBIN;  // [HY*HX]
     const int ntx = (d.cx + FEAT_TX - 1) / FEAT_TX;
     const int j0 = (tile % ntx) * FEAT_TX, i0 = (tile / ntx) * FEAT_TY;
     const int t = threadIdx.x;
@@ -490,21 +516,20 @@ __device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float ep
     for (int s = 0; s < 2; s++) {
         const int k = t + s * NT;
         if (k >= HY * HX) continue;
-        float *dst = hS + k * CS;
+        float2 *dst = hS + k * (NBIN / 2);
+        float e = 0.0f;   // E = sum_{n<9} (h_n + h_{n+9})^2 of this cell
+        float hv[NBIN];
 #pragma unroll
         for (int q = 0; q < NBIN / 2; q++) {
-            dst[2 * q] = in[s] ? v[s][q].x : 0.0f;
-            dst[2 * q + 1] = in[s] ? v[s][q].y : 0.0f;
+            const float2 x = in[s] ? v[s][q] : make_float2(0.0f, 0.0f);
+            dst[q] = x;
+            hv[2 * q] = x.x;
+            hv[2 * q + 1] = x.y;
         }
-    }
-    __syncthreads();
-    for (int k = t; k < HY * HX; k += NT) {
-        const float *h = hS + k * CS;
-        float e = 0.0f;
 #pragma unroll
         for (int n = 0; n < 9; n++) {
-            const float s = h[n] + h[n + 9];
-            e += s * s;
+            const float sn = hv[n] + hv[n + 9];
+            e += sn * sn;
         }
         eS[k] = e;
     }
@@ -514,38 +539,60 @@ __device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float ep
     const int i = i0 + ti, j = j0 + tj;
     if (i < d.cy && j < d.cx) {
         const int r = ti + 1, c = tj + 1;
-        const float *h = hS + (r * HX + c) * CS;
+        const float2 *h = hS + (r * HX + c) * (NBIN / 2);
         float hv[NBIN];
 #pragma unroll
-        for (int b = 0; b < NBIN; b++) hv[b] = h[b];
+        for (int q = 0; q < NBIN / 2; q++) {
+            const float2 x = h[q];
+            hv[2 * q] = x.x;
+            hv[2 * q + 1] = x.y;
+        }
         const float e00 = eS[r * HX + c];
         const float S0 = e00 + eS[r * HX + c - 1] + eS[(r - 1) * HX + c] + eS[(r - 1) * HX + c - 1];
         const float S1 = e00 + eS[r * HX + c + 1] + eS[(r - 1) * HX + c] + eS[(r - 1) * HX + c + 1];
         const float S2 = e00 + eS[r * HX + c - 1] + eS[(r + 1) * HX + c] + eS[(r + 1) * HX + c - 1];
         const float S3 = e00 + eS[r * HX + c + 1] + eS[(r + 1) * HX + c] + eS[(r + 1) * HX + c + 1];
-        const float N0 = 1.0f / sqrtf(S0 + eps), N1 = 1.0f / sqrtf(S1 + eps);
-        const float N2 = 1.0f / sqrtf(S2 + eps), N3 = 1.0f / sqrtf(S3 + eps);
+        // halved normalisers and cap: 1/2 min(h N, tau) = min(h N/2, tau/2)
+        // exactly (scaling by 2^-1 commutes with rounding and with min), so
+        // the 1/2 of the averages is folded in; N_k = rsqrt(S_k + eps), the
+        // hardware reciprocal square root
+        const float N0 = 0.5f * rsqrtf(S0 + eps), N1 = 0.5f * rsqrtf(S1 + eps);
+        const float N2 = 0.5f * rsqrtf(S2 + eps), N3 = 0.5f * rsqrtf(S3 + eps);
+        const float tauh = 0.5f * tau;
 
         float f[32];
-        float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+        // blocks (0, 1) and (2, 3) in packed pairs (two IEEE products or
+        // sums per instruction); each feature sums its four terms as
+        // (a0 + a2) + (a1 + a3)
+        const float2 N01 = make_float2(N0, N1), N23 = make_float2(N2, N3);
+        float2 t01 = make_float2(0.0f, 0.0f), t23 = make_float2(0.0f, 0.0f);   // halved bin sums
 #pragma unroll
         for (int o = 0; o < NBIN; o++) {
-            const float a0 = fminf(hv[o] * N0, tau), a1 = fminf(hv[o] * N1, tau);
-            const float a2 = fminf(hv[o] * N2, tau), a3 = fminf(hv[o] * N3, tau);
-            f[o] = 0.5f * (((a0 + a1) + a2) + a3);
-            t0 += a0; t1 += a1; t2 += a2; t3 += a3;
+            const float2 p01 = fmul2(make_float2(hv[o], hv[o]), N01);
+            const float2 p23 = fmul2(make_float2(hv[o], hv[o]), N23);
+            const float2 a01 = make_float2(fminf(p01.x, tauh), fminf(p01.y, tauh));
+            const float2 a23 = make_float2(fminf(p23.x, tauh), fminf(p23.y, tauh));
+            const float2 s02 = fadd2(a01, a23);
+            f[o] = s02.x + s02.y;
+            t01 = fadd2(t01, a01);
+            t23 = fadd2(t23, a23);
         }
 #pragma unroll
         for (int o = 0; o < 9; o++) {
             const float s = hv[o] + hv[o + 9];
-            const float a0 = fminf(s * N0, tau), a1 = fminf(s * N1, tau);
-            const float a2 = fminf(s * N2, tau), a3 = fminf(s * N3, tau);
-            f[NBIN + o] = 0.5f * (((a0 + a1) + a2) + a3);
+            const float2 p01 = fmul2(make_float2(s, s), N01);
+            const float2 p23 = fmul2(make_float2(s, s), N23);
+            const float2 a01 = make_float2(fminf(p01.x, tauh), fminf(p01.y, tauh));
+            const float2 a23 = make_float2(fminf(p23.x, tauh), fminf(p23.y, tauh));
+            const float2 s02 = fadd2(a01, a23);
+            f[NBIN + o] = s02.x + s02.y;
         }
-        f[27] = 0.2357f * t0;
-        f[28] = 0.2357f * t1;
-        f[29] = 0.2357f * t2;
-        f[30] = 0.2357f * t3;
+        // 0.2357 x (the unhalved sum) = (2 x 0.2357) x t, both exactly
+        constexpr float k2 = 2.0f * 0.2357f;
+        f[27] = k2 * t01.x;
+        f[28] = k2 * t01.y;
+        f[29] = k2 * t23.x;
+        f[30] = k2 * t23.y;
         f[31] = 0.0f;
 
         const size_t plane = (size_t)d.cy * d.cx * CHUNK;
@@ -565,15 +612,16 @@ __device__ __forceinline__ void feat_tile(const LevelDesc &d, int tile, float ep
         }
         if (d.feat_hi) {
             // fp16 split for the tensor-core correlation: hi = f rounded to
-            // fp16, lo = (f - hi) rounded to fp16; |f - hi - lo| <= 2^-22 |f|
+            // fp16, lo = (f - hi) rounded to fp16; |f - hi - lo| <= 2^-22 |f|;
+            // two channels per conversion
             uint32_t hw[16], lw[16];
 #pragma unroll
             for (int o = 0; o < 16; o++) {
-                const __half h0 = __float2half_rn(f[2 * o]), h1 = __float2half_rn(f[2 * o + 1]);
-                const __half l0 = __float2half_rn(f[2 * o] - __half2float(h0));
-                const __half l1 = __float2half_rn(f[2 * o + 1] - __half2float(h1));
-                hw[o] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-                lw[o] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+                const __half2 h2 = __floats2half2_rn(f[2 * o], f[2 * o + 1]);
+                const float2 hf = __half22float2(h2);
+                const __half2 l2 = __floats2half2_rn(f[2 * o] - hf.x, f[2 * o + 1] - hf.y);
+                hw[o] = *reinterpret_cast<const uint32_t *>(&h2);
+                lw[o] = *reinterpret_cast<const uint32_t *>(&l2);
             }
             // group-major planes [4 channel groups][cy*cx cells][8 channels]:
             // a run of cells of one group is contiguous (bulk-copy friendly)
