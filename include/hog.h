@@ -343,14 +343,16 @@ int hog_pipeline_run(hog_ctx *ctx, const hog_ert *m, const hog_frame *frames, in
 
 /* Same result as hog_detect, from frames in HOST memory: the frames are
  * copied to the device inside the call and processed like
- * hog_detect_batched.  All frames are checked first (HOG_EINVAL, nothing
- * copied).  With more frames than max_batch / 2 they move in chunks of up to
- * max_batch / 2 through two halves of the device staging area on a copy
- * stream of the context, so the copy of chunk k+1 overlaps the detection of
- * chunk k.  Frames in page-locked memory are copied directly (dense frames
- * that follow each other in one copy); others are first copied into pinned
- * host staging.  The frames must stay valid until the call returns; it
- * synchronises the stream. */
+ * hog_detect_batched, in groups of up to max_batch frames.  All frames are
+ * checked first (HOG_EINVAL, nothing copied).  A group of more than
+ * max_batch / 2 frames moves in chunks of up to max_batch / 2 through two
+ * halves of the device staging area on a copy stream of the context: the
+ * copy of chunk k+1 overlaps the per-frame stages (pyramid .. candidate
+ * keys) of chunk k, and one suppression launch then takes the whole group.
+ * Frames in page-locked memory are copied directly (dense frames that
+ * follow each other in one copy); others are first copied into pinned host
+ * staging.  The frames must stay valid until the call returns; it
+ * synchronises the stream (once per group). */
 int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog_det *dets,
                     int32_t det_cap, int32_t *counts, void *stream);
 

@@ -115,6 +115,11 @@ struct PlanInfo {
 // Execution of a detection batch: one launch per stage, or the persistent
 // fused launch (pyramid .. correlation) followed by the suppression launch.
 enum { MODE_STAGED = 0, MODE_FUSED = 1 };
+// Parts of a batch to enqueue: the per-frame stages up to the candidate keys
+// (pyramid .. correlation), the suppression, or both.  hog_detect_host runs
+// the front of each chunk of frames as its copy arrives and the back of all
+// of them at once.
+enum { STAGES_FRONT = 1, STAGES_BACK = 2, STAGES_ALL = 3 };
 
 struct CachedPlan {
     std::vector<uint64_t> sig;              // batch shape: sizes, pitches, pointer alignment, regions
@@ -125,7 +130,7 @@ struct CachedPlan {
     size_t cap = 0;
     uint64_t used = 0;
     int runs = 0;                           // eager runs so far (graphs are captured after one)
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // per mode
+    cudaGraphExec_t graph[2][4] = {};       // per mode and stage set (STAGES_*)
 };
 }  // namespace
 
@@ -185,6 +190,7 @@ struct hog_ctx {
     // hog_detect_host: copy stream and events of the double-buffered staging
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_done[2] = {nullptr, nullptr}, stage_free = nullptr;
+    cudaEvent_t front_done[2] = {nullptr, nullptr};   // a chunk's front stages, per staging half
     // training arena (hog_backward), grown on demand
     char *d_train = nullptr;
     size_t train_cap = 0;
@@ -309,7 +315,8 @@ void free_ctx(hog_ctx *ctx) {
         if (e) cudaEventDestroy(e);
     for (auto &cp : ctx->plans) {
         F(cp.d);
-        for (auto &g : cp.graph) if (g) cudaGraphExecDestroy(g);
+        for (auto &gm : cp.graph)
+            for (auto &g : gm) if (g) cudaGraphExecDestroy(g);
     }
     F(ctx->d_fctr);
     F(ctx->d_train);
@@ -317,6 +324,8 @@ void free_ctx(hog_ctx *ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (cudaEvent_t e : ctx->copy_done)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->front_done)
         if (e) cudaEventDestroy(e);
     if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
     for (Geometry *g : ctx->geoms) {
@@ -880,7 +889,8 @@ int upload_plan(hog_ctx *ctx, const PlanBuilder &pb, const PlanInfo &info, char 
 }
 
 // Launch every stage of a plan that is resident at d on `stream`.
-int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t stream) {
+int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t stream,
+                int stages = STAGES_ALL) {
     const PlanLayout &L = info.L;
     const LevelDesc *descs = reinterpret_cast<const LevelDesc *>(d + L.descs);
     int rc = collect_profile(ctx);
@@ -888,56 +898,65 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
     auto mark = [&](int i) -> cudaError_t {
         return ctx->prof ? cudaEventRecord(ctx->prof_ev[i], stream) : cudaSuccess;
     };
-    CUDA_TRY(ctx, mark(0));
-    int npyr = 0;
-    if (L.npyrd > 0) {
-        CUDA_TRY(ctx, launch_pyramid_direct(descs, reinterpret_cast<const Job *>(d + L.pyrd), L.npyrd,
-                                            stream));
-        npyr++;
+    if (stages & STAGES_FRONT) {
+        CUDA_TRY(ctx, mark(0));
+        int npyr = 0;
+        if (L.npyrd > 0) {
+            CUDA_TRY(ctx, launch_pyramid_direct(descs, reinterpret_cast<const Job *>(d + L.pyrd), L.npyrd,
+                                                stream));
+            npyr++;
+        }
+        for (size_t s = 1; s < L.pyr.size(); s++) {
+            CUDA_TRY(ctx, launch_pyramid(descs, reinterpret_cast<const Job *>(d + L.pyr[s]),
+                                         L.npyr[s], stream));
+            npyr += L.npyr[s] > 0;
+        }
+        CUDA_TRY(ctx, mark(1));
+        CUDA_TRY(ctx, mark(2));
+        CUDA_TRY(ctx, launch_hist(descs, reinterpret_cast<const Job *>(d + L.hist), info.nhist, stream));
+        CUDA_TRY(ctx, mark(3));
+        CUDA_TRY(ctx, mark(4));
+        CUDA_TRY(ctx, launch_feat(descs, reinterpret_cast<const Job *>(d + L.feat), info.nfeat,
+                                  ctx->p.eps, ctx->p.trunc, stream));
+        CUDA_TRY(ctx, mark(5));
+        CUDA_TRY(ctx, mark(6));
+        if (info.tcf_grid > 0)
+            CUDA_TRY(ctx, launch_corr_tcf(descs, reinterpret_cast<const TcBand *>(d + L.bands),
+                                          reinterpret_cast<const int32_t *>(d + L.cta_first), info.tcf_grid,
+                                          ctx->d_wtc, ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
+                                          stream));
+        else if (info.ntc > 0 || info.ntcr > 0)
+            CUDA_TRY(ctx, launch_corr_tc(descs, reinterpret_cast<const Job *>(d + L.tc), info.ntc,
+                                         reinterpret_cast<const Job *>(d + L.tcr), info.ntcr, ctx->d_wtc,
+                                         ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
+                                         ctx->num_sms * corr_tc_ctas_per_sm(ctx->nfk), stream));
+        else
+            CUDA_TRY(ctx, launch_corr(descs, reinterpret_cast<const Job *>(d + L.corr), info.ncorr,
+                                      ctx->d_w, ctx->nfk, ctx->nf, ctx->p.threshold, stream));
+        CUDA_TRY(ctx, mark(7));
+        if (ctx->prof) {
+            hog_stage_stat *st = ctx->stats;
+            st[0].launches += npyr; st[0].units += info.px;
+            st[1].launches += info.nhist > 0; st[1].units += info.nhist > 0 ? info.cells : 0;
+            st[2].launches += info.nfeat > 0; st[2].units += info.nfeat > 0 ? info.cells : 0;
+            st[3].launches += (info.ncorr > 0) + (info.ntc > 0) + (info.ntcr > 0) + (info.tcf_grid > 0);
+            st[3].units += (info.ncorr > 0 || info.ntcr > 0 || info.tcf_grid > 0) ? info.wins : 0;
+        }
     }
-    for (size_t s = 1; s < L.pyr.size(); s++) {
-        CUDA_TRY(ctx, launch_pyramid(descs, reinterpret_cast<const Job *>(d + L.pyr[s]),
-                                     L.npyr[s], stream));
-        npyr += L.npyr[s] > 0;
+    if (stages & STAGES_BACK) {
+        CUDA_TRY(ctx, mark(8));
+        if (info.nframes > 0)
+            CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.nframes,
+                                     info.max_npos, ctx->d_flags, stream, ctx->nms_cluster));
+        CUDA_TRY(ctx, mark(9));
+        if (ctx->prof) {
+            ctx->stats[4].launches += info.nframes > 0;
+            ctx->stats[4].units += info.nframes;
+        }
     }
-    CUDA_TRY(ctx, mark(1));
-    CUDA_TRY(ctx, mark(2));
-    CUDA_TRY(ctx, launch_hist(descs, reinterpret_cast<const Job *>(d + L.hist), info.nhist, stream));
-    CUDA_TRY(ctx, mark(3));
-    CUDA_TRY(ctx, mark(4));
-    CUDA_TRY(ctx, launch_feat(descs, reinterpret_cast<const Job *>(d + L.feat), info.nfeat,
-                              ctx->p.eps, ctx->p.trunc, stream));
-    CUDA_TRY(ctx, mark(5));
-    CUDA_TRY(ctx, mark(6));
-    if (info.tcf_grid > 0)
-        CUDA_TRY(ctx, launch_corr_tcf(descs, reinterpret_cast<const TcBand *>(d + L.bands),
-                                      reinterpret_cast<const int32_t *>(d + L.cta_first), info.tcf_grid,
-                                      ctx->d_wtc, ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
-                                      stream));
-    else if (info.ntc > 0 || info.ntcr > 0)
-        CUDA_TRY(ctx, launch_corr_tc(descs, reinterpret_cast<const Job *>(d + L.tc), info.ntc,
-                                     reinterpret_cast<const Job *>(d + L.tcr), info.ntcr, ctx->d_wtc,
-                                     ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
-                                     ctx->num_sms * corr_tc_ctas_per_sm(ctx->nfk), stream));
-    else
-        CUDA_TRY(ctx, launch_corr(descs, reinterpret_cast<const Job *>(d + L.corr), info.ncorr,
-                                  ctx->d_w, ctx->nfk, ctx->nf, ctx->p.threshold, stream));
-    CUDA_TRY(ctx, mark(7));
-    CUDA_TRY(ctx, mark(8));
-    if (info.nframes > 0)
-        CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.nframes,
-                                 info.max_npos, ctx->d_flags, stream, ctx->nms_cluster));
-    CUDA_TRY(ctx, mark(9));
     if (ctx->prof) {
         ctx->prof_pending = true;
-        ctx->prof_mask = 0x1f;
-        hog_stage_stat *st = ctx->stats;
-        st[0].launches += npyr; st[0].units += info.px;
-        st[1].launches += info.nhist > 0; st[1].units += info.nhist > 0 ? info.cells : 0;
-        st[2].launches += info.nfeat > 0; st[2].units += info.nfeat > 0 ? info.cells : 0;
-        st[3].launches += (info.ncorr > 0) + (info.ntc > 0) + (info.ntcr > 0) + (info.tcf_grid > 0);
-        st[3].units += (info.ncorr > 0 || info.ntcr > 0 || info.tcf_grid > 0) ? info.wins : 0;
-        st[4].launches += info.nframes > 0; st[4].units += info.nframes;
+        ctx->prof_mask = (stages & STAGES_FRONT ? 0xfu : 0u) | (stages & STAGES_BACK ? 0x10u : 0u);
     }
     return HOG_OK;
 }
@@ -981,9 +1000,11 @@ int rebase_plan(hog_ctx *ctx, CachedPlan &cp, const std::vector<const uint8_t *>
     return HOG_OK;
 }
 
+// Frame i of the batch works in buffer slot slot_base + i (slot_base > 0:
+// one chunk of a larger batch whose suppression runs over all its slots).
 int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, cudaStream_t stream,
                 const char **d_out, const PlanInfo **info_out, CachedPlan **entry = nullptr,
-                const hog_roi *rois = nullptr) {
+                const hog_roi *rois = nullptr, int slot_base = 0) {
     // Signature of the batch's shape (frame sizes, pitches, the data
     // pointers' alignment mod 16, regions); the pointers themselves are
     // compared apart.  A plan of the same shape and other frames is rebased:
@@ -992,7 +1013,7 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
     std::vector<const uint8_t *> ptrs((size_t)nb);
     sig.reserve(2 + 2 * (size_t)nb + (rois ? 5 * (size_t)nb : 0));
     sig.push_back((uint64_t)nb | (rois ? (1ull << 63) : 0ull));
-    sig.push_back((uint64_t)(uint32_t)frame_base);
+    sig.push_back((uint64_t)(uint32_t)frame_base | ((uint64_t)(uint32_t)slot_base << 32));
     for (int i = 0; i < nb; i++) {
         ptrs[i] = frames[i].data;
         sig.push_back((uint64_t)(uintptr_t)frames[i].data & 15u);
@@ -1040,7 +1061,7 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
         FrameOpts o;
         o.nms = g->npos > 0;
         o.roi = rois ? &rois[i] : nullptr;
-        add_frame(ctx, pb, *g, f, i, frame_base + i, o);
+        add_frame(ctx, pb, *g, f, slot_base + i, frame_base + i, o);
     }
     build_fused_items(pb);
     if (ctx->wait_withhold)   // failure-path test: one wait expects a completion nothing gives
@@ -1054,8 +1075,9 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
     CachedPlan *victim = &ctx->plans[0];
     for (auto &cp : ctx->plans)
         if (!cp.d || cp.used < victim->used) victim = &cp;
-    for (auto &g : victim->graph)
-        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto &gm : victim->graph)
+        for (auto &g : gm)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     victim->runs = 0;
     if (victim->cap < info.L.total) {
         if (victim->d) {
@@ -1083,12 +1105,12 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
 }
 
 // Persistent fused launch of pyramid .. correlation, then suppression.
-int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t stream) {
+int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t stream,
+                      int stages = STAGES_ALL) {
     const PlanLayout &L = info.L;
     if ((size_t)info.nctr + 8 > ctx->fctr_cap)
         return fail(ctx, HOG_EINTERNAL, "fused counter capacity %zu < %d", ctx->fctr_cap, info.nctr + 8);
     int *head = ctx->d_fctr + info.nctr, *abort_flag = head + 1;
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_fctr, 0, sizeof(int) * ((size_t)info.nctr + 2), stream));
     FusedArgs a;
     a.items = reinterpret_cast<const FusedItem *>(d + L.items);
     a.nitems = info.nitems;
@@ -1109,66 +1131,80 @@ int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStr
     auto mark = [&](int i) -> cudaError_t {
         return ctx->prof ? cudaEventRecord(ctx->prof_ev[i], stream) : cudaSuccess;
     };
-    CUDA_TRY(ctx, mark(10));
-    CUDA_TRY(ctx, launch_fused(a, ctx->nfk, ctx->fused_grid, stream));
-    if (info.tcf_grid > 0)   // tensor-core correlation after the fused stages
-        CUDA_TRY(ctx, launch_corr_tcf(a.descs, reinterpret_cast<const TcBand *>(d + L.bands),
-                                      reinterpret_cast<const int32_t *>(d + L.cta_first), info.tcf_grid,
-                                      ctx->d_wtc, ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
-                                      stream));
-    else if (info.ntc > 0 || info.ntcr > 0)
-        CUDA_TRY(ctx, launch_corr_tc(a.descs, reinterpret_cast<const Job *>(d + L.tc), info.ntc,
-                                     reinterpret_cast<const Job *>(d + L.tcr), info.ntcr, ctx->d_wtc,
-                                     ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
-                                     ctx->num_sms * corr_tc_ctas_per_sm(ctx->nfk), stream));
-    CUDA_TRY(ctx, mark(11));
-    CUDA_TRY(ctx, mark(8));
-    if (info.nframes > 0)
-        CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.nframes,
-                                 info.max_npos, ctx->d_flags, stream, ctx->nms_cluster));
-    CUDA_TRY(ctx, mark(9));
+    if (stages & STAGES_FRONT) {
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_fctr, 0, sizeof(int) * ((size_t)info.nctr + 2), stream));
+        CUDA_TRY(ctx, mark(10));
+        CUDA_TRY(ctx, launch_fused(a, ctx->nfk, ctx->fused_grid, stream));
+        if (info.tcf_grid > 0)   // tensor-core correlation after the fused stages
+            CUDA_TRY(ctx, launch_corr_tcf(a.descs, reinterpret_cast<const TcBand *>(d + L.bands),
+                                          reinterpret_cast<const int32_t *>(d + L.cta_first), info.tcf_grid,
+                                          ctx->d_wtc, ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
+                                          stream));
+        else if (info.ntc > 0 || info.ntcr > 0)
+            CUDA_TRY(ctx, launch_corr_tc(a.descs, reinterpret_cast<const Job *>(d + L.tc), info.ntc,
+                                         reinterpret_cast<const Job *>(d + L.tcr), info.ntcr, ctx->d_wtc,
+                                         ctx->nfk, ctx->nf, ctx->p.threshold, ctx->d_flags,
+                                         ctx->num_sms * corr_tc_ctas_per_sm(ctx->nfk), stream));
+        CUDA_TRY(ctx, mark(11));
+        if (ctx->prof) {
+            ctx->stats[5].launches += (info.nitems > 0) + (info.ntc > 0) + (info.ntcr > 0) + (info.tcf_grid > 0);
+            ctx->stats[5].units += info.wins;
+        }
+    }
+    if (stages & STAGES_BACK) {
+        CUDA_TRY(ctx, mark(8));
+        if (info.nframes > 0)
+            CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.nframes,
+                                     info.max_npos, ctx->d_flags, stream, ctx->nms_cluster));
+        CUDA_TRY(ctx, mark(9));
+        if (ctx->prof) {
+            ctx->stats[4].launches += info.nframes > 0;
+            ctx->stats[4].units += info.nframes;
+        }
+    }
     if (ctx->prof) {
         ctx->prof_pending = true;
-        ctx->prof_mask = (1u << 4) | (1u << 5);
-        ctx->stats[5].launches += (info.nitems > 0) + (info.ntc > 0) + (info.ntcr > 0) + (info.tcf_grid > 0);
-        ctx->stats[5].units += info.wins;
-        ctx->stats[4].launches += info.nframes > 0; ctx->stats[4].units += info.nframes;
+        ctx->prof_mask = (stages & STAGES_FRONT ? 1u << 5 : 0u) | (stages & STAGES_BACK ? 1u << 4 : 0u);
     }
     return HOG_OK;
 }
 
-// Everything one detection batch enqueues before its outputs are packed.
+// Everything one detection batch enqueues before its outputs are packed
+// (stages: STAGES_ALL), or one part of it.  The front alone leaves the
+// flags as they are: the caller clears them once before a run of fronts.
 int enqueue_batch(hog_ctx *ctx, int mode, const char *d, const PlanInfo &info, int nb,
-                  cudaStream_t stream) {
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_counts, 0, sizeof(int32_t) * nb, stream));
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), stream));
-    return mode == MODE_FUSED ? launch_fused_plan(ctx, d, info, stream)
-                              : launch_plan(ctx, d, info, stream);
+                  cudaStream_t stream, int stages = STAGES_ALL) {
+    if (stages & STAGES_BACK) CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_counts, 0, sizeof(int32_t) * nb, stream));
+    if (stages == STAGES_ALL) CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), stream));
+    return mode == MODE_FUSED ? launch_fused_plan(ctx, d, info, stream, stages)
+                              : launch_plan(ctx, d, info, stream, stages);
 }
 
 // Run a batch eagerly, or -- from its second use on, with use_graph and no
 // profiling -- as a CUDA graph captured once per cached plan and mode.
-int run_batch(hog_ctx *ctx, int mode, CachedPlan *cp, int nb, bool use_graph, cudaStream_t stream) {
+int run_batch(hog_ctx *ctx, int mode, CachedPlan *cp, int nb, bool use_graph, cudaStream_t stream,
+              int stages = STAGES_ALL) {
     if (!use_graph || ctx->prof || cp->runs < 1) {
         cp->runs++;
-        return enqueue_batch(ctx, mode, cp->d, cp->info, nb, stream);
+        return enqueue_batch(ctx, mode, cp->d, cp->info, nb, stream, stages);
     }
-    if (!cp->graph[mode]) {
+    cudaGraphExec_t &ge = cp->graph[mode][stages];
+    if (!ge) {
         if (!ctx->cap_stream) CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
         CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_batch(ctx, mode, cp->d, cp->info, nb, ctx->cap_stream);
+        int rc = enqueue_batch(ctx, mode, cp->d, cp->info, nb, ctx->cap_stream, stages);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
         if (e != cudaSuccess) return fail(ctx, HOG_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&cp->graph[mode], g, 0);
+        e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
-            cp->graph[mode] = nullptr;
+            ge = nullptr;
             return fail(ctx, HOG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
         }
     }
-    CUDA_TRY(ctx, cudaGraphLaunch(cp->graph[mode], stream));
+    CUDA_TRY(ctx, cudaGraphLaunch(ge, stream));
     return HOG_OK;
 }
 
@@ -1177,7 +1213,8 @@ void clear_plans(hog_ctx *ctx) {
     cudaDeviceSynchronize();
     for (auto &cp : ctx->plans) {
         if (cp.d) cudaFree(cp.d);
-        for (auto &g : cp.graph) if (g) cudaGraphExecDestroy(g);
+        for (auto &gm : cp.graph)
+            for (auto &g : gm) if (g) cudaGraphExecDestroy(g);
     }
     ctx->plans.clear();
 }
@@ -1193,13 +1230,10 @@ int check_frame(hog_ctx *ctx, const hog_frame *f, bool device) {
     return HOG_OK;
 }
 
-int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, hog_det *dets,
-                  int det_cap, int *written_out, int32_t *counts, cudaStream_t stream,
-                  int mode = MODE_STAGED, bool use_graph = false, const hog_roi *rois = nullptr) {
-    int written = 0;
-    bool truncated = false;
-    // A pinned (page-locked, mapped) output buffer is written by the device
-    // directly; any other host buffer is filled from the context's staging.
+// The device address of a pinned (page-locked, mapped) output buffer, which
+// the device then writes directly; null for any other host buffer (filled
+// from the context's staging).
+hog_det *mapped_dets(hog_det *dets, int det_cap) {
     hog_det *dets_dev = nullptr;
     if (dets && det_cap > 0) {
         cudaPointerAttributes attr;
@@ -1208,6 +1242,48 @@ int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, 
             dets_dev = static_cast<hog_det *>(attr.devicePointer);
         cudaGetLastError();
     }
+    return dets_dev;
+}
+
+// After the suppression of slots 0 .. nb-1 (frames b0 .. b0+nb-1 of the
+// call) is enqueued: kept boxes of all frames packed frame after frame (into
+// dets_dev, or the context's mapped staging) by one kernel, then one
+// synchronisation and the counts.  written and truncated accumulate.
+int finish_batch(hog_ctx *ctx, int nb, int b0, hog_det *dets, hog_det *dets_dev, int det_cap, int &written,
+                 bool &truncated, int32_t *counts, cudaStream_t stream) {
+    const size_t D = (size_t)ctx->p.max_dets_per_frame;
+    const int room = dets ? std::max(det_cap - written, 0) : 0;
+    if (dets_dev)
+        CUDA_TRY(ctx, launch_pack(ctx->d_dets, ctx->p.max_dets_per_frame, ctx->d_counts, nb,
+                                  dets_dev + written, room, ctx->m_counts, stream));
+    else
+        CUDA_TRY(ctx, launch_pack(ctx->d_dets, ctx->p.max_dets_per_frame, ctx->d_counts, nb, ctx->m_dets,
+                                  (int)(D * ctx->p.max_batch), ctx->m_counts, stream));
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                                  stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    if (ctx->h_flags[2]) return fail(ctx, HOG_ETIMEOUT, "a bounded device wait gave up; results are invalid");
+    size_t off = 0;
+    for (int i = 0; i < nb; i++) {
+        const int c = ctx->h_counts[i];
+        if (counts) counts[b0 + i] = c;
+        const int k = std::min(c, ctx->p.max_dets_per_frame);
+        if (c > k) truncated = true;
+        const int take = std::min(k, std::max(det_cap - written, 0));
+        if (take > 0 && !dets_dev) std::memcpy(dets + written, ctx->h_dets + off, sizeof(hog_det) * take);
+        if (take < k) truncated = true;
+        written += take;
+        off += k;
+    }
+    return HOG_OK;
+}
+
+int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, hog_det *dets,
+                  int det_cap, int *written_out, int32_t *counts, cudaStream_t stream,
+                  int mode = MODE_STAGED, bool use_graph = false, const hog_roi *rois = nullptr) {
+    int written = 0;
+    bool truncated = false;
+    hog_det *dets_dev = mapped_dets(dets, det_cap);
     for (int b0 = 0; b0 < n; b0 += ctx->p.max_batch) {
         const int nb = std::min(ctx->p.max_batch, n - b0);
         const char *dplan = nullptr;
@@ -1218,35 +1294,8 @@ int detect_device(hog_ctx *ctx, const hog_frame *frames, int n, int frame_base, 
         if (rc) return rc;
         rc = run_batch(ctx, mode, cp, nb, use_graph, stream);
         if (rc) return rc;
-        // kept boxes of all frames, packed frame after frame into mapped
-        // pinned host memory by one kernel, then one synchronisation
-        const size_t D = (size_t)ctx->p.max_dets_per_frame;
-        const int room = dets ? std::max(det_cap - written, 0) : 0;
-        if (dets_dev)
-            CUDA_TRY(ctx, launch_pack(ctx->d_dets, ctx->p.max_dets_per_frame, ctx->d_counts, nb,
-                                      dets_dev + written, room, ctx->m_counts, stream));
-        else
-            CUDA_TRY(ctx, launch_pack(ctx->d_dets, ctx->p.max_dets_per_frame, ctx->d_counts, nb,
-                                      ctx->m_dets, (int)(D * ctx->p.max_batch), ctx->m_counts,
-                                      stream));
-        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, 4 * sizeof(int),
-                                      cudaMemcpyDeviceToHost, stream));
-        CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-        if (ctx->h_flags[2])
-            return fail(ctx, HOG_ETIMEOUT, "a bounded device wait gave up; results are invalid");
-        size_t off = 0;
-        for (int i = 0; i < nb; i++) {
-            const int c = ctx->h_counts[i];
-            if (counts) counts[b0 + i] = c;
-            const int k = std::min(c, ctx->p.max_dets_per_frame);
-            if (c > k) truncated = true;
-            const int take = std::min(k, std::max(det_cap - written, 0));
-            if (take > 0 && !dets_dev)
-                std::memcpy(dets + written, ctx->h_dets + off, sizeof(hog_det) * take);
-            if (take < k) truncated = true;
-            written += take;
-            off += k;
-        }
+        rc = finish_batch(ctx, nb, b0, dets, dets_dev, det_cap, written, truncated, counts, stream);
+        if (rc) return rc;
     }
     if (written_out) *written_out = written;
     return truncated ? fail(ctx, HOG_ECAPACITY, "detections truncated (%d written)", written)
@@ -1671,94 +1720,123 @@ int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog
     }
     if (!ctx->copy_stream) {
         CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-        CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->copy_done[0], cudaEventDisableTiming));
-        CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->copy_done[1], cudaEventDisableTiming));
+        for (int k = 0; k < 2; k++) {
+            CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->copy_done[k], cudaEventDisableTiming));
+            CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->front_done[k], cudaEventDisableTiming));
+        }
         CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->stage_free, cudaEventDisableTiming));
     }
-    // Chunks: with more frames than half the staging slots, the frames go
-    // in chunks of up to max_batch / 2 through two halves of the staging
-    // area, so that the host-to-device copy of chunk k+1 (on the copy
-    // stream) overlaps the detection of chunk k.
+    // Groups of up to max_batch frames.  A group of more than max_batch / 2
+    // frames goes in chunks of up to max_batch / 2 through two halves of the
+    // staging area: the host-to-device copy of chunk k+1 (on the copy
+    // stream) overlaps the front stages of chunk k (pyramid .. correlation,
+    // in buffer slots of their own), and one suppression launch then takes
+    // the whole group, as a batch of the group's size would.
     const int half = std::max(1, ctx->p.max_batch / 2);
-    const int chunk = n_frames > half ? std::min(half, (n_frames + 3) / 4) : std::max(n_frames, 1);
-    const int nchunks = (n_frames + chunk - 1) / chunk;
     std::vector<hog_frame> dev((size_t)ctx->p.max_batch);
-
-    // enqueue the copy of chunk k into staging half (k & 1) on the copy
-    // stream.  Frames that are dense (pitch = w), follow each other in
-    // pinned host memory and fill their device slot exactly (w * h =
-    // fbytes) move as one copy; pinned-ness is looked up once per run.
-    auto copy_chunk = [&](int k) -> int {
-        const int b0 = k * chunk, nb = std::min(chunk, n_frames - b0);
-        const size_t base = (size_t)(nchunks > 1 ? (k & 1) * chunk : 0);
-        cudaStream_t cs = ctx->copy_stream;
-        for (int i = 0; i < nb;) {
-            const hog_frame &f = frames[b0 + i];
-            uint8_t *d = ctx->d_stage + (base + i) * fbytes;
-            if (f.w == 0 || f.h == 0) { i++; continue; }
-            cudaPointerAttributes attr;
-            const bool pinned = cudaPointerGetAttributes(&attr, f.data) == cudaSuccess &&
-                                attr.type == cudaMemoryTypeHost;
-            cudaGetLastError();
-            const size_t fb = (size_t)f.w * f.h;
-            int run = 1;
-            if (pinned && f.pitch == f.w && fb == fbytes) {
-                while (i + run < nb) {
-                    const hog_frame &g = frames[b0 + i + run];
-                    if (g.w != f.w || g.h != f.h || g.pitch != f.pitch || g.data != f.data + run * fb) break;
-                    run++;
-                }
-                CUDA_TRY(ctx, cudaMemcpyAsync(d, f.data, fb * run, cudaMemcpyHostToDevice, cs));
-                i += run;
-                continue;
-            }
-            const uint8_t *srcp = f.data;
-            size_t spitch = (size_t)f.pitch;
-            if (!pinned) {   // stage through pinned memory so the copy is asynchronous
-                uint8_t *h = ctx->h_stage + (base + i) * fbytes;
-                for (int y = 0; y < f.h; y++) std::memcpy(h + (size_t)y * f.w, f.data + (size_t)y * f.pitch, f.w);
-                srcp = h;
-                spitch = (size_t)f.w;
-            }
-            CUDA_TRY(ctx, cudaMemcpy2DAsync(d, (size_t)f.w, srcp, spitch, (size_t)f.w, (size_t)f.h,
-                                            cudaMemcpyHostToDevice, cs));
-            i++;
-        }
-        CUDA_TRY(ctx, cudaEventRecord(ctx->copy_done[k & 1], cs));
-        return HOG_OK;
-    };
+    hog_det *dets_dev = mapped_dets(dets, det_cap);
+    int written = 0;
+    bool truncated = false;
 
     // the copy stream may only overwrite staging that no earlier work on
     // `stream` still reads
     CUDA_TRY(ctx, cudaEventRecord(ctx->stage_free, stream));
     CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->stage_free, 0));
-    int total = 0;
-    bool truncated = false;
-    int rc = nchunks > 0 ? copy_chunk(0) : HOG_OK;
-    for (int k = 0; k < nchunks && !rc; k++) {
-        // chunk k+1 goes into the other half, whose last reader (chunk k-1)
-        // has finished: detect_device synchronised `stream` before returning
-        if (k + 1 < nchunks) rc = copy_chunk(k + 1);
-        if (rc) break;
-        const int b0 = k * chunk, nb = std::min(chunk, n_frames - b0);
-        const size_t base = (size_t)(nchunks > 1 ? (k & 1) * chunk : 0);
-        for (int i = 0; i < nb; i++) {
-            const hog_frame &f = frames[b0 + i];
-            dev[i] = hog_frame{ctx->d_stage + (base + i) * fbytes, f.w, f.h, f.w};
+    int rc = HOG_OK;
+    for (int g0 = 0; g0 < n_frames && !rc; g0 += ctx->p.max_batch) {
+        const int ng = std::min(ctx->p.max_batch, n_frames - g0);
+        const int chunk = ng > half ? std::min(half, (ng + 3) / 4) : ng;
+        const int nchunks = (ng + chunk - 1) / chunk;
+        auto staged = [&](int k, int i) {   // staging slot of frame i of chunk k
+            return (size_t)(nchunks > 1 ? (k & 1) * chunk : 0) + (size_t)i;
+        };
+
+        // enqueue the copy of chunk k into its staging half on the copy
+        // stream.  Frames that are dense (pitch = w), follow each other in
+        // pinned host memory and fill their device slot exactly (w * h =
+        // fbytes) move as one copy.
+        auto copy_chunk = [&](int k) -> int {
+            const int b0 = g0 + k * chunk, nb = std::min(chunk, ng - k * chunk);
+            cudaStream_t cs = ctx->copy_stream;
+            for (int i = 0; i < nb;) {
+                const hog_frame &f = frames[b0 + i];
+                uint8_t *d = ctx->d_stage + staged(k, i) * fbytes;
+                if (f.w == 0 || f.h == 0) { i++; continue; }
+                cudaPointerAttributes attr;
+                const bool pinned = cudaPointerGetAttributes(&attr, f.data) == cudaSuccess &&
+                                    attr.type == cudaMemoryTypeHost;
+                cudaGetLastError();
+                const size_t fb = (size_t)f.w * f.h;
+                int run = 1;
+                if (pinned && f.pitch == f.w && fb == fbytes) {
+                    while (i + run < nb) {
+                        const hog_frame &g = frames[b0 + i + run];
+                        if (g.w != f.w || g.h != f.h || g.pitch != f.pitch || g.data != f.data + run * fb) break;
+                        run++;
+                    }
+                    CUDA_TRY(ctx, cudaMemcpyAsync(d, f.data, fb * run, cudaMemcpyHostToDevice, cs));
+                    i += run;
+                    continue;
+                }
+                const uint8_t *srcp = f.data;
+                size_t spitch = (size_t)f.pitch;
+                if (!pinned) {   // stage through pinned memory so the copy is asynchronous
+                    uint8_t *h = ctx->h_stage + staged(k, i) * fbytes;
+                    for (int y = 0; y < f.h; y++)
+                        std::memcpy(h + (size_t)y * f.w, f.data + (size_t)y * f.pitch, f.w);
+                    srcp = h;
+                    spitch = (size_t)f.w;
+                }
+                CUDA_TRY(ctx, cudaMemcpy2DAsync(d, (size_t)f.w, srcp, spitch, (size_t)f.w, (size_t)f.h,
+                                                cudaMemcpyHostToDevice, cs));
+                i++;
+            }
+            CUDA_TRY(ctx, cudaEventRecord(ctx->copy_done[k & 1], cs));
+            return HOG_OK;
+        };
+
+        // the fronts leave the flags alone: clear them once for the group
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), stream));
+        rc = copy_chunk(0);
+        for (int k = 0; k < nchunks && !rc; k++) {
+            if (k + 1 < nchunks) {
+                // chunk k+1 goes into the half chunk k-1 read: after its front
+                if (k >= 1)
+                    CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->front_done[(k + 1) & 1], 0));
+                rc = copy_chunk(k + 1);
+                if (rc) break;
+            }
+            const int c0 = k * chunk, nb = std::min(chunk, ng - c0);
+            for (int i = 0; i < nb; i++) {
+                const hog_frame &f = frames[g0 + c0 + i];
+                dev[c0 + i] = hog_frame{ctx->d_stage + staged(k, i) * fbytes, f.w, f.h, f.w};
+            }
+            CUDA_TRY(ctx, cudaStreamWaitEvent(stream, ctx->copy_done[k & 1], 0));
+            const char *dplan = nullptr;
+            const PlanInfo *info = nullptr;
+            CachedPlan *cp = nullptr;
+            rc = cached_plan(ctx, dev.data() + c0, nb, g0 + c0, stream, &dplan, &info, &cp, nullptr, c0);
+            if (rc) break;
+            rc = run_batch(ctx, ctx->batched_mode, cp, nb, true, stream,
+                           nchunks > 1 ? STAGES_FRONT : STAGES_ALL);
+            if (rc) break;
+            CUDA_TRY(ctx, cudaEventRecord(ctx->front_done[k & 1], stream));
         }
-        CUDA_TRY(ctx, cudaStreamWaitEvent(stream, ctx->copy_done[k & 1], 0));
-        const int cap = dets ? std::max(det_cap - total, 0) : 0;
-        int wrote = 0;
-        rc = detect_device(ctx, dev.data(), nb, b0, dets ? dets + total : nullptr, cap, &wrote,
-                           counts ? counts + b0 : nullptr, stream, ctx->batched_mode, true);
-        if (rc == HOG_ECAPACITY) { truncated = true; rc = HOG_OK; }
-        total += wrote;
+        if (!rc && nchunks > 1) {   // suppression of the whole group
+            const char *dplan = nullptr;
+            const PlanInfo *info = nullptr;
+            CachedPlan *cp = nullptr;
+            rc = cached_plan(ctx, dev.data(), ng, g0, stream, &dplan, &info, &cp);
+            if (!rc) rc = run_batch(ctx, ctx->batched_mode, cp, ng, true, stream, STAGES_BACK);
+        }
+        if (!rc) rc = finish_batch(ctx, ng, g0, dets, dets_dev, det_cap, written, truncated, counts, stream);
     }
     if (rc) {
         cudaStreamSynchronize(ctx->copy_stream);   // no copy still writes the staging area
+        cudaStreamSynchronize(stream);             // nor a front still reads it
         return rc;
     }
-    return truncated ? fail(ctx, HOG_ECAPACITY, "detections truncated") : HOG_OK;
+    return truncated ? fail(ctx, HOG_ECAPACITY, "detections truncated (%d written)", written) : HOG_OK;
 }
 
 int hog_autotune(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, const char *cache_path,

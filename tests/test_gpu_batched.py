@@ -110,3 +110,30 @@ def test_batch_tensor_and_chunked_host_copies(H, synth):
         assert gc.tolist() == wc.tolist() and np.array_equal(got, want)
     got, gc = det.detect_host(mixed[:1])                 # one frame: no chunking
     assert gc[0] == wc[0]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", [0, 1])
+def test_host_chunks_with_one_suppression(H, synth, mode):
+    """hog_detect_host on a group of more than max_batch / 2 frames runs the
+    per-frame stages chunk by chunk (each chunk in buffer slots of its own)
+    and one suppression launch over the whole group: per-stage and fused
+    modes give the device result, on a full group, a group with a ragged
+    last chunk, two groups, and with the output capacity cut short."""
+    W = synth.filters(5)
+    det = H.Detector(W, max_w=640, max_h=480, max_batch=8)
+    det.set_batched_mode(mode)
+    host = synth.eyeblink_stream(19, start=40)
+    pinned = torch.from_numpy(host).pin_memory().numpy()
+    fd = dev(host)
+    for n in (8, 7, 19):
+        ref, rc = det.detect([fd[i] for i in range(n)])
+        for _ in range(2):   # the second call replays the cached plans' graphs
+            got, gc = det.detect_host(pinned[:n])
+            assert gc.tolist() == rc.tolist() and np.array_equal(got, ref), n
+            assert (got["frame"] == np.repeat(np.arange(n), rc)).all()
+    ref, rc = det.detect([fd[i] for i in range(8)])
+    cap = int(rc[:3].sum()) + 5
+    part, pc = det.detect_host(pinned[:8], det_cap=cap, allow_capacity=True)
+    assert pc.tolist() == rc.tolist() and len(part) == cap
+    assert np.array_equal(part, ref[:cap])
