@@ -873,8 +873,9 @@ def main():
     plain.set_profiling(False)
     plain.close()
 
-    # ---- e2e: host frames in pinned memory through hog_detect_host
-    for _ in range(max(1, args.warmup // 2)):
+    # ---- e2e: host frames in pinned memory through hog_detect_host (the
+    # warm-up calls build the chunks' plans and capture their graphs)
+    for _ in range(max(3, args.warmup)):
         det.detect_host(pinned_np, out=out_np)
     barrier()
     t0 = time.perf_counter()

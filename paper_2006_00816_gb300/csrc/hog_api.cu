@@ -185,7 +185,7 @@ struct hog_ctx {
     uint16_t *d_fh = nullptr;       // per slot: fp16 feature planes hi, lo [cells][32]
     float *d_gm = nullptr;          // per slot: row-shift matrices [10 F][cells] per level
     size_t cells_slot = 0, fh_slot = 0, gm_slot = 0;
-    int plan_cache_max = 8;         // cached batch plans (a server raises it)
+    int plan_cache_max = 16;        // cached batch plans (a server raises it)
     cudaStream_t cap_stream = nullptr;
     // hog_detect_host: copy stream and events of the double-buffered staging
     cudaStream_t copy_stream = nullptr;
@@ -1731,7 +1731,8 @@ int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog
     // staging area: the host-to-device copy of chunk k+1 (on the copy
     // stream) overlaps the front stages of chunk k (pyramid .. correlation,
     // in buffer slots of their own), and one suppression launch then takes
-    // the whole group, as a batch of the group's size would.
+    // the whole group, as a batch of the group's size would.  The first
+    // chunk is a quarter of the others: its copy is the one nothing hides.
     const int half = std::max(1, ctx->p.max_batch / 2);
     std::vector<hog_frame> dev((size_t)ctx->p.max_batch);
     hog_det *dets_dev = mapped_dets(dets, det_cap);
@@ -1746,7 +1747,10 @@ int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog
     for (int g0 = 0; g0 < n_frames && !rc; g0 += ctx->p.max_batch) {
         const int ng = std::min(ctx->p.max_batch, n_frames - g0);
         const int chunk = ng > half ? std::min(half, (ng + 3) / 4) : ng;
-        const int nchunks = (ng + chunk - 1) / chunk;
+        std::vector<int> cbeg(1, 0);   // first frame of each chunk in the group, then ng
+        for (int at = ng > half ? std::max(1, chunk / 4) : ng; at < ng; at += chunk) cbeg.push_back(at);
+        cbeg.push_back(ng);
+        const int nchunks = (int)cbeg.size() - 1;
         auto staged = [&](int k, int i) {   // staging slot of frame i of chunk k
             return (size_t)(nchunks > 1 ? (k & 1) * chunk : 0) + (size_t)i;
         };
@@ -1756,7 +1760,7 @@ int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog
         // pinned host memory and fill their device slot exactly (w * h =
         // fbytes) move as one copy.
         auto copy_chunk = [&](int k) -> int {
-            const int b0 = g0 + k * chunk, nb = std::min(chunk, ng - k * chunk);
+            const int b0 = g0 + cbeg[k], nb = cbeg[k + 1] - cbeg[k];
             cudaStream_t cs = ctx->copy_stream;
             for (int i = 0; i < nb;) {
                 const hog_frame &f = frames[b0 + i];
@@ -1806,7 +1810,7 @@ int hog_detect_host(hog_ctx *ctx, const hog_frame *frames, int32_t n_frames, hog
                 rc = copy_chunk(k + 1);
                 if (rc) break;
             }
-            const int c0 = k * chunk, nb = std::min(chunk, ng - c0);
+            const int c0 = cbeg[k], nb = cbeg[k + 1] - c0;
             for (int i = 0; i < nb; i++) {
                 const hog_frame &f = frames[g0 + c0 + i];
                 dev[c0 + i] = hog_frame{ctx->d_stage + staged(k, i) * fbytes, f.w, f.h, f.w};
