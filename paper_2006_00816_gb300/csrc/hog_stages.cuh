@@ -33,8 +33,10 @@ __device__ __forceinline__ T ld_in(const T *p) {
 // x = 20k .. 20k+19 read exactly the 24 source bytes 24k .. 24k+23 of each
 // of their two source rows: six aligned 32-bit loads per row, byte offsets
 // and weights known at compile time, five 32-bit stores.  Tile PYR_TX x
-// PYR_TY = 160 x 32 outputs, 256 threads (8 x 20 columns, 32 rows); edge
-// groups and unaligned sources (a caller's frame) take the per-pixel path.
+// PYR_TY = 160 x 32 outputs, 256 threads (8 x 20 columns, 32 rows).  A
+// group at a level's right edge takes the same path with its reads kept
+// inside the source row and byte stores; only unaligned sources (a
+// caller's frame) take the per-pixel path.
 //
 // Direct-to-size level (Section 6.6, future work): level s straight from
 // the frame with the ratio (6/5)^s, source coordinate ((2x+1) 6^s - 5^s) /
@@ -128,14 +130,29 @@ __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
     const uint8_t *r1 = r0 + d.spitch;
     uint8_t *out = d.dst + (size_t)y * d.pitch + x;
     const int sx = (x / 5) * 6;   // first source column of the group
-    const bool fast = x + PYR_GROUP <= d.w && sx + 24 <= d.sw &&
-                      ((reinterpret_cast<uintptr_t>(r0 + sx) | (uintptr_t)d.spitch) & 3u) == 0;
+    // word reads where the rows are 4-byte aligned.  At the right edge of a
+    // level the group's last source words or outputs may lie past the row:
+    // only source bytes inside the row are read (no output in range needs
+    // the others: x0 + 1 <= sw - 1; a word the row's end cuts is read byte
+    // by byte), outputs past the width are not written
+    const bool fast = ((reinterpret_cast<uintptr_t>(r0 + sx) | (uintptr_t)d.spitch) & 3u) == 0;
     if (fast) {
+        const bool edge = x + PYR_GROUP > d.w || sx + 24 > d.sw;
         uint32_t a[6], b[6];
 #pragma unroll
         for (int q = 0; q < 6; q++) {
-            a[q] = ld_in<COH>(reinterpret_cast<const uint32_t *>(r0 + sx) + q);
-            b[q] = ld_in<COH>(reinterpret_cast<const uint32_t *>(r1 + sx) + q);
+            const int c = sx + 4 * q;   // first source column of word q
+            if (!edge || c + 4 <= d.sw) {
+                a[q] = ld_in<COH>(reinterpret_cast<const uint32_t *>(r0 + sx) + q);
+                b[q] = ld_in<COH>(reinterpret_cast<const uint32_t *>(r1 + sx) + q);
+            } else {
+                a[q] = 0u;
+                b[q] = 0u;
+                for (int k = 0; k < 4 && c + k < d.sw; k++) {
+                    a[q] |= (uint32_t)ld_in<COH>(r0 + c + k) << (8 * k);
+                    b[q] |= (uint32_t)ld_in<COH>(r1 + c + k) << (8 * k);
+                }
+            }
         }
         uint32_t packed[5] = {0u, 0u, 0u, 0u, 0u};
 #pragma unroll
@@ -146,8 +163,13 @@ __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
             const int acc = wy0 * top + wy1 * bot;
             packed[i >> 2] |= (uint32_t)((acc + 50) / 100) << (8 * (i & 3));
         }
+        if (!edge) {
 #pragma unroll
-        for (int q = 0; q < 5; q++) reinterpret_cast<uint32_t *>(out)[q] = packed[q];   // x, pitch: 4 | .
+            for (int q = 0; q < 5; q++) reinterpret_cast<uint32_t *>(out)[q] = packed[q];   // x, pitch: 4 | .
+        } else {
+            for (int i = 0; i < PYR_GROUP && x + i < d.w; i++)
+                out[i] = (uint8_t)(packed[i >> 2] >> (8 * (i & 3)));
+        }
         return;
     }
     for (int i = 0; i < PYR_GROUP && x + i < d.w; i++) {
