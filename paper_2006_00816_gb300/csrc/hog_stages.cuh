@@ -155,13 +155,15 @@ __device__ __forceinline__ void pyramid_tile(const LevelDesc &d, int tile) {
             }
         }
         uint32_t packed[5] = {0u, 0u, 0u, 0u, 0u};
+        const uint32_t uw0 = (uint32_t)wy0, uw1 = (uint32_t)wy1;
 #pragma unroll
         for (int i = 0; i < PYR_GROUP; i++) {
-            const int o = (12 * i + 1) / 10, fx = (12 * i + 1) % 10;   // constants
-            const int top = (10 - fx) * pyr_byte(a, o) + fx * pyr_byte(a, o + 1);
-            const int bot = (10 - fx) * pyr_byte(b, o) + fx * pyr_byte(b, o + 1);
-            const int acc = wy0 * top + wy1 * bot;
-            packed[i >> 2] |= (uint32_t)((acc + 50) / 100) << (8 * (i & 3));
+            const int o = (12 * i + 1) / 10;
+            const uint32_t fx = (12 * i + 1) % 10;   // constants
+            const uint32_t top = (10 - fx) * (uint32_t)pyr_byte(a, o) + fx * (uint32_t)pyr_byte(a, o + 1);
+            const uint32_t bot = (10 - fx) * (uint32_t)pyr_byte(b, o) + fx * (uint32_t)pyr_byte(b, o + 1);
+            const uint32_t acc = uw0 * top + uw1 * bot;
+            packed[i >> 2] |= ((acc + 50u) / 100u) << (8 * (i & 3));
         }
         if (!edge) {
 #pragma unroll
