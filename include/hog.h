@@ -229,8 +229,10 @@ int hog_get_corr_engine(const hog_ctx *ctx, int32_t *engine);
  * each frame's suppression on a thread-block cluster of c CTAs (positions
  * split across the CTAs' shared memory, neighbour states read through
  * distributed shared memory); c = 0 (default): automatic -- clusters of
- * about SMs / frames CTAs, and at least the size whose state fits in shared
- * memory.  The kept boxes are the same for every c.  Drops cached plans and
+ * about SMs / frames CTAs when that is at least 8 (batches of a few frames),
+ * else one CTA per frame; at least 2 for frames too large for a one-CTA
+ * shared-memory workspace (about 57,800 window positions, e.g. larger than
+ * 1280x1024).  The kept boxes are the same for every c.  Drops cached plans and
  * graphs when c changes.  HOG_EINVAL for other values. */
 int hog_set_nms_cluster(hog_ctx *ctx, int32_t c);
 

@@ -107,6 +107,9 @@ struct PlanLayout {
 struct PlanInfo {
     PlanLayout L;
     int nhist = 0, nfeat = 0, ncorr = 0, nframes = 0, max_npos = 0, ntc = 0, ntcr = 0;
+    // suppression: frames per workspace class (the plan's frames are sorted
+    // by class) and the largest npos of each
+    int ncls[NMS_WS_CLASSES] = {}, cls_npos[NMS_WS_CLASSES] = {};
     int tcf_grid = 0;               // fused tensor-core correlation: CTAs (0: not used)
     int nitems = 0, nctr = 0;       // persistent fused launch: work items, counters
     int64_t px = 0, cells = 0, wins = 0;
@@ -785,6 +788,14 @@ void build_tc_bands(PlanBuilder &pb, int num_sms) {
     }
 }
 
+// The suppression launches take a batch's frames by workspace class, so the
+// plan holds them sorted by class (stable: frame order within a class).
+void sort_frames(PlanBuilder &pb) {
+    std::stable_sort(pb.frames.begin(), pb.frames.end(), [](const FrameDesc &a, const FrameDesc &b) {
+        return nms_ws_class(a.npos) < nms_ws_class(b.npos);
+    });
+}
+
 void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
     PlanLayout &L = info.L;
     size_t off = 0;
@@ -819,7 +830,12 @@ void layout_plan(const PlanBuilder &pb, int nf, PlanInfo &info) {
     info.tcf_grid = pb.cta_first.empty() ? 0 : (int)pb.cta_first.size() - 1;
     info.nframes = (int)pb.frames.size();
     info.max_npos = 0;
-    for (const FrameDesc &f : pb.frames) info.max_npos = std::max(info.max_npos, f.npos);
+    for (const FrameDesc &f : pb.frames) {
+        info.max_npos = std::max(info.max_npos, f.npos);
+        const int k = nms_ws_class(f.npos);
+        info.ncls[k]++;
+        info.cls_npos[k] = std::max(info.cls_npos[k], f.npos);
+    }
     info.px = info.cells = info.wins = 0;
     for (const LevelDesc &ld : pb.descs) {
         if (ld.level >= 1) info.px += (int64_t)ld.w * ld.h;
@@ -946,8 +962,8 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
     if (stages & STAGES_BACK) {
         CUDA_TRY(ctx, mark(8));
         if (info.nframes > 0)
-            CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.nframes,
-                                     info.max_npos, ctx->d_flags, stream, ctx->nms_cluster));
+            CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.ncls,
+                                     info.cls_npos, ctx->d_flags, stream, ctx->nms_cluster));
         CUDA_TRY(ctx, mark(9));
         if (ctx->prof) {
             ctx->stats[4].launches += info.nframes > 0;
@@ -964,6 +980,7 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
 // Build, upload and launch a one-off plan (inspection entry points).
 int run_plan(hog_ctx *ctx, PlanBuilder &pb, cudaStream_t stream) {
     build_tc_bands(pb, ctx->num_sms);
+    sort_frames(pb);
     PlanInfo info;
     layout_plan(pb, ctx->nf, info);
     int rc = upload_plan(ctx, pb, info, nullptr, stream);
@@ -1068,6 +1085,7 @@ int cached_plan(hog_ctx *ctx, const hog_frame *frames, int nb, int frame_base, c
         for (FusedItem &it : pb.items)
             if (it.wait >= 0) { it.target += 1; break; }
     build_tc_bands(pb, ctx->num_sms);
+    sort_frames(pb);
     PlanInfo info;
     layout_plan(pb, ctx->nf, info);
     // least recently used entry (or a free one)
@@ -1154,8 +1172,8 @@ int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStr
     if (stages & STAGES_BACK) {
         CUDA_TRY(ctx, mark(8));
         if (info.nframes > 0)
-            CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.nframes,
-                                     info.max_npos, ctx->d_flags, stream, ctx->nms_cluster));
+            CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.ncls,
+                                     info.cls_npos, ctx->d_flags, stream, ctx->nms_cluster));
         CUDA_TRY(ctx, mark(9));
         if (ctx->prof) {
             ctx->stats[4].launches += info.nframes > 0;

@@ -339,13 +339,38 @@ cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, int32_t *nbr_t,
 cudaError_t launch_pack(const hog_det *dets, int per_frame, const int32_t *counts, int nframes,
                         hog_det *out, int out_cap, int32_t *counts_out, cudaStream_t stream);
 
-// max_npos: largest npos of the frames (selects the shared- or global-memory
-// workspace).  flags[0] |= 1 on capacity overflow; flags[2] |= 1 if a bounded
-// wait gave up.
-cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *flags,
+// frames: sorted by workspace class (nms_ws_class of npos); ncls[k] frames
+// of class k with at most max_npos[k] positions, each class its own launch.
+// flags[0] |= 1 on capacity overflow; flags[2] |= 1 if a bounded wait gave up.
+cudaError_t launch_nms(const FrameDesc *frames, const int *ncls, const int *max_npos, int *flags,
                        cudaStream_t stream, int cluster_request);
 // Cluster size launch_nms uses for such a batch (1 = one CTA per frame).
 int nms_cluster_size(int nframes, int max_npos, int request);
+
+// Suppression workspace of the one-CTA form, per frame: key high words,
+// which also record decisions (4 B per position), the candidate list (2 B
+// per position in shared memory, 4 B in global memory), the suppression
+// bitmask (1 bit) and the resume slot (1 B).  640x480 frames (9,537
+// positions) take 68 KB: three CTAs per SM.
+__host__ __device__ constexpr size_t nms_ws_bytes(int npos, bool in_smem) {
+    return (size_t)npos * (in_smem ? 7 : 9) + 4 * (size_t)((npos + 31) / 32) + 64;
+}
+// Positions a shared-memory workspace can index (16-bit list entries).
+constexpr int NMS_SMEM_MAX_NPOS = 65535;
+constexpr int NMS_SMEM_MAX = 200 * 1024;        // all of the workspace in shared memory
+constexpr int NMS_KEYS_SMEM_MAX = 226 * 1024;   // the key words alone in shared memory (227 KB less static)
+// Where a frame's one-CTA suppression keeps its workspace: everything in
+// shared memory (three CTAs per SM at 640x480), the key words alone in
+// shared memory (the list, bitmask and resume slots in global memory; one
+// CTA of 1024 threads per SM, frames up to about 57,800 positions, e.g.
+// 1280x1024), or everything in global memory.
+enum { NMS_WS_SMEM = 0, NMS_WS_KEYS = 1, NMS_WS_GLOBAL = 2, NMS_WS_CLASSES = 3 };
+__host__ __device__ constexpr size_t nms_keys_bytes(int npos) { return 4 * (size_t)npos + 64; }
+__host__ __device__ constexpr int nms_ws_class(int npos) {
+    return nms_ws_bytes(npos, true) <= (size_t)NMS_SMEM_MAX && npos <= NMS_SMEM_MAX_NPOS ? NMS_WS_SMEM
+           : nms_keys_bytes(npos) <= (size_t)NMS_KEYS_SMEM_MAX                          ? NMS_WS_KEYS
+                                                                                         : NMS_WS_GLOBAL;
+}
 
 // Histogram tile width (blocks) for a level of cx x cy cells and height h
 // pixels: the bw in [HIST_BW_MIN, HIST_BW_MAX] whose tiles issue the fewest

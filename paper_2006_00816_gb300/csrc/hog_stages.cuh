@@ -891,16 +891,6 @@ __device__ __forceinline__ WinBox window_box(double rx, double ry, int u, int v)
     return b;
 }
 
-// Workspace per frame: key high words, which also record decisions (4 B per
-// position), the candidate list (2 B per position in shared memory, 4 B in
-// global memory), the suppression bitmask (1 bit) and the resume slot (1 B).
-// 640x480 frames (9,537 positions) take 68 KB: three CTAs per SM.
-__host__ __device__ constexpr size_t nms_ws_bytes(int npos, bool in_smem) {
-    return (size_t)npos * (in_smem ? 7 : 9) + 4 * (size_t)((npos + 31) / 32) + 64;
-}
-// Positions a shared-memory workspace can index (16-bit list entries).
-constexpr int NMS_SMEM_MAX_NPOS = 65535;
-
 // Whether window position p of a frame is scanned: at or after the first
 // scanned level, and inside its level's rectangle when the frame has a
 // region of interest.  Other positions carry no key.
@@ -912,17 +902,20 @@ __device__ __forceinline__ bool nms_scanned(const FrameDesc &fd, int p) {
     return u >= fd.roi_u0[l] && u < fd.roi_u1[l] && v >= fd.roi_v0[l] && v < fd.roi_v1[l];
 }
 
-template <bool SM, int NT, bool COH>
+// WS: where the workspace lives (nms_ws_class): NMS_WS_SMEM all of it in
+// shared memory, NMS_WS_KEYS the key words in shared memory and the rest in
+// fd.ws, NMS_WS_GLOBAL all of it in fd.ws.
+template <int WS, int NT, bool COH>
 __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *smem, int *flags,
                                           int *sh /* NT/32 + 4 ints of shared memory */) {
-    using idx_t = typename std::conditional<SM, uint16_t, int32_t>::type;
+    using idx_t = typename std::conditional<WS == NMS_WS_SMEM, uint16_t, int32_t>::type;
     const int t = threadIdx.x;
     const int npos = fd.npos;
-    unsigned char *base = SM ? smem : reinterpret_cast<unsigned char *>(fd.ws);
+    unsigned char *base = WS == NMS_WS_SMEM ? smem : reinterpret_cast<unsigned char *>(fd.ws);
     // key high word of each position while it is undecided; its decision
     // overwrites it: NMS_KEPTKEY (above every key) or NMS_NOKEY (below every
     // key, as for a position that never had one)
-    volatile uint32_t *khi = reinterpret_cast<volatile uint32_t *>(base);
+    volatile uint32_t *khi = reinterpret_cast<volatile uint32_t *>(WS == NMS_WS_GLOBAL ? base : smem);
     idx_t *list = reinterpret_cast<idx_t *>(base + 4 * (size_t)npos);   // undecided, position order
     // suppression bitmask: bit q set once a neighbour of q has been kept, so
     // q (if ranked below it) is suppressed without scanning its neighbours

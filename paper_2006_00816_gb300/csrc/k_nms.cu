@@ -30,7 +30,11 @@ namespace hogk {
 namespace {
 constexpr int NMS_NT = 1024;         // cluster form: threads per CTA
 constexpr int NMS_BATCH_NT = 512;    // one CTA per frame: three CTAs per SM for 640x480 frames
-constexpr int NMS_SMEM_MAX = 200 * 1024;   // dynamic shared memory for keys and states
+constexpr int NMS_KEYS_NT = 1024;    // one CTA per frame, key words in shared memory
+// Automatic cluster size: clusters only when a frame would get at least this
+// many SMs (on 152 SMs: up to 19 frames).  At 51-77 frames per batch one CTA
+// per frame measured 1.3-1.8x faster than clusters of 2 or 4.
+constexpr int NMS_AUTO_CLUSTER_MIN = 8;
 
 __device__ __forceinline__ double box_iou(const WinBox &a, const WinBox &b) {
     const double ix1 = a.x > b.x ? a.x : b.x;
@@ -99,13 +103,17 @@ __global__ void __launch_bounds__(256) nms_geometry_kernel(GeomDesc g, int32_t *
     cnt[p] = (uint8_t)n;
 }
 
-// Three CTAs per SM with the workspace in shared memory (40 registers).
-template <bool SM>
-__global__ void __launch_bounds__(NMS_BATCH_NT, SM ? 3 : 2)
+// One CTA per frame: three per SM with the whole workspace in shared memory
+// (40 registers); one per SM of 1024 threads with the key words alone in
+// shared memory; two per SM with everything in global memory.
+template <int WS>
+__global__ void __launch_bounds__(WS == NMS_WS_KEYS ? NMS_KEYS_NT : NMS_BATCH_NT,
+                                  WS == NMS_WS_SMEM ? 3 : (WS == NMS_WS_KEYS ? 1 : 2))
     nms_kernel(const FrameDesc *__restrict__ frames, int *flags) {
+    constexpr int NT = WS == NMS_WS_KEYS ? NMS_KEYS_NT : NMS_BATCH_NT;
     extern __shared__ __align__(16) unsigned char nsm[];
-    __shared__ int sh[NMS_BATCH_NT / 32 + 4];   // warp sums, total
-    nms_frame<SM, NMS_BATCH_NT, false>(frames[blockIdx.x], nsm, flags, sh);
+    __shared__ int sh[NT / 32 + 4];   // warp sums, total
+    nms_frame<WS, NT, false>(frames[blockIdx.x], nsm, flags, sh);
 }
 
 __global__ void __launch_bounds__(256) pack_kernel(const hog_det *__restrict__ dets, int per_frame,
@@ -917,9 +925,11 @@ int nms_cluster_max(int *nsm) {
 }  // namespace
 
 // Cluster size for a batch: `request` 1 = one CTA per frame, 2..16 = that
-// size, 0 = automatic -- spread the batch over the SMs (SMs / frames, a
-// power of two), and at least the size whose per-CTA state fits in shared
-// memory.  Returns 1 for the one-CTA form.
+// size, 0 = automatic -- a cluster of SMs / frames CTAs (a power of two) when
+// that is at least NMS_AUTO_CLUSTER_MIN (a few frames: each gets many SMs),
+// else one CTA per frame, whose frames then run side by side (measured
+// faster from a few dozen frames on); and at least 2 for frames whose
+// one-CTA workspace lives in global memory.  Returns 1 for the one-CTA form.
 int nms_cluster_size(int nframes, int max_npos, int request) {
     int nsm = 1;
     const int cmax = nms_cluster_max(&nsm);
@@ -930,29 +940,20 @@ int nms_cluster_size(int nframes, int max_npos, int request) {
     } else {
         const int want = nsm / nframes;
         c = 1;
-        while (c * 2 <= want && c * 2 <= cmax) c *= 2;
-        if ((nms_ws_bytes(max_npos, true) > (size_t)NMS_SMEM_MAX || max_npos > NMS_SMEM_MAX_NPOS) &&
-            c < 2)
-            c = 2;
+        if (want >= NMS_AUTO_CLUSTER_MIN)
+            while (c * 2 <= want && c * 2 <= cmax) c *= 2;
+        if (nms_ws_class(max_npos) == NMS_WS_GLOBAL && c < 2) c = 2;
     }
+    if (c < 2) return 1;
     while (c < cmax && nms_cluster_ws_bytes(max_npos, c, 0) > (size_t)NMS_SMEM_MAX) c *= 2;
-    if (c >= 2 && nms_cluster_ws_bytes(max_npos, c, 0) > (size_t)NMS_SMEM_MAX) return 1;
+    if (nms_cluster_ws_bytes(max_npos, c, 0) > (size_t)NMS_SMEM_MAX) return 1;
     return c;
 }
 
-cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *flags,
-                       cudaStream_t stream, int cluster_request) {
-    if (nframes <= 0) return cudaSuccess;
-    static PerDevice attr;
-    cudaError_t e_attr = attr.once([&]() {
-        cudaError_t e = cudaFuncSetAttribute(nms_kernel<true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, NMS_SMEM_MAX);
-        if (e == cudaSuccess)   // all of the unified L1 as shared memory: three frames per SM
-            e = cudaFuncSetAttribute(nms_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     cudaSharedmemCarveoutMaxShared);
-        return e;
-    });
-    if (e_attr != cudaSuccess) return e_attr;
+namespace {
+// The frames of one workspace class.
+cudaError_t launch_nms_class(const FrameDesc *frames, int nframes, int max_npos, int cls, int *flags,
+                             cudaStream_t stream, int cluster_request) {
     const int c = nms_cluster_size(nframes, max_npos, cluster_request);
     if (c >= 2) {
         cudaLaunchConfig_t cfg = {};
@@ -991,12 +992,39 @@ cudaError_t launch_nms(const FrameDesc *frames, int nframes, int max_npos, int *
         cfg.dynamicSmemBytes = nms_cluster_ws_bytes(max_npos, c, 0);
         return cudaLaunchKernelEx(&cfg, nms_cluster_kernel<0>, frames, flags);
     }
-    const size_t ws = nms_ws_bytes(max_npos, true);
-    if (ws <= (size_t)NMS_SMEM_MAX && max_npos <= NMS_SMEM_MAX_NPOS)
-        nms_kernel<true><<<nframes, NMS_BATCH_NT, ws, stream>>>(frames, flags);
+    if (cls == NMS_WS_SMEM)
+        nms_kernel<NMS_WS_SMEM><<<nframes, NMS_BATCH_NT, nms_ws_bytes(max_npos, true), stream>>>(frames, flags);
+    else if (cls == NMS_WS_KEYS)
+        nms_kernel<NMS_WS_KEYS><<<nframes, NMS_KEYS_NT, nms_keys_bytes(max_npos), stream>>>(frames, flags);
     else
-        nms_kernel<false><<<nframes, NMS_BATCH_NT, 0, stream>>>(frames, flags);
+        nms_kernel<NMS_WS_GLOBAL><<<nframes, NMS_BATCH_NT, 0, stream>>>(frames, flags);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_nms(const FrameDesc *frames, const int *ncls, const int *max_npos, int *flags,
+                       cudaStream_t stream, int cluster_request) {
+    static PerDevice attr;
+    cudaError_t e_attr = attr.once([&]() {
+        cudaError_t e = cudaFuncSetAttribute(nms_kernel<NMS_WS_SMEM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, NMS_SMEM_MAX);
+        if (e == cudaSuccess)   // all of the unified L1 as shared memory: three frames per SM
+            e = cudaFuncSetAttribute(nms_kernel<NMS_WS_SMEM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(nms_kernel<NMS_WS_KEYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     NMS_KEYS_SMEM_MAX);
+        return e;
+    });
+    if (e_attr != cudaSuccess) return e_attr;
+    int off = 0;
+    for (int k = 0; k < NMS_WS_CLASSES; k++) {
+        if (ncls[k] <= 0) continue;
+        cudaError_t e = launch_nms_class(frames + off, ncls[k], max_npos[k], k, flags, stream, cluster_request);
+        if (e != cudaSuccess) return e;
+        off += ncls[k];
+    }
+    return cudaSuccess;
 }
 
 }  // namespace hogk

@@ -184,6 +184,9 @@ def test_nms_cluster_sizes_agree_on_batches(H, synth, batched):
             assert got.tobytes() == ref.tobytes(), c
     det.set_nms_cluster(0)
     assert det.nms_cluster_size(1, 1280, 1024) >= 2
+    cmax = det.nms_cluster_size(1, 640, 480)
+    assert det.nms_cluster_size(4, 640, 480) == cmax    # a few frames: many SMs each
+    assert det.nms_cluster_size(64, 1280, 1024) == 1    # dozens: one CTA per frame
     assert det.nms_cluster_size(152, 640, 480) == 1
     with pytest.raises(H.HogError):
         det.set_nms_cluster(3)
