@@ -190,6 +190,7 @@ struct hog_ctx {
     size_t cells_slot = 0, fh_slot = 0, gm_slot = 0;
     int plan_cache_max = 16;        // cached batch plans (a server raises it)
     cudaStream_t cap_stream = nullptr;
+    NmsStreams nms_par = {};        // suppression classes side by side (created at hog_create)
     // hog_detect_host: copy stream and events of the double-buffered staging
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_done[2] = {nullptr, nullptr}, stage_free = nullptr;
@@ -325,6 +326,11 @@ void free_ctx(hog_ctx *ctx) {
     F(ctx->d_train);
     F(ctx->d_wuser); F(ctx->d_wtc); F(ctx->d_fh); F(ctx->d_gm);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (cudaStream_t q : ctx->nms_par.side)
+        if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t q : ctx->nms_par.join)
+        if (q) cudaEventDestroy(q);
+    if (ctx->nms_par.fork) cudaEventDestroy(ctx->nms_par.fork);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (cudaEvent_t e : ctx->copy_done)
         if (e) cudaEventDestroy(e);
@@ -963,7 +969,7 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
         CUDA_TRY(ctx, mark(8));
         if (info.nframes > 0)
             CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.ncls,
-                                     info.cls_npos, ctx->d_flags, stream, ctx->nms_cluster));
+                                     info.cls_npos, ctx->d_flags, stream, ctx->nms_cluster, &ctx->nms_par));
         CUDA_TRY(ctx, mark(9));
         if (ctx->prof) {
             ctx->stats[4].launches += info.nframes > 0;
@@ -1173,7 +1179,7 @@ int launch_fused_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStr
         CUDA_TRY(ctx, mark(8));
         if (info.nframes > 0)
             CUDA_TRY(ctx, launch_nms(reinterpret_cast<const FrameDesc *>(d + L.frames), info.ncls,
-                                     info.cls_npos, ctx->d_flags, stream, ctx->nms_cluster));
+                                     info.cls_npos, ctx->d_flags, stream, ctx->nms_cluster, &ctx->nms_par));
         CUDA_TRY(ctx, mark(9));
         if (ctx->prof) {
             ctx->stats[4].launches += info.nframes > 0;
@@ -1441,6 +1447,11 @@ int hog_create(const hog_params *p, const float *filters_host, int32_t n_filters
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&ctx->m_counts, ctx->h_counts, 0);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_flags, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->plan_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->nms_par.fork, cudaEventDisableTiming);
+    for (int k = 0; k < NMS_WS_CLASSES - 1 && e == cudaSuccess; k++) {
+        e = cudaStreamCreateWithFlags(&ctx->nms_par.side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->nms_par.join[k], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         g_create_error = std::string("allocation failed: ") + cudaGetErrorString(e);
         cudaGetLastError();

@@ -339,11 +339,6 @@ cudaError_t launch_nms_geometry(const GeomDesc &g, int32_t *nbr, int32_t *nbr_t,
 cudaError_t launch_pack(const hog_det *dets, int per_frame, const int32_t *counts, int nframes,
                         hog_det *out, int out_cap, int32_t *counts_out, cudaStream_t stream);
 
-// frames: sorted by workspace class (nms_ws_class of npos); ncls[k] frames
-// of class k with at most max_npos[k] positions, each class its own launch.
-// flags[0] |= 1 on capacity overflow; flags[2] |= 1 if a bounded wait gave up.
-cudaError_t launch_nms(const FrameDesc *frames, const int *ncls, const int *max_npos, int *flags,
-                       cudaStream_t stream, int cluster_request);
 // Cluster size launch_nms uses for such a batch (1 = one CTA per frame).
 int nms_cluster_size(int nframes, int max_npos, int request);
 
@@ -371,6 +366,20 @@ __host__ __device__ constexpr int nms_ws_class(int npos) {
            : nms_keys_bytes(npos) <= (size_t)NMS_KEYS_SMEM_MAX                          ? NMS_WS_KEYS
                                                                                          : NMS_WS_GLOBAL;
 }
+
+// Streams and events for running a batch's suppression classes side by side:
+// the larger classes on side streams forked from and joined back into the
+// caller's stream (also under graph capture, as parallel branches).
+struct NmsStreams {
+    cudaStream_t side[NMS_WS_CLASSES - 1];
+    cudaEvent_t fork, join[NMS_WS_CLASSES - 1];
+};
+// frames: sorted by workspace class (nms_ws_class of npos); ncls[k] frames
+// of class k with at most max_npos[k] positions, each class its own launch
+// (concurrent through par when it is given and several classes have frames).
+// flags[0] |= 1 on capacity overflow; flags[2] |= 1 if a bounded wait gave up.
+cudaError_t launch_nms(const FrameDesc *frames, const int *ncls, const int *max_npos, int *flags,
+                       cudaStream_t stream, int cluster_request, const NmsStreams *par = nullptr);
 
 // Histogram tile width (blocks) for a level of cx x cy cells and height h
 // pixels: the bw in [HIST_BW_MIN, HIST_BW_MAX] whose tiles issue the fewest

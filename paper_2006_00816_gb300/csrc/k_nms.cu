@@ -1003,7 +1003,7 @@ cudaError_t launch_nms_class(const FrameDesc *frames, int nframes, int max_npos,
 }  // namespace
 
 cudaError_t launch_nms(const FrameDesc *frames, const int *ncls, const int *max_npos, int *flags,
-                       cudaStream_t stream, int cluster_request) {
+                       cudaStream_t stream, int cluster_request, const NmsStreams *par) {
     static PerDevice attr;
     cudaError_t e_attr = attr.once([&]() {
         cudaError_t e = cudaFuncSetAttribute(nms_kernel<NMS_WS_SMEM>,
@@ -1017,14 +1017,44 @@ cudaError_t launch_nms(const FrameDesc *frames, const int *ncls, const int *max_
         return e;
     });
     if (e_attr != cudaSuccess) return e_attr;
-    int off = 0;
-    for (int k = 0; k < NMS_WS_CLASSES; k++) {
-        if (ncls[k] <= 0) continue;
-        cudaError_t e = launch_nms_class(frames + off, ncls[k], max_npos[k], k, flags, stream, cluster_request);
-        if (e != cudaSuccess) return e;
-        off += ncls[k];
+    int off[NMS_WS_CLASSES], nonempty = 0;
+    for (int k = 0, o = 0; k < NMS_WS_CLASSES; k++) {
+        off[k] = o;
+        o += ncls[k];
+        nonempty += ncls[k] > 0;
     }
-    return cudaSuccess;
+    if (!par || nonempty < 2) {
+        for (int k = 0; k < NMS_WS_CLASSES; k++) {
+            if (ncls[k] <= 0) continue;
+            cudaError_t e = launch_nms_class(frames + off[k], ncls[k], max_npos[k], k, flags, stream,
+                                             cluster_request);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    // the larger classes (longer frames, one CTA or a cluster per SM) go
+    // first, each on a side stream; the shared-memory class fills the SMs
+    // they leave on the caller's stream
+    cudaError_t e = cudaEventRecord(par->fork, stream);
+    int nside = 0;
+    for (int k = NMS_WS_CLASSES - 1; k >= 1 && e == cudaSuccess; k--) {
+        if (ncls[k] <= 0) continue;
+        cudaStream_t s = par->side[nside];
+        e = cudaStreamWaitEvent(s, par->fork, 0);
+        if (e == cudaSuccess)
+            e = launch_nms_class(frames + off[k], ncls[k], max_npos[k], k, flags, s, cluster_request);
+        if (e == cudaSuccess) e = cudaEventRecord(par->join[nside], s);
+        if (e == cudaSuccess) nside++;
+    }
+    if (e == cudaSuccess && ncls[0] > 0)
+        e = launch_nms_class(frames + off[0], ncls[0], max_npos[0], 0, flags, stream, cluster_request);
+    // join every branch that was forked, also after an error (a capture
+    // must end with its side streams joined)
+    for (int j = 0; j < nside; j++) {
+        cudaError_t ej = cudaStreamWaitEvent(stream, par->join[j], 0);
+        if (e == cudaSuccess) e = ej;
+    }
+    return e;
 }
 
 }  // namespace hogk
