@@ -905,6 +905,7 @@ __device__ __forceinline__ bool nms_scanned(const FrameDesc &fd, int p) {
 // WS: where the workspace lives (nms_ws_class): NMS_WS_SMEM all of it in
 // shared memory, NMS_WS_KEYS the key words in shared memory and the rest in
 // fd.ws, NMS_WS_GLOBAL all of it in fd.ws.
+constexpr int NMS_SCAN_U = 4;   // candidates whose scans start together
 template <int WS, int NT, bool COH>
 __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *smem, int *flags,
                                           int *sh /* NT/32 + 4 ints of shared memory */) {
@@ -1028,40 +1029,59 @@ __device__ __forceinline__ void nms_frame(const FrameDesc &fd, unsigned char *sm
                     }
                 }
             }
-            // candidates with slots left: the warp scans them one at a time,
-            // a lane per slot, and takes the first unsettled slot in order
-            for (unsigned um = __ballot_sync(0xffffffffu, p >= 0 && !dead && !wait && !done); um;
-                 um &= um - 1) {
-                const int src = __ffs(um) - 1;
-                const int pp = __shfl_sync(0xffffffffu, p, src);
-                const uint32_t hpp = __shfl_sync(0xffffffffu, hp, src);
-                int res = 0, at = 0;   // 0: all settled, 1: kept neighbour, 2: undecided one
-                for (int sb = __shfl_sync(0xffffffffu, settled, src);; sb += 32) {
-                    const int sl = sb + lane;
-                    const int q = sl < MAXN ? __ldg(nbr_t + (size_t)pp * MAXN + sl) : -1;
-                    const unsigned end = __ballot_sync(0xffffffffu, q < 0);
-                    uint32_t cls = 0;
-                    if (q >= 0) {
-                        const uint32_t hq = khi[q];
-                        if (hq == NMS_KEPTKEY) cls = 1u;
-                        else if (hq != NMS_NOKEY && above(q, pp, hq, hpp)) cls = 2u;
-                    }
-                    const unsigned hit = __ballot_sync(0xffffffffu, cls != 0);
-                    if (hit) {   // slots after the list's end are -1: a hit comes first
-                        const int f = __ffs(hit) - 1;
-                        res = (int)__shfl_sync(0xffffffffu, cls, f);
-                        at = sb + f;
-                        break;
-                    }
-                    if (end) {
-                        at = sb + __ffs(end) - 1;
-                        break;
-                    }
+            // candidates with slots left: the warp scans them, a lane per
+            // slot, and takes the first unsettled slot in order.  NMS_SCAN_U
+            // candidates at a time: their first 32 slots are loaded together
+            // (one wait on L2 for all of them), the rest one chunk at a time
+            for (unsigned um = __ballot_sync(0xffffffffu, p >= 0 && !dead && !wait && !done); um;) {
+                int srcs[NMS_SCAN_U], sbs[NMS_SCAN_U], qs[NMS_SCAN_U];
+#pragma unroll
+                for (int j = 0; j < NMS_SCAN_U; j++) {
+                    srcs[j] = um ? __ffs(um) - 1 : -1;   // warp-uniform
+                    um &= um ? um - 1 : 0u;
+                    const int sj = srcs[j] < 0 ? 0 : srcs[j];
+                    const int pj = __shfl_sync(0xffffffffu, p, sj);
+                    sbs[j] = __shfl_sync(0xffffffffu, settled, sj);
+                    const int sl = sbs[j] + lane;
+                    qs[j] = srcs[j] >= 0 && sl < MAXN ? __ldg(nbr_t + (size_t)pj * MAXN + sl) : -1;
                 }
-                if (lane == src) {
-                    if (res == 1) dead = true;
-                    else if (res == 2) wait = true;
-                    settled = at;
+#pragma unroll
+                for (int j = 0; j < NMS_SCAN_U; j++) {
+                    const int src = srcs[j];
+                    if (src < 0) break;   // warp-uniform
+                    const int pp = __shfl_sync(0xffffffffu, p, src);
+                    const uint32_t hpp = __shfl_sync(0xffffffffu, hp, src);
+                    int res = 0, at = 0;   // 0: all settled, 1: kept neighbour, 2: undecided one
+                    int q = qs[j];
+                    for (int sb = sbs[j];; sb += 32) {
+                        if (sb != sbs[j]) {
+                            const int sl = sb + lane;
+                            q = sl < MAXN ? __ldg(nbr_t + (size_t)pp * MAXN + sl) : -1;
+                        }
+                        const unsigned end = __ballot_sync(0xffffffffu, q < 0);
+                        uint32_t cls = 0;
+                        if (q >= 0) {
+                            const uint32_t hq = khi[q];
+                            if (hq == NMS_KEPTKEY) cls = 1u;
+                            else if (hq != NMS_NOKEY && above(q, pp, hq, hpp)) cls = 2u;
+                        }
+                        const unsigned hit = __ballot_sync(0xffffffffu, cls != 0);
+                        if (hit) {   // slots after the list's end are -1: a hit comes first
+                            const int f = __ffs(hit) - 1;
+                            res = (int)__shfl_sync(0xffffffffu, cls, f);
+                            at = sb + f;
+                            break;
+                        }
+                        if (end) {
+                            at = sb + __ffs(end) - 1;
+                            break;
+                        }
+                    }
+                    if (lane == src) {
+                        if (res == 1) dead = true;
+                        else if (res == 2) wait = true;
+                        settled = at;
+                    }
                 }
             }
             if (p >= 0) {
