@@ -137,3 +137,23 @@ def test_host_chunks_with_one_suppression(H, synth, mode):
     part, pc = det.detect_host(pinned[:8], det_cap=cap, allow_capacity=True)
     assert pc.tolist() == rc.tolist() and len(part) == cap
     assert np.array_equal(part, ref[:cap])
+
+
+@pytest.mark.gpu
+def test_host_chunks_mixed_workspace_classes(H, synth):
+    """A chunked host group whose frames fall in two suppression workspace
+    classes (whole workspace in shared memory, key words alone in shared
+    memory), which one back plan launches side by side: equal to the device
+    batch and to the per-frame calls."""
+    W = synth.filters(5)
+    frames = synth.mixed_frames(12)
+    sizes = {f.shape for f in frames}
+    assert (1024, 1280) in sizes or (720, 1280) in sizes
+    assert (480, 640) in sizes or (240, 320) in sizes
+    det = H.Detector(W, max_w=1280, max_h=1024, max_batch=8)
+    ref, rc = det.detect([dev(f) for f in frames])
+    dev_b, dc = det.detect([dev(f) for f in frames], batched=True)
+    assert dc.tolist() == rc.tolist() and np.array_equal(dev_b, ref)
+    for _ in range(2):
+        got, gc = det.detect_host(frames)
+        assert gc.tolist() == rc.tolist() and np.array_equal(got, ref)
