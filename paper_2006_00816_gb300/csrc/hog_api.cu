@@ -923,35 +923,15 @@ int launch_plan(hog_ctx *ctx, const char *d, const PlanInfo &info, cudaStream_t 
     if (stages & STAGES_FRONT) {
         CUDA_TRY(ctx, mark(0));
         int npyr = 0;
-        // the pyramid steps in order: the large ones as launches of their
-        // own, the trailing run of steps with at most one tile per CTA of
-        // the chain cluster (the last levels of a few frames) in one cluster
-        // launch, where separate launches would cost more than their work
-        struct Step { size_t off; int n; bool direct; };
-        Step steps[PYR_CHAIN_MAX_STEPS + MAX_LEVELS];
-        int ns = 0;
-        if (L.npyrd > 0) steps[ns++] = {L.pyrd, L.npyrd, true};
-        for (size_t s = 1; s < L.pyr.size(); s++)
-            if (L.npyr[s] > 0) steps[ns++] = {L.pyr[s], L.npyr[s], false};
-        const int cc = ns >= 2 ? pyramid_chain_size() : 0;
-        int k0 = ns;   // first step of the chained tail
-        while (cc > 0 && k0 > 0 && steps[k0 - 1].n <= cc && ns - (k0 - 1) <= PYR_CHAIN_MAX_STEPS) k0--;
-        if (ns - k0 < 2) k0 = ns;
-        for (int k = 0; k < k0; k++) {
-            const Job *jb = reinterpret_cast<const Job *>(d + steps[k].off);
-            CUDA_TRY(ctx, steps[k].direct ? launch_pyramid_direct(descs, jb, steps[k].n, stream)
-                                          : launch_pyramid(descs, jb, steps[k].n, stream));
+        if (L.npyrd > 0) {
+            CUDA_TRY(ctx, launch_pyramid_direct(descs, reinterpret_cast<const Job *>(d + L.pyrd), L.npyrd,
+                                                stream));
             npyr++;
         }
-        if (k0 < ns) {
-            PyrChain chain;
-            chain.nsteps = ns - k0;
-            for (int k = k0; k < ns; k++) {
-                chain.first[k - k0] = (int32_t)(steps[k].off / sizeof(Job));
-                chain.count[k - k0] = steps[k].n;
-            }
-            CUDA_TRY(ctx, launch_pyramid_chain(descs, reinterpret_cast<const Job *>(d), chain, stream));
-            npyr++;
+        for (size_t s = 1; s < L.pyr.size(); s++) {
+            CUDA_TRY(ctx, launch_pyramid(descs, reinterpret_cast<const Job *>(d + L.pyr[s]),
+                                         L.npyr[s], stream));
+            npyr += L.npyr[s] > 0;
         }
         CUDA_TRY(ctx, mark(1));
         CUDA_TRY(ctx, mark(2));

@@ -321,21 +321,6 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // ---- launchers (each enqueues on `stream`; return cudaGetLastError()) ----
 cudaError_t launch_pyramid(const LevelDesc *descs, const Job *jobs, int njobs,
                            cudaStream_t stream);
-// The small pyramid steps of a batch (the last levels of a few frames) in one
-// launch: one thread-block cluster walks the steps in order (step k's jobs
-// are jobs[first[k] .. first[k] + count[k])), each CTA taking at most one
-// tile per step, with a cluster barrier between steps.  Returns
-// cudaErrorNotSupported, launching nothing, where no cluster of at least 8
-// CTAs can run or a step has more tiles than the cluster has CTAs.
-constexpr int PYR_CHAIN_MAX_STEPS = MAX_LEVELS + 1;
-struct PyrChain {
-    int32_t nsteps;
-    int32_t first[PYR_CHAIN_MAX_STEPS], count[PYR_CHAIN_MAX_STEPS];
-};
-cudaError_t launch_pyramid_chain(const LevelDesc *descs, const Job *jobs, const PyrChain &chain,
-                                 cudaStream_t stream);
-// CTAs of the chain's cluster on the current device (0: no chain).
-int pyramid_chain_size();
 cudaError_t launch_pyramid_direct(const LevelDesc *descs, const Job *jobs, int njobs,
                                   cudaStream_t stream);
 cudaError_t launch_hist(const LevelDesc *descs, const Job *jobs, int njobs,
